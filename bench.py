@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Throughput of the adjoint-gradient evaluation on one GB300 (or N replicas).
+
+Workload: 256^3 cells of 1 mm, design box = output grid, M0 = (0, 0, Ms),
+p = 3, rho ~ U[0,1] (seed 7), objective J = sum over a centred 64 x 64 patch of
+the top layer of (H_z - 0.2 Ms)^2; padded FFT grid 512^3. One step = one
+stray-field + adjoint-gradient evaluation (tm_objective_and_gradient: forward
+x/y/z/y/x passes with the fused objective, adjoint passes with the fused chain
+rule) followed by one projected-gradient update (tm_optimize_step). The
+tensor setup is excluded, as in the paper's timings.
+
+Arms:
+  native (default)  the CUDA library through its C ABI
+  cufft             the same pipeline built on cuFFT (comparison baseline)
+  reference         the float64 CPU oracle on the host cores
+
+Multi-GPU: the path does not shard (a 3-D FFT convolution needs an all-to-all
+transpose); N ranks run independent replicas, value = sum of their evals/s.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "adjoint-gradient evals/s at 256^3 cells, FP32 vs FP64 oracle; % of HBM peak"
+UNIT = "evals/s"
+
+# DRAM bytes per launch of the z pass at 256^3 from one ncu capture
+# (profiles/zpass_256cube_ncu.md); valid only while the kernel source is unchanged.
+ZPASS_TRAFFIC = {"bytes": None, "source_sha1": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "cufft", "reference"], default="native")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    import torch
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return rank, ws, local, dist
+    return 0, 1, 0, None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def alg_bytes(wl, L):
+    """Algorithmic bytes per launch of each kernel kind (half spectra kx = 0..L/2, no padding)."""
+    nx, ny, nz = wl.n_out
+    nzd = wl.nzd
+    Lx, Ly, Lz = L
+    K = Lx // 2 + 1
+    c8 = 3 * 8
+    T = 6 * (Lz // 2 + 1) * (Ly // 2 + 1) * K * 4
+    # forward (zin = nzd, zout = nz) and adjoint (zin = nz, zout = nzd) launches alternate; average them
+    def yz(zin, zout):
+        return {
+            "y_forward": c8 * zin * K * (ny + Ly),
+            "z_pass": c8 * K * Ly * (zin + zout) + T,
+            "y_inverse": c8 * zout * K * (Ly + ny),
+        }
+    f, a = yz(nzd, nz), yz(nz, nzd)
+    out = {k: (f[k] + a[k]) / 2 for k in f}
+    out["x_forward"] = 4 * nzd * ny * nx + c8 * nzd * ny * K
+    obj = c8 * nz * ny * K * 2 + nz * ny * nx  # spectra in, adjoint spectra out, mask
+    chain = c8 * nzd * ny * K + 8 * nzd * ny * nx
+    out["x_inverse"] = (obj + chain) / 2
+    return out
+
+
+def sha1(path):
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def cpu_baseline(wl, args):
+    """The float64 oracle, as it stands, on the host cores: one evaluation of the same workload."""
+    import numpy as np
+
+    from oracle import convolution as C
+    from oracle import objective as O
+
+    cores = len(os.sched_getaffinity(0))
+    t0 = time.time()
+    op = C.FFTOperator(C.Geometry(wl.n_out, wl.nzd, wl.cellsize), workers=cores)
+    t_setup = time.time() - t0
+    rho = wl.rho()
+    t0 = time.perf_counter()
+    J, G, _ = O.objective_and_gradient(op, rho, wl.M0_const(), wl.p, wl.mask(), wl.Ht_const_vec(), wl.w)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one full float64 evaluation (objective + adjoint gradient) of the {wl.n_out[0]}^3 workload, "
+                      f"scipy.fft workers={cores}; tensor setup ({t_setup:.0f} s) excluded",
+            "seconds": dt, "J": J, "G_norm": float(np.linalg.norm(G))}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1707_09898_gb300 import workloads as W
+
+    wl = W.config4(args.n)
+    from oracle import convolution as C
+    from oracle import objective as O
+    from oracle import optimizer as P
+
+    cores = len(os.sched_getaffinity(0))
+    op = C.FFTOperator(C.Geometry(wl.n_out, wl.nzd, wl.cellsize), workers=cores)
+    rho = wl.rho().astype("float64")
+    # each step: one oracle evaluation + update; the timed count is capped so the run stays within minutes
+    steps = max(1, min(args.steps, 3))
+    warm = min(args.warmup, 1)
+    for _ in range(warm):
+        J, G, _ = O.objective_and_gradient(op, rho, wl.M0_const(), wl.p, wl.mask(), wl.Ht_const_vec(), wl.w)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        J, G, _ = O.objective_and_gradient(op, rho, wl.M0_const(), wl.p, wl.mask(), wl.Ht_const_vec(), wl.w)
+        rho = P.projected_gradient_step(rho, G, wl.alpha, True)
+    dt = time.perf_counter() - t0
+    v = steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": steps,
+        "warmup": warm, "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "cells": list(wl.n_out), "fft": [2 * n for n in wl.n_out]},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{steps} full float64 evaluations + updates of the {args.n}^3 workload "
+                                   f"(requested {args.steps}; capped at 3 to bound the run), workers={cores}"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import torch
+
+    rank, ws, local, dist = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    barrier(dist)
+    __graft_entry__.build()
+    from paper_1707_09898_gb300 import Magnet
+    from paper_1707_09898_gb300 import workloads as W
+
+    wl = W.config4(args.n)
+    if args.impl == "cufft":
+        from paper_1707_09898_gb300.cufft_pipeline import CufftMagnet as Impl
+    else:
+        Impl = Magnet
+    m = Impl(wl.n_out, wl.nzd, wl.cellsize, M0=wl.M0_const(), p=wl.p, device=local)
+    rho0 = torch.from_numpy(wl.rho()).to(dev)
+    rho = rho0.clone()
+    mask = torch.from_numpy(wl.mask()).to(dev)
+    Htc, w = tuple(float(v) for v in wl.Ht_const_vec()), wl.w
+    G = torch.empty_like(rho)
+
+    def step():
+        m.objective_and_gradient(rho, mask, Ht_const=Htc, w=w, G=G, sync=False)
+        m.optimize_step(rho, G, wl.alpha, True)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    J0 = m.objective()
+    rho.copy_(rho0)
+    launches_per_step = None
+    if hasattr(m, "profile"):
+        m.profile(True)
+    clocks = Clocks(local)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(s)
+    for _ in range(args.steps):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    barrier(dist)
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, dist)
+    prof = m.profile_read() if hasattr(m, "profile") else {}
+    if hasattr(m, "profile"):
+        m.profile(False)
+        launches_per_step = sum(v[1] for v in prof.values()) / args.steps
+
+    # end to end through the public API: pinned host rho in, J out, every step
+    e2e = None
+    if not args.no_e2e:
+        rho_h = torch.from_numpy(wl.rho()).pin_memory()
+        Js = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            rho.copy_(rho_h, non_blocking=True)
+            m.objective_and_gradient(rho, mask, Ht_const=Htc, w=w, G=G, sync=False)
+            m.optimize_step(rho, G, wl.alpha, True)
+            Js.append(m.objective())  # 8-byte device-to-host read, synchronises
+        dt = time.perf_counter() - t0
+        dt = max_over_ranks(dt, dist)
+        e2e = {"value": ws * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(rho.numel() * 4),
+               "d2h_bytes_per_step": 8}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    value = ws * args.steps / (ms_max / 1e3)
+    hbm, peak_kind = peaks()
+    L = m.fft_lengths()
+    roof = None
+    if prof:
+        ab = alg_bytes(wl, L)
+        kind = max((k for k in prof if prof[k][1] > 0 and k in ab), key=lambda k: prof[k][0])
+        t_launch = prof[kind][0] / prof[kind][1] / 1e3
+        achieved = ab[kind] / t_launch / 1e9
+        traffic = None
+        src = os.path.join(ROOT, "paper_1707_09898_gb300", "csrc", "k_yz.cu")
+        if kind == "z_pass" and ZPASS_TRAFFIC["bytes"] and ZPASS_TRAFFIC["source_sha1"] == sha1(src):
+            traffic = ZPASS_TRAFFIC["bytes"]
+        roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                "alg_bytes_per_launch": ab[kind], "ms_per_launch": t_launch * 1e3,
+                "per_kernel_ms_per_step": {k: prof[k][0] / args.steps for k in prof}}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "impl": args.impl,
+        "config": {"workload": wl.name, "cells": list(wl.n_out), "fft": list(L), "step": "objective+gradient+update",
+                   "parallelism": f"replicas{ws}", "l2": "working set (>2 GB) larger than L2; no flush"},
+        "clocks": ck, "gpu_launches": (int(round(launches_per_step * args.steps)) if launches_per_step else None),
+        "roofline": roof, "e2e": e2e, "J_first": J0,
+    }
+    if ws == 1 and not args.no_cpu_baseline and args.impl == "native":
+        try:
+            line["cpu_baseline"] = cpu_baseline(wl, args)
+        except Exception as ex:  # report, never fall back
+            line["cpu_baseline"] = {"error": repr(ex)}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

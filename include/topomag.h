@@ -1,0 +1,157 @@
+/*
+ * topomag -- C ABI of the GPU (sm_103a) finite-difference magnet topology
+ * optimizer: the FFT-accelerated stray-field operator, its adjoint gradient and
+ * a projected-gradient update, after Abert et al., "A fast finite-difference
+ * algorithm for topology optimization of permanent magnets" (arXiv:1707.09898).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Geometry. The output grid has n_out = (nx, ny, nz) cuboid cells of size
+ *   cellsize = (dx, dy, dz) metres. The design box is its bottom slab
+ *   z in [0, nzd) with the same nx, ny. The density rho lives on the design box
+ *   (rho = 0, hence M = 0, outside it); fields live on the output grid.
+ * Layout. Every array is a C-contiguous float32 (or uint8) array:
+ *   rho, dJdrho      [nzd][ny][nx]
+ *   H, gH, H_target  [3][nz][ny][nx]   (component-major: x, y, z)
+ *   mask             [nz][ny][nx]      (uint8, nonzero = target cell)
+ *   M0 (varying)     [3][nzd][ny][nx]  (A/m)
+ * Units. M0 and H in A/m; J in (A/m)^2 times the weights.
+ * Memory. Array pointers are DEVICE pointers on the context's device, owned by
+ *   the caller; the library never frees them. 16-byte alignment is recommended
+ *   (the update kernel vectorises when both of its arrays are aligned).
+ *   The library owns the tensor, twiddle tables and workspace of a context.
+ * Streams. `stream` is a cudaStream_t (NULL = legacy default stream). Calls
+ *   enqueue their kernels on it and return without synchronising, except where
+ *   stated (tm_set_tensor, and tm_objective_and_gradient with J_host != NULL).
+ *   A context must not be used from two host threads at once, and calls on one
+ *   context must not overlap on the GPU (they share its workspace).
+ * Errors. Every int-returning call returns TM_OK (0) or a negative code and then
+ *   leaves a message for tm_last_error(). Nothing is thrown across the ABI.
+ */
+#ifndef TOPOMAG_H
+#define TOPOMAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TM_OK 0
+#define TM_ERR_ARG (-1)      /* null/invalid argument */
+#define TM_ERR_SIZE (-2)     /* grid outside the supported sizes */
+#define TM_ERR_STATE (-3)    /* call order: e.g. no grid, no tensor, no M0 */
+#define TM_ERR_CUDA (-4)     /* a CUDA call failed (message has the CUDA error) */
+#define TM_ERR_NOMEM (-5)    /* device allocation failed */
+
+typedef struct tm_ctx tm_ctx;
+
+/* Create a context bound to CUDA device `device`. *out receives the handle. */
+int tm_create(tm_ctx** out, int device);
+
+/* Release the context and everything it owns (not the caller's arrays). */
+void tm_destroy(tm_ctx* ctx);
+
+/* Message of the last failing call on ctx (empty string if none). */
+const char* tm_last_error(const tm_ctx* ctx);
+
+/* Library version string. */
+const char* tm_version(void);
+
+/*
+ * Grid (Sec. "Discretization": regular cuboid grid, Eq. (convolution)).
+ * n_out[3] = (nx, ny, nz), each in [4, 288]; 1 <= nzd <= nz; cellsize[3] > 0.
+ * Each axis is zero padded to L = the smallest supported even 2^a 3^b >= 2 n
+ * (open boundaries). Allocates the workspace; discards tensor and M0.
+ * TM_ERR_SIZE if an axis is outside the supported range.
+ */
+int tm_set_grid(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[3]);
+
+/* The padded FFT lengths (Lx, Ly, Lz) chosen by tm_set_grid. */
+int tm_get_fft_lengths(const tm_ctx* ctx, int L[3]);
+
+/* Penalty exponent p of M = rho^p M0 (Sec. "Methodology", Eq. 2). Default 3. p >= 1. */
+int tm_set_penalty(tm_ctx* ctx, double p);
+
+/*
+ * Prescribed magnetization M0 (Sec. "Methodology", Eq. 2): spatially constant
+ * (M0_dev == NULL, M0_const[3] in A/m) or varying (M0_dev = device array
+ * [3][nzd][ny][nx], copied into the context on `stream`).
+ */
+int tm_set_M0(tm_ctx* ctx, const float* M0_dev, const double M0_const[3], void* stream);
+
+/*
+ * Demagnetization tensor (Sec. "Discretization", Eq. (demag_tensor)) in float64
+ * on the device: Newell's closed form for offsets with max(|i|,|j|,|k|) <= 16,
+ * a tent-averaged dipole rule beyond; transformed once, scaled by
+ * -1/(Lx Ly Lz) and stored as float32. Synchronises `stream`. Setup only.
+ */
+int tm_set_tensor(tm_ctx* ctx, void* stream);
+
+/*
+ * Stray field H = D[M(rho)] = -sum_j N(i - j) rho_j^p M0_j on the output grid
+ * (Sec. "Discretization", Eq. (convolution); Sec. "Methodology", Eq. 2).
+ * rho [nzd][ny][nx] in [0, 1] -> H [3][nz][ny][nx].
+ */
+int tm_stray_field(tm_ctx* ctx, const float* rho, float* H, void* stream);
+
+/*
+ * Adjoint of tm_stray_field w.r.t. rho for an arbitrary cotangent gH:
+ * dJdrho_j = p rho_j^(p-1) M0_j . (D gH)_j, D self-adjoint (Sec. "Methodology",
+ * Eqs. (adjoint1)-(adjoint2) and the operator form of the gradient).
+ * gH [3][nz][ny][nx] -> dJdrho [nzd][ny][nx].
+ */
+int tm_stray_field_adjoint(tm_ctx* ctx, const float* rho, const float* gH, float* dJdrho, void* stream);
+
+/*
+ * Objective and adjoint gradient (Sec. "Methodology", Eq. (objective_function)
+ * and Eqs. (adjoint1)-(adjoint2)) for the least-squares objective
+ *   J = sum_{i: mask_i != 0} sum_c w_c (H_{i,c} - Ht_{i,c})^2,
+ * with Ht = H_target (device [3][nz][ny][nx]) or, if H_target == NULL, the
+ * constant vector Ht_const[3]. w[3] are host floats.
+ * Writes dJdrho [nzd][ny][nx]; H_out (device [3][nz][ny][nx]) if not NULL.
+ * J (float64) is kept on the device; if J_host != NULL the call synchronises
+ * `stream` and stores it there, else read it later with tm_get_objective.
+ */
+int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask, const float* H_target,
+                              const float Ht_const[3], const float w[3], double* J_host, float* dJdrho,
+                              float* H_out, void* stream);
+
+/* J of the last tm_objective_and_gradient (synchronises `stream`). */
+int tm_get_objective(tm_ctx* ctx, double* J_host, void* stream);
+
+/*
+ * Projected-gradient step on the box 0 <= rho <= 1 (box constraint of Sec.
+ * "Methodology"): rho <- clip(rho - alpha G / max|G|, 0, 1) if normalize != 0
+ * (no change when max|G| = 0), else rho <- clip(rho - alpha G, 0, 1).
+ * rho [nzd][ny][nx] updated in place; G = dJdrho [nzd][ny][nx].
+ */
+int tm_optimize_step(tm_ctx* ctx, float* rho, const float* dJdrho, float alpha, int normalize, void* stream);
+
+/*
+ * Per-kernel timing. tm_profile(ctx, 1) starts recording a CUDA event pair on
+ * the launch stream around every kernel the context launches (and resets the
+ * record); tm_profile(ctx, 0) stops. tm_profile_read synchronises on the
+ * recorded events and returns, per kernel kind, the summed event time in ms and
+ * the launch count. Kinds: 0 x forward, 1 y forward, 2 z pass (forward z FFT,
+ * tensor product, inverse z FFT), 3 y inverse, 4 x inverse (+ objective or
+ * chain rule), 5 other (objective reduction, update).
+ */
+int tm_profile(tm_ctx* ctx, int on);
+int tm_profile_read(tm_ctx* ctx, double ms[6], int launches[6]);
+
+/*
+ * Inspection (tests): the float64 tensor N at the offsets of the non-negative
+ * octant, host array [6][nz][ny][nx] (components xx, yy, zz, xy, xz, yz), and
+ * the stored float32 transformed tensor, host array [6][Lz/2+1][Ly/2+1][Lx/2+1]
+ * (already multiplied by -1/(Lx Ly Lz)). Both synchronise `stream`.
+ */
+int tm_debug_tensor_octant(tm_ctx* ctx, double* host_out, void* stream);
+int tm_debug_tensor_spectrum(tm_ctx* ctx, float* host_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TOPOMAG_H */

@@ -1,0 +1,78 @@
+"""ctypes loader of libtopomag.so (argument marshalling only).
+
+The library is built in-tree by ``paper_1707_09898_gb300.build``. There is no
+fallback: if the shared object is missing or does not load, every call raises.
+"""
+
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtopomag.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "topomag.h")
+
+TM_OK = 0
+ERRORS = {-1: "TM_ERR_ARG", -2: "TM_ERR_SIZE", -3: "TM_ERR_STATE", -4: "TM_ERR_CUDA", -5: "TM_ERR_NOMEM"}
+
+_lib = None
+
+c_int3 = ctypes.c_int * 3
+c_double3 = ctypes.c_double * 3
+c_float3 = ctypes.c_float * 3
+vp = ctypes.c_void_p
+
+_SIGS = {
+    "tm_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int]),
+    "tm_destroy": (None, [vp]),
+    "tm_last_error": (ctypes.c_char_p, [vp]),
+    "tm_version": (ctypes.c_char_p, []),
+    "tm_set_grid": (ctypes.c_int, [vp, c_int3, ctypes.c_int, c_double3]),
+    "tm_get_fft_lengths": (ctypes.c_int, [vp, c_int3]),
+    "tm_set_penalty": (ctypes.c_int, [vp, ctypes.c_double]),
+    "tm_set_M0": (ctypes.c_int, [vp, vp, c_double3, vp]),
+    "tm_set_tensor": (ctypes.c_int, [vp, vp]),
+    "tm_stray_field": (ctypes.c_int, [vp, vp, vp, vp]),
+    "tm_stray_field_adjoint": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+    "tm_objective_and_gradient": (ctypes.c_int, [vp, vp, vp, vp, c_float3, c_float3, ctypes.POINTER(ctypes.c_double),
+                                                 vp, vp, vp]),
+    "tm_get_objective": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), vp]),
+    "tm_optimize_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_float, ctypes.c_int, vp]),
+    "tm_profile": (ctypes.c_int, [vp, ctypes.c_int]),
+    "tm_profile_read": (ctypes.c_int, [vp, ctypes.c_double * 6, ctypes.c_int * 6]),
+    "tm_debug_tensor_octant": (ctypes.c_int, [vp, vp, vp]),
+    "tm_debug_tensor_spectrum": (ctypes.c_int, [vp, vp, vp]),
+}
+
+
+def header_functions():
+    """Names of the functions declared in include/topomag.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(tm_\w+)\s*\(", txt)))
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libtopomag.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class TopomagError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(ctx, code):
+    if code != TM_OK:
+        msg = lib().tm_last_error(ctx).decode() if ctx else ""
+        raise TopomagError(code, msg)

@@ -1,0 +1,589 @@
+// C ABI of libtopomag: context, workspace and the pass sequences of the
+// stray-field operator D, its adjoint, the fused objective/gradient and the
+// projected update. Every array argument is a caller-owned device pointer.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/topomag.h"
+#include "fft.cuh"
+#include "internal.h"
+
+using namespace tmk;
+
+struct tm_ctx {
+  int device = 0;
+  int nx = 0, ny = 0, nz = 0, nzd = 0;
+  double d[3] = {0, 0, 0};
+  int L[3] = {0, 0, 0};
+  int P = 0;
+  double p = 3.0;
+  bool have_grid = false, have_tensor = false, have_M0 = false;
+  bool m0_var = false;
+  double M0c[3] = {0, 0, 0};
+  float* M0v = nullptr;     // [3][nzd][ny][nx]
+  float* T = nullptr;       // [6][Lz/2+1][Ly/2+1][P]
+  float2* A = nullptr;      // [3][nz][ny][P]
+  float2* B = nullptr;      // [3][nz][Ly][P]
+  float2* tw = nullptr;     // twiddles: Lx | Ly | Lz
+  int2* zcol = nullptr;     // [Ly]
+  double* Jpart = nullptr;  // [ceil(nz*ny/rows_per_block)]
+  int nJpart = 0;
+  double* Jdev = nullptr;
+  unsigned int* gmax = nullptr;
+  double* Jhost = nullptr;  // pinned
+  // per-kernel event timing (tm_profile)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev;  // pairs
+  std::vector<int> ev_kind;
+  size_t ev_used = 0;
+  char err[512] = {0};
+};
+
+namespace {
+
+int fail(tm_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? TM_ERR_NOMEM : TM_ERR_CUDA, "%s: %s", #call, \
+                  cudaGetErrorString(e_));                                                         \
+  } while (0)
+
+#define CKL(call)                                                                                  \
+  do {                                                                                             \
+    int r_ = (call);                                                                               \
+    if (r_ != 0) {                                                                                 \
+      cudaError_t e_ = cudaGetLastError();                                                         \
+      return fail(ctx, r_ == -2 ? TM_ERR_SIZE : TM_ERR_CUDA, "%s failed: %s", #call,               \
+                  cudaGetErrorString(e_));                                                         \
+    }                                                                                              \
+  } while (0)
+
+int pick_length(int n) {
+  static const int ls[] = {
+#define TM_LIST(LL) LL,
+      TM_FOR_EACH_L(TM_LIST)
+#undef TM_LIST
+  };
+  for (int L : ls)
+    if (L >= 2 * n) return L;
+  return 0;
+}
+
+void free_grid(tm_ctx* c) {
+  cudaFree(c->M0v);
+  cudaFree(c->T);
+  cudaFree(c->A);
+  cudaFree(c->B);
+  cudaFree(c->tw);
+  cudaFree(c->zcol);
+  cudaFree(c->Jpart);
+  c->M0v = nullptr;
+  c->T = nullptr;
+  c->A = c->B = c->tw = nullptr;
+  c->zcol = nullptr;
+  c->Jpart = nullptr;
+  c->have_grid = c->have_tensor = c->have_M0 = false;
+}
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+enum { KIND_XFWD = 0, KIND_YFWD, KIND_ZPASS, KIND_YINV, KIND_XINV, KIND_OTHER, KIND_N };
+
+// Records a start/stop event pair around one launch when profiling is on.
+struct Timed {
+  tm_ctx* c;
+  cudaStream_t s;
+  size_t slot = (size_t)-1;
+  Timed(tm_ctx* ctx, int kind, cudaStream_t st) : c(ctx), s(st) {
+    if (!c->prof_on) return;
+    if (c->ev_used * 2 + 2 > c->ev.size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return;
+      if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return;
+      }
+      c->ev.push_back(a);
+      c->ev.push_back(b);
+      c->ev_kind.push_back(kind);
+    }
+    slot = c->ev_used++;
+    c->ev_kind[slot] = kind;
+    cudaEventRecord(c->ev[2 * slot], s);
+  }
+  ~Timed() {
+    if (slot != (size_t)-1) cudaEventRecord(c->ev[2 * slot + 1], s);
+  }
+};
+
+long long design_cells(const tm_ctx* c) { return (long long)c->nzd * c->ny * c->nx; }
+long long out_cells(const tm_ctx* c) { return (long long)c->nz * c->ny * c->nx; }
+
+int check_ready(tm_ctx* ctx) {
+  if (!ctx) return TM_ERR_ARG;
+  if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
+  if (!ctx->have_tensor) return fail(ctx, TM_ERR_STATE, "no tensor: call tm_set_tensor first");
+  if (!ctx->have_M0) return fail(ctx, TM_ERR_STATE, "no M0: call tm_set_M0 first");
+  CK(cudaSetDevice(ctx->device));
+  return TM_OK;
+}
+
+// Common middle: forward y, z (tensor), inverse y on A/B. Input planes zin, output planes zout.
+int conv_yz(tm_ctx* ctx, int zin, int zout, cudaStream_t s) {
+  const int Lx = ctx->L[0], Ly = ctx->L[1], Lz = ctx->L[2];
+  const long long P = ctx->P;
+  YArgs y{};
+  y.in = ctx->A;
+  y.out = ctx->B;
+  y.n_in = ctx->ny;
+  y.n_out = Ly;
+  y.nplanes = zin;
+  y.P = ctx->P;
+  y.in_pstride = P;
+  y.out_pstride = P;
+  y.in_zstride = (long long)ctx->ny * P;
+  y.out_zstride = (long long)Ly * P;
+  y.in_cstride = (long long)ctx->nz * ctx->ny * P;
+  y.out_cstride = (long long)ctx->nz * Ly * P;
+  y.tw = ctx->tw + Lx;
+  {
+    Timed t(ctx, KIND_YFWD, s);
+    CKL(launch_yfwd(Ly, y, s));
+  }
+
+  ZArgs z{};
+  z.buf = ctx->B;
+  z.cstride = (long long)ctx->nz * Ly * P;
+  z.zstride = (long long)Ly * P;
+  z.n_in = zin;
+  z.n_out = zout;
+  z.Ly = Ly;
+  z.P = ctx->P;
+  z.T = ctx->T;
+  z.Tz = (long long)(Ly / 2 + 1) * P;
+  z.Tc = (long long)(Lz / 2 + 1) * z.Tz;
+  z.zcol = ctx->zcol;
+  z.tw = ctx->tw + Lx + Ly;
+  {
+    Timed t(ctx, KIND_ZPASS, s);
+    CKL(launch_zpass(Lz, z, s));
+  }
+
+  YArgs yi{};
+  yi.in = ctx->B;
+  yi.out = ctx->A;
+  yi.n_in = Ly;
+  yi.n_out = ctx->ny;
+  yi.nplanes = zout;
+  yi.P = ctx->P;
+  yi.in_pstride = P;
+  yi.out_pstride = P;
+  yi.in_zstride = (long long)Ly * P;
+  yi.out_zstride = (long long)ctx->ny * P;
+  yi.in_cstride = (long long)ctx->nz * Ly * P;
+  yi.out_cstride = (long long)ctx->nz * ctx->ny * P;
+  yi.tw = ctx->tw + Lx;
+  {
+    Timed t(ctx, KIND_YINV, s);
+    CKL(launch_yinv(Ly, yi, s));
+  }
+  return TM_OK;
+}
+
+void fill_m0(const tm_ctx* ctx, float* M0c, const float** M0v, long long* cs) {
+  for (int c = 0; c < 3; c++) M0c[c] = (float)ctx->M0c[c];
+  *M0v = ctx->m0_var ? ctx->M0v : nullptr;
+  *cs = design_cells(ctx);
+}
+
+// forward x pass from rho (design rows) into A
+int xfwd_rho(tm_ctx* ctx, const float* rho, cudaStream_t s) {
+  XFwdArgs x{};
+  x.rows = ctx->nzd * ctx->ny;
+  x.nx = ctx->nx;
+  x.P = ctx->P;
+  x.src = ctx->m0_var ? SRC_RHO_FIELD : SRC_RHO_CONST;
+  x.rho = rho;
+  fill_m0(ctx, x.M0c, &x.M0v, &x.M0v_cstride);
+  x.p = (float)ctx->p;
+  x.out = ctx->A;
+  x.out_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
+  x.tw = ctx->tw;
+  Timed t(ctx, KIND_XFWD, s);
+  CKL(launch_xfwd(ctx->L[0], x, s));
+  return TM_OK;
+}
+
+// inverse x pass on design rows with the chain rule into G (+ max |G|)
+int xinv_chain(tm_ctx* ctx, const float* rho, float* G, cudaStream_t s) {
+  CK(cudaMemsetAsync(ctx->gmax, 0, sizeof(unsigned int), s));
+  XInvArgs x{};
+  x.rows = ctx->nzd * ctx->ny;
+  x.nx = ctx->nx;
+  x.P = ctx->P;
+  x.sink = SINK_CHAIN;
+  x.in = ctx->A;
+  x.in_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
+  x.rho = rho;
+  fill_m0(ctx, x.M0c, &x.M0v, &x.M0v_cstride);
+  x.p = (float)ctx->p;
+  x.G = G;
+  x.gmax = ctx->gmax;
+  x.tw = ctx->tw;
+  Timed t(ctx, KIND_XINV, s);
+  CKL(launch_xinv(ctx->L[0], x, s));
+  return TM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tm_version(void) { return "topomag 0.1 (sm_103a)"; }
+
+int tm_create(tm_ctx** out, int device) {
+  if (!out) return TM_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return TM_ERR_ARG;
+  tm_ctx* ctx = new tm_ctx();
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->Jdev, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->gmax, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->Jhost, sizeof(double));
+  if (e != cudaSuccess) {
+    tm_destroy(ctx);
+    return TM_ERR_CUDA;
+  }
+  *out = ctx;
+  return TM_OK;
+}
+
+void tm_destroy(tm_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  free_grid(ctx);
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  cudaFree(ctx->Jdev);
+  cudaFree(ctx->gmax);
+  if (ctx->Jhost) cudaFreeHost(ctx->Jhost);
+  delete ctx;
+}
+
+const char* tm_last_error(const tm_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+int tm_set_grid(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[3]) {
+  if (!ctx || !n_out || !cellsize) return fail(ctx, TM_ERR_ARG, "null argument");
+  for (int a = 0; a < 3; a++) {
+    if (n_out[a] < 4 || n_out[a] > kMaxL / 2)
+      return fail(ctx, TM_ERR_SIZE, "n_out[%d] = %d outside [4, %d]", a, n_out[a], kMaxL / 2);
+    if (!(cellsize[a] > 0.0) || !isfinite(cellsize[a])) return fail(ctx, TM_ERR_ARG, "cellsize[%d] must be > 0", a);
+  }
+  if (nzd < 1 || nzd > n_out[2]) return fail(ctx, TM_ERR_ARG, "nzd = %d outside [1, nz = %d]", nzd, n_out[2]);
+  CK(cudaSetDevice(ctx->device));
+  free_grid(ctx);
+  ctx->nx = n_out[0];
+  ctx->ny = n_out[1];
+  ctx->nz = n_out[2];
+  ctx->nzd = nzd;
+  for (int a = 0; a < 3; a++) {
+    ctx->d[a] = cellsize[a];
+    ctx->L[a] = pick_length(n_out[a]);
+    if (ctx->L[a] == 0) return fail(ctx, TM_ERR_SIZE, "no supported FFT length for n = %d", n_out[a]);
+  }
+  const int Lx = ctx->L[0], Ly = ctx->L[1], Lz = ctx->L[2];
+  ctx->P = ((Lx / 2 + 1) + TB - 1) / TB * TB;
+  const long long P = ctx->P;
+  if (zpass_smem(Lz) > 227 * 1024) return fail(ctx, TM_ERR_SIZE, "Lz = %d too large for the z pass", Lz);
+
+  CK(cudaMalloc(&ctx->A, 3LL * ctx->nz * ctx->ny * P * sizeof(float2)));
+  CK(cudaMalloc(&ctx->B, 3LL * ctx->nz * Ly * P * sizeof(float2)));
+  CK(cudaMalloc(&ctx->T, 6LL * (Lz / 2 + 1) * (Ly / 2 + 1) * P * sizeof(float)));
+  // twiddles W_L^m = exp(-2 pi i m / L) from float64 host values
+  std::vector<float2> tw;
+  for (int a = 0; a < 3; a++)
+    for (int m = 0; m < ctx->L[a]; m++) {
+      const double t = 2.0 * M_PI * (double)m / (double)ctx->L[a];
+      tw.push_back(make_float2((float)cos(t), (float)(-sin(t))));
+    }
+  CK(cudaMalloc(&ctx->tw, tw.size() * sizeof(float2)));
+  CK(cudaMemcpy(ctx->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  // z-pass column order: ky and Ly - ky adjacent (both read the same folded tensor column)
+  std::vector<int2> zc;
+  for (int ky = 0; ky <= Ly / 2; ky++) {
+    zc.push_back(make_int2(host_pos_of_k(Ly, ky), ky));
+    if (ky > 0 && ky < Ly / 2) zc.push_back(make_int2(host_pos_of_k(Ly, Ly - ky), Ly - ky));
+  }
+  CK(cudaMalloc(&ctx->zcol, zc.size() * sizeof(int2)));
+  CK(cudaMemcpy(ctx->zcol, zc.data(), zc.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  const int rpb = xinv_rows_per_block();
+  ctx->nJpart = (ctx->nz * ctx->ny + rpb - 1) / rpb;
+  CK(cudaMalloc(&ctx->Jpart, ctx->nJpart * sizeof(double)));
+  ctx->have_grid = true;
+  ctx->err[0] = 0;
+  return TM_OK;
+}
+
+int tm_get_fft_lengths(const tm_ctx* ctx, int L[3]) {
+  if (!ctx || !L) return TM_ERR_ARG;
+  if (!ctx->have_grid) return TM_ERR_STATE;
+  for (int a = 0; a < 3; a++) L[a] = ctx->L[a];
+  return TM_OK;
+}
+
+int tm_set_penalty(tm_ctx* ctx, double p) {
+  if (!ctx) return TM_ERR_ARG;
+  if (!(p >= 1.0) || !isfinite(p)) return fail(ctx, TM_ERR_ARG, "penalty p = %g must be >= 1", p);
+  ctx->p = p;
+  return TM_OK;
+}
+
+int tm_set_M0(tm_ctx* ctx, const float* M0_dev, const double M0_const[3], void* stream) {
+  if (!ctx) return TM_ERR_ARG;
+  if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
+  CK(cudaSetDevice(ctx->device));
+  if (M0_dev) {
+    if (!ctx->M0v) CK(cudaMalloc(&ctx->M0v, 3 * design_cells(ctx) * sizeof(float)));
+    CK(cudaMemcpyAsync(ctx->M0v, M0_dev, 3 * design_cells(ctx) * sizeof(float), cudaMemcpyDeviceToDevice,
+                       S(stream)));
+    ctx->m0_var = true;
+    for (int c = 0; c < 3; c++) ctx->M0c[c] = 0.0;
+  } else {
+    if (!M0_const) return fail(ctx, TM_ERR_ARG, "M0_dev and M0_const both null");
+    for (int c = 0; c < 3; c++) {
+      if (!isfinite(M0_const[c])) return fail(ctx, TM_ERR_ARG, "M0_const not finite");
+      ctx->M0c[c] = M0_const[c];
+    }
+    ctx->m0_var = false;
+  }
+  ctx->have_M0 = true;
+  return TM_OK;
+}
+
+int tm_set_tensor(tm_ctx* ctx, void* stream) {
+  if (!ctx) return TM_ERR_ARG;
+  if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
+  CK(cudaSetDevice(ctx->device));
+  int r = tensor_setup(ctx->nx, ctx->ny, ctx->nz, ctx->d, ctx->L[0], ctx->L[1], ctx->L[2], ctx->P, ctx->T, nullptr,
+                       S(stream), ctx->err, sizeof(ctx->err));
+  if (r != 0) return TM_ERR_CUDA;
+  ctx->have_tensor = true;
+  return TM_OK;
+}
+
+int tm_stray_field(tm_ctx* ctx, const float* rho, float* H, void* stream) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!rho || !H) return fail(ctx, TM_ERR_ARG, "null array");
+  cudaStream_t s = S(stream);
+  if ((r = xfwd_rho(ctx, rho, s))) return r;
+  if ((r = conv_yz(ctx, ctx->nzd, ctx->nz, s))) return r;
+  XInvArgs x{};
+  x.rows = ctx->nz * ctx->ny;
+  x.nx = ctx->nx;
+  x.P = ctx->P;
+  x.sink = SINK_FIELD;
+  x.in = ctx->A;
+  x.in_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
+  x.H = H;
+  x.H_cstride = out_cells(ctx);
+  x.tw = ctx->tw;
+  {
+    Timed t(ctx, KIND_XINV, s);
+    CKL(launch_xinv(ctx->L[0], x, s));
+  }
+  return TM_OK;
+}
+
+int tm_stray_field_adjoint(tm_ctx* ctx, const float* rho, const float* gH, float* dJdrho, void* stream) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!rho || !gH || !dJdrho) return fail(ctx, TM_ERR_ARG, "null array");
+  cudaStream_t s = S(stream);
+  XFwdArgs x{};
+  x.rows = ctx->nz * ctx->ny;
+  x.nx = ctx->nx;
+  x.P = ctx->P;
+  x.src = SRC_VECTOR;
+  x.vec = gH;
+  x.vec_cstride = out_cells(ctx);
+  x.out = ctx->A;
+  x.out_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
+  x.tw = ctx->tw;
+  {
+    Timed t(ctx, KIND_XFWD, s);
+    CKL(launch_xfwd(ctx->L[0], x, s));
+  }
+  if ((r = conv_yz(ctx, ctx->nz, ctx->nzd, s))) return r;
+  return xinv_chain(ctx, rho, dJdrho, s);
+}
+
+int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask, const float* H_target,
+                              const float Ht_const[3], const float w[3], double* J_host, float* dJdrho,
+                              float* H_out, void* stream) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!rho || !mask || !w || !dJdrho) return fail(ctx, TM_ERR_ARG, "null array");
+  if (!H_target && !Ht_const) return fail(ctx, TM_ERR_ARG, "H_target and Ht_const both null");
+  cudaStream_t s = S(stream);
+  if ((r = xfwd_rho(ctx, rho, s))) return r;
+  if ((r = conv_yz(ctx, ctx->nzd, ctx->nz, s))) return r;
+  XInvArgs x{};
+  x.rows = ctx->nz * ctx->ny;
+  x.nx = ctx->nx;
+  x.P = ctx->P;
+  x.sink = SINK_OBJECTIVE;
+  x.in = ctx->A;
+  x.in_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
+  x.H = H_out;
+  x.H_cstride = out_cells(ctx);
+  x.mask = mask;
+  x.Ht = H_target;
+  x.Ht_cstride = out_cells(ctx);
+  for (int c = 0; c < 3; c++) {
+    x.Htc[c] = Ht_const ? Ht_const[c] : 0.0f;
+    x.w[c] = w[c];
+  }
+  x.adj_out = ctx->A;
+  x.Jpart = ctx->Jpart;
+  x.tw = ctx->tw;
+  {
+    Timed t(ctx, KIND_XINV, s);
+    CKL(launch_xinv(ctx->L[0], x, s));
+  }
+  {
+    Timed t(ctx, KIND_OTHER, s);
+    CKL(launch_j_finalize(ctx->Jpart, ctx->nJpart, ctx->Jdev, s));
+  }
+  if ((r = conv_yz(ctx, ctx->nz, ctx->nzd, s))) return r;
+  if ((r = xinv_chain(ctx, rho, dJdrho, s))) return r;
+  if (J_host) {
+    CK(cudaMemcpyAsync(ctx->Jhost, ctx->Jdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *J_host = *ctx->Jhost;
+  }
+  return TM_OK;
+}
+
+int tm_get_objective(tm_ctx* ctx, double* J_host, void* stream) {
+  if (!ctx || !J_host) return fail(ctx, TM_ERR_ARG, "null argument");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemcpyAsync(ctx->Jhost, ctx->Jdev, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  *J_host = *ctx->Jhost;
+  return TM_OK;
+}
+
+int tm_optimize_step(tm_ctx* ctx, float* rho, const float* dJdrho, float alpha, int normalize, void* stream) {
+  if (!ctx) return TM_ERR_ARG;
+  if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
+  if (!rho || !dJdrho) return fail(ctx, TM_ERR_ARG, "null array");
+  if (!isfinite(alpha)) return fail(ctx, TM_ERR_ARG, "alpha not finite");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = S(stream);
+  const long long n = design_cells(ctx);
+  Timed t(ctx, KIND_OTHER, s);
+  if (normalize) {
+    CK(cudaMemsetAsync(ctx->gmax, 0, sizeof(unsigned int), s));
+    CKL(launch_absmax(dJdrho, n, ctx->gmax, s));
+  }
+  CKL(launch_update(rho, dJdrho, n, alpha, normalize, ctx->gmax, s));
+  return TM_OK;
+}
+
+int tm_profile(tm_ctx* ctx, int on) {
+  if (!ctx) return TM_ERR_ARG;
+  ctx->prof_on = on != 0;
+  ctx->ev_used = 0;
+  return TM_OK;
+}
+
+int tm_profile_read(tm_ctx* ctx, double ms[6], int launches[6]) {
+  if (!ctx || !ms || !launches) return fail(ctx, TM_ERR_ARG, "null argument");
+  CK(cudaSetDevice(ctx->device));
+  for (int k = 0; k < KIND_N; k++) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (size_t i = 0; i < ctx->ev_used; i++) {
+    CK(cudaEventSynchronize(ctx->ev[2 * i + 1]));
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, ctx->ev[2 * i], ctx->ev[2 * i + 1]));
+    ms[ctx->ev_kind[i]] += t;
+    launches[ctx->ev_kind[i]] += 1;
+  }
+  return TM_OK;
+}
+
+int tm_debug_tensor_octant(tm_ctx* ctx, double* host_out, void* stream) {
+  if (!ctx || !host_out) return fail(ctx, TM_ERR_ARG, "null argument");
+  if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
+  CK(cudaSetDevice(ctx->device));
+  float* tmp = nullptr;
+  CK(cudaMalloc(&tmp, 6LL * (ctx->L[2] / 2 + 1) * (ctx->L[1] / 2 + 1) * ctx->P * sizeof(float)));
+  int r = tensor_setup(ctx->nx, ctx->ny, ctx->nz, ctx->d, ctx->L[0], ctx->L[1], ctx->L[2], ctx->P, tmp, host_out,
+                       S(stream), ctx->err, sizeof(ctx->err));
+  cudaFree(tmp);
+  return r ? TM_ERR_CUDA : TM_OK;
+}
+
+int tm_debug_tensor_spectrum(tm_ctx* ctx, float* host_out, void* stream) {
+  if (!ctx || !host_out) return fail(ctx, TM_ERR_ARG, "null argument");
+  if (!ctx->have_tensor) return fail(ctx, TM_ERR_STATE, "no tensor: call tm_set_tensor first");
+  CK(cudaSetDevice(ctx->device));
+  const int KX = ctx->L[0] / 2 + 1;
+  const long long rows = 6LL * (ctx->L[2] / 2 + 1) * (ctx->L[1] / 2 + 1);
+  CK(cudaMemcpy2DAsync(host_out, KX * sizeof(float), ctx->T, ctx->P * sizeof(float), KX * sizeof(float), rows,
+                       cudaMemcpyDeviceToHost, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  return TM_OK;
+}
+
+}  // extern "C"
+
+namespace tmk {
+
+int host_pos_of_k(int L, int k) {
+  int pos = 0, span = L, rem = k;
+  for (int s = 0; s < plan_stages(L); s++) {
+    const int R = plan_radix(L, s);
+    span /= R;
+    pos += (rem % R) * span;
+    rem /= R;
+  }
+  return pos;
+}
+
+int host_k_of_pos(int L, int pos) {
+  const int S = plan_stages(L);
+  int d[8];
+  int rem = pos;
+  for (int s = S - 1; s >= 0; s--) {
+    d[s] = rem % plan_radix(L, s);
+    rem /= plan_radix(L, s);
+  }
+  int k = 0, m = 1;
+  for (int s = 0; s < S; s++) {
+    k += d[s] * m;
+    m *= plan_radix(L, s);
+  }
+  return k;
+}
+
+}  // namespace tmk

@@ -1,0 +1,399 @@
+// Shared-memory batched FFT engine for the stray-field convolution (sm_103a).
+//
+// The convolution of Sec. "Discretization" (Eq. (convolution)) is evaluated in
+// Fourier space; only the product N^(k) M^(k) needs the frequency index, so the
+// forward transforms are in-place mixed-radix decimation-in-frequency (natural
+// order in, digit-reversed order out) and the inverse transforms are the exact
+// reverse decimation-in-time (digit-reversed in, natural out). No reordering
+// pass is ever made.
+//
+// A tile holds 16 lines of one length-L transform in shared memory, element
+// (pos, line) at tile[pos * 16 + line]. A half-warp covers the 16 lines of one
+// position, so every 8-byte shared access of a stage touches one 128-byte row:
+// bank-conflict free for any radix pattern. Radices are 32, 16, 8, 4, 2 and 3
+// (in-register DFTs); lengths are L = 2^a 3^b with b <= 2, 8 <= L <= 1024.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tmk {
+
+constexpr int TB = 16;  // lines per tile
+
+template <typename T>
+struct alignas(2 * sizeof(T)) cx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> mk(T a, T b) {
+  cx<T> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ cx<T> scale(cx<T> a, T s) { return mk(a.x * s, a.y * s); }
+// a * w
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> w) {
+  return mk(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+// a * conj(w)
+template <typename T>
+__device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> w) {
+  return mk(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> zero() { return mk<T>(T(0), T(0)); }
+
+// ---------------------------------------------------------------------------
+// Exact values cos(2 pi m / 32), m = 0..8 (the rest follow by symmetry).
+__host__ __device__ constexpr double cos32_q(int m) {
+  return m == 0 ? 1.0
+       : m == 1 ? 0.980785280403230449126
+       : m == 2 ? 0.923879532511286756128
+       : m == 3 ? 0.831469612302545237079
+       : m == 4 ? 0.707106781186547524401
+       : m == 5 ? 0.555570233019602224743
+       : m == 6 ? 0.382683432365089771728
+       : m == 7 ? 0.195090322016128267848
+                : 0.0;
+}
+// cos and sin of 2 pi m / 32 for m in [0, 16)
+__host__ __device__ constexpr double cos32(int m) { return m <= 8 ? cos32_q(m) : -cos32_q(16 - m); }
+__host__ __device__ constexpr double sin32(int m) { return m <= 8 ? cos32_q(8 - m) : cos32_q(m - 8); }
+constexpr double kSqrt3Half = 0.866025403784438646764;
+
+// a * W_32^m with W = exp(-2 pi i / 32) (forward) or its conjugate (inverse); m in [0,16)
+template <typename T, bool INV>
+__device__ __forceinline__ cx<T> tw32(cx<T> a, int m) {
+  if (m == 0) return a;
+  if (m == 8) return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);
+  const T c = T(cos32(m)), s = T(sin32(m));
+  if (!INV) return mk(a.x * c + a.y * s, a.y * c - a.x * s);
+  return mk(a.x * c - a.y * s, a.y * c + a.x * s);
+}
+
+// In-register DFT of size N (natural order in and out). Forward uses
+// exp(-2 pi i jk / N), inverse exp(+2 pi i jk / N), both unnormalised.
+template <typename T, int N, bool INV>
+struct Dft {
+  static __device__ __forceinline__ void run(cx<T>* v) {
+    static_assert(N == 2 || N == 4 || N == 8 || N == 16 || N == 32, "radix");
+    cx<T> e[N / 2], o[N / 2];
+#pragma unroll
+    for (int i = 0; i < N / 2; i++) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    Dft<T, N / 2, INV>::run(e);
+    Dft<T, N / 2, INV>::run(o);
+#pragma unroll
+    for (int k = 0; k < N / 2; k++) {
+      cx<T> t = tw32<T, INV>(o[k], k * (32 / N));
+      v[k] = e[k] + t;
+      v[k + N / 2] = e[k] - t;
+    }
+  }
+};
+template <typename T, bool INV>
+struct Dft<T, 1, INV> {
+  static __device__ __forceinline__ void run(cx<T>*) {}
+};
+template <typename T, bool INV>
+struct Dft<T, 3, INV> {
+  static __device__ __forceinline__ void run(cx<T>* v) {
+    cx<T> t = v[1] + v[2], d = v[1] - v[2];
+    cx<T> m = v[0] - scale(t, T(0.5));
+    cx<T> s = scale(d, T(kSqrt3Half));
+    v[0] = v[0] + t;
+    if (!INV) {
+      v[1] = mk(m.x + s.y, m.y - s.x);
+      v[2] = mk(m.x - s.y, m.y + s.x);
+    } else {
+      v[1] = mk(m.x - s.y, m.y + s.x);
+      v[2] = mk(m.x + s.y, m.y - s.x);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Plans: L = 2^a 3^b. The power-of-two part is one stage (when b > 0 and
+// a <= 5) or two near-equal stages; then b radix-3 stages. Every plan has at
+// least two stages.
+__host__ __device__ constexpr int exp2_of(int L) {
+  int a = 0;
+  while (L > 1 && L % 2 == 0) { L /= 2; a++; }
+  return a;
+}
+__host__ __device__ constexpr int exp3_of(int L) {
+  int b = 0;
+  while (L > 1 && L % 3 == 0) { L /= 3; b++; }
+  return b;
+}
+__host__ __device__ constexpr bool two_pow2_stages(int L) { return exp3_of(L) == 0 || exp2_of(L) > 5; }
+__host__ __device__ constexpr int plan_stages(int L) {
+  return (two_pow2_stages(L) ? 2 : (exp2_of(L) > 0 ? 1 : 0)) + exp3_of(L);
+}
+__host__ __device__ constexpr int plan_radix(int L, int s) {
+  if (two_pow2_stages(L)) {
+    const int a = exp2_of(L), a1 = (a + 1) / 2, a2 = a - a1;
+    if (s == 0) return 1 << a1;
+    if (s == 1) return 1 << a2;
+    return 3;
+  }
+  if (s == 0) return 1 << exp2_of(L);
+  return 3;
+}
+// G_s = L / (R_0 ... R_{s-1}): size of the sub-transforms stage s works on
+__host__ __device__ constexpr int plan_span(int L, int s) {
+  int G = L;
+  for (int t = 0; t < s; t++) G /= plan_radix(L, t);
+  return G;
+}
+__host__ __device__ constexpr bool supported_length(int L) {
+  if (L < 8 || L > 1024 || L % 2 != 0) return false;
+  int r = L;
+  while (r % 2 == 0) r /= 2;
+  while (r % 3 == 0) r /= 3;
+  return r == 1 && exp3_of(L) <= 2;
+}
+
+// Position (after the forward DIF) of frequency k, and its inverse.
+template <int L>
+__device__ __forceinline__ int pos_of_k(int k) {
+  int pos = 0, span = L, rem = k;
+#pragma unroll
+  for (int s = 0; s < plan_stages(L); s++) {
+    const int R = plan_radix(L, s);
+    span /= R;
+    pos += (rem % R) * span;
+    rem /= R;
+  }
+  return pos;
+}
+template <int L>
+__device__ __forceinline__ int k_of_pos(int pos) {
+  constexpr int S = plan_stages(L);
+  int d[S > 0 ? S : 1];
+  int rem = pos;
+#pragma unroll
+  for (int s = S - 1; s >= 0; s--) {
+    const int R = plan_radix(L, s);
+    d[s] = rem % R;
+    rem /= R;
+  }
+  int k = 0, m = 1;
+#pragma unroll
+  for (int s = 0; s < S; s++) {
+    k += d[s] * m;
+    m *= plan_radix(L, s);
+  }
+  return k;
+}
+
+// ---------------------------------------------------------------------------
+// Stage kernels on a tile. Unit u of stage s: line = u % 16, t = u / 16,
+// group g = t / M, j = t % M; it owns positions g*G + j + q*M, q < R.
+template <int L, int s>
+struct StageShape {
+  static constexpr int R = plan_radix(L, s);
+  static constexpr int G = plan_span(L, s);
+  static constexpr int M = G / R;
+  static constexpr int NU = (L / R) * TB;  // units per stage
+};
+
+// twiddle for DIF output q / DIT input q of unit (j): W_G^{jq} = tw[j q L/G]
+template <typename T, int L, int s, bool INV>
+__device__ __forceinline__ void apply_twiddles(cx<T>* v, int j, const cx<T>* tw) {
+  using S = StageShape<L, s>;
+  if (S::M == 1) return;
+  if (j == 0) return;
+#pragma unroll
+  for (int q = 1; q < S::R; q++) {
+    const cx<T> w = tw[(j * q) * (L / S::G)];
+    v[q] = INV ? cmulc(v[q], w) : cmul(v[q], w);
+  }
+}
+
+// One forward DIF stage in place on the tile.
+template <typename T, int L, int s, int NT>
+__device__ __forceinline__ void dif_stage(cx<T>* tile, const cx<T>* tw) {
+  using S = StageShape<L, s>;
+  constexpr int ITER = (S::NU + NT - 1) / NT;
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * NT + threadIdx.x;
+    if (S::NU % NT == 0 || u < S::NU) {
+      const int line = u % TB, t = u / TB, g = t / S::M, j = t % S::M;
+      const int base = g * S::G + j;
+      cx<T> v[S::R];
+#pragma unroll
+      for (int q = 0; q < S::R; q++) v[q] = tile[(base + q * S::M) * TB + line];
+      Dft<T, S::R, false>::run(v);
+      apply_twiddles<T, L, s, false>(v, j, tw);
+#pragma unroll
+      for (int q = 0; q < S::R; q++) tile[(base + q * S::M) * TB + line] = v[q];
+    }
+  }
+}
+
+// One inverse DIT stage in place on the tile.
+template <typename T, int L, int s, int NT>
+__device__ __forceinline__ void dit_stage(cx<T>* tile, const cx<T>* tw) {
+  using S = StageShape<L, s>;
+  constexpr int ITER = (S::NU + NT - 1) / NT;
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * NT + threadIdx.x;
+    if (S::NU % NT == 0 || u < S::NU) {
+      const int line = u % TB, t = u / TB, g = t / S::M, j = t % S::M;
+      const int base = g * S::G + j;
+      cx<T> v[S::R];
+#pragma unroll
+      for (int q = 0; q < S::R; q++) v[q] = tile[(base + q * S::M) * TB + line];
+      apply_twiddles<T, L, s, true>(v, j, tw);
+      Dft<T, S::R, true>::run(v);
+#pragma unroll
+      for (int q = 0; q < S::R; q++) tile[(base + q * S::M) * TB + line] = v[q];
+    }
+  }
+}
+
+// Stage 0 forward, reading its inputs through ld(pos, line) (zero beyond the
+// valid range is the loader's job) and writing the tile. All loads of a thread
+// are issued before any arithmetic.
+template <typename T, int L, int NT, typename LD>
+__device__ __forceinline__ void dif_stage0_load(cx<T>* tile, const cx<T>* tw, LD ld) {
+  using S = StageShape<L, 0>;
+  constexpr int ITER = (S::NU + NT - 1) / NT;
+  cx<T> v[ITER][S::R];
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * NT + threadIdx.x;
+    if (S::NU % NT == 0 || u < S::NU) {
+      const int line = u % TB, j = u / TB;
+#pragma unroll
+      for (int q = 0; q < S::R; q++) v[it][q] = ld(j + q * S::M, line);
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * NT + threadIdx.x;
+    if (S::NU % NT == 0 || u < S::NU) {
+      const int line = u % TB, j = u / TB;
+      Dft<T, S::R, false>::run(v[it]);
+      apply_twiddles<T, L, 0, false>(v[it], j, tw);
+#pragma unroll
+      for (int q = 0; q < S::R; q++) tile[(j + q * S::M) * TB + line] = v[it][q];
+    }
+  }
+}
+
+// Last forward stage (M = 1), writing its outputs through st(pos, line, v).
+template <typename T, int L, int NT, typename ST>
+__device__ __forceinline__ void dif_last_store(const cx<T>* tile, ST st) {
+  constexpr int s = plan_stages(L) - 1;
+  using S = StageShape<L, s>;
+  static_assert(S::M == 1, "last stage");
+  constexpr int ITER = (S::NU + NT - 1) / NT;
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * NT + threadIdx.x;
+    if (S::NU % NT == 0 || u < S::NU) {
+      const int line = u % TB, g = u / TB;
+      cx<T> v[S::R];
+#pragma unroll
+      for (int q = 0; q < S::R; q++) v[q] = tile[(g * S::R + q) * TB + line];
+      Dft<T, S::R, false>::run(v);
+#pragma unroll
+      for (int q = 0; q < S::R; q++) st(g * S::R + q, line, v[q]);
+    }
+  }
+}
+
+// First inverse stage (the last plan stage, M = 1) reading ld(pos, line).
+template <typename T, int L, int NT, typename LD>
+__device__ __forceinline__ void dit_last_load(cx<T>* tile, LD ld) {
+  constexpr int s = plan_stages(L) - 1;
+  using S = StageShape<L, s>;
+  static_assert(S::M == 1, "last stage");
+  constexpr int ITER = (S::NU + NT - 1) / NT;
+  cx<T> v[ITER][S::R];
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * NT + threadIdx.x;
+    if (S::NU % NT == 0 || u < S::NU) {
+      const int line = u % TB, g = u / TB;
+#pragma unroll
+      for (int q = 0; q < S::R; q++) v[it][q] = ld(g * S::R + q, line);
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * NT + threadIdx.x;
+    if (S::NU % NT == 0 || u < S::NU) {
+      const int line = u % TB, g = u / TB;
+      Dft<T, S::R, true>::run(v[it]);
+#pragma unroll
+      for (int q = 0; q < S::R; q++) tile[(g * S::R + q) * TB + line] = v[it][q];
+    }
+  }
+}
+
+// Last inverse stage (plan stage 0), natural-order outputs through st(pos, line, v).
+template <typename T, int L, int NT, typename ST>
+__device__ __forceinline__ void dit_stage0_store(const cx<T>* tile, const cx<T>* tw, ST st) {
+  using S = StageShape<L, 0>;
+  constexpr int ITER = (S::NU + NT - 1) / NT;
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * NT + threadIdx.x;
+    if (S::NU % NT == 0 || u < S::NU) {
+      const int line = u % TB, j = u / TB;
+      cx<T> v[S::R];
+#pragma unroll
+      for (int q = 0; q < S::R; q++) v[q] = tile[(j + q * S::M) * TB + line];
+      apply_twiddles<T, L, 0, true>(v, j, tw);
+      Dft<T, S::R, true>::run(v);
+#pragma unroll
+      for (int q = 0; q < S::R; q++) st(j + q * S::M, line, v[q]);
+    }
+  }
+}
+
+// Helpers running stage ranges with a block barrier after each stage.
+template <typename T, int L, int NT, int s, int e>
+struct DifRange {
+  static __device__ __forceinline__ void run(cx<T>* tile, const cx<T>* tw) {
+    if constexpr (s < e) {
+      dif_stage<T, L, s, NT>(tile, tw);
+      __syncthreads();
+      DifRange<T, L, NT, s + 1, e>::run(tile, tw);
+    }
+  }
+};
+// inverse stages s = hi-1 down to lo
+template <typename T, int L, int NT, int lo, int hi>
+struct DitRange {
+  static __device__ __forceinline__ void run(cx<T>* tile, const cx<T>* tw) {
+    if constexpr (hi > lo) {
+      dit_stage<T, L, hi - 1, NT>(tile, tw);
+      __syncthreads();
+      DitRange<T, L, NT, lo, hi - 1>::run(tile, tw);
+    }
+  }
+};
+
+// Cooperative copy of the length-L twiddle table W_L^m into shared memory.
+template <typename T, int NT>
+__device__ __forceinline__ void load_twiddles(cx<T>* dst, const cx<T>* src, int L) {
+  for (int i = threadIdx.x; i < L; i += NT) dst[i] = src[i];
+}
+
+}  // namespace tmk

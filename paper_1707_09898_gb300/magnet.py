@@ -1,0 +1,197 @@
+"""Python face of libtopomag: a context object and torch.autograd Functions.
+
+Every step of the computation runs in the CUDA library; this module only
+marshals device pointers, sizes and the current torch stream.
+
+Method: Abert et al., "A fast finite-difference algorithm for topology
+optimization of permanent magnets" (arXiv:1707.09898): M = rho^p M0
+(Sec. "Methodology", Eq. 2), H = D[M] by the FFT-accelerated convolution with
+the demagnetization tensor (Sec. "Discretization", Eqs. (convolution) and
+(demag_tensor)), objective J(H(rho), rho) (Eq. (objective_function)) and its
+adjoint gradient (Eqs. (adjoint1)-(adjoint2)).
+"""
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+F32, U8 = torch.float32, torch.uint8
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Magnet:
+    """One grid: output box n_out = (nx, ny, nz), design slab z < nzd, cell size in metres."""
+
+    def __init__(self, n_out, nzd, cellsize=(1e-3, 1e-3, 1e-3), M0=(0.0, 0.0, 1.0 / (4e-7 * 3.141592653589793)),
+                 p=3.0, device=0, tensor=True):
+        self.L = _lib.lib()
+        self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
+        h = ctypes.c_void_p()
+        _lib.check(None, self.L.tm_create(ctypes.byref(h), self.device.index or 0))
+        self.h = h
+        self.n_out = tuple(int(v) for v in n_out)
+        self.nzd = int(nzd)
+        self.cellsize = tuple(float(v) for v in cellsize)
+        self._ck(self.L.tm_set_grid(self.h, _lib.c_int3(*self.n_out), self.nzd, _lib.c_double3(*self.cellsize)))
+        self._ck(self.L.tm_set_penalty(self.h, float(p)))
+        self.p = float(p)
+        self.set_M0(M0)
+        if tensor:
+            self.set_tensor()
+
+    # -- plumbing ------------------------------------------------------------
+    def _ck(self, code):
+        _lib.check(self.h, code)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.tm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def design_shape(self):
+        return (self.nzd, self.n_out[1], self.n_out[0])
+
+    @property
+    def out_shape(self):
+        return (self.n_out[2], self.n_out[1], self.n_out[0])
+
+    def fft_lengths(self):
+        L = _lib.c_int3()
+        self._ck(self.L.tm_get_fft_lengths(self.h, L))
+        return tuple(L)
+
+    def _dev(self, t, dtype, shape, name):
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != dtype:
+            raise TypeError(f"{name} must be a {dtype} tensor on {self.device}")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+        return t.contiguous()
+
+    # -- setup ---------------------------------------------------------------
+    def set_M0(self, M0):
+        """Constant M0 (3 numbers, A/m) or a varying field (3, nzd, ny, nx) float32 on the device."""
+        if isinstance(M0, torch.Tensor) and M0.dim() == 4:
+            m = self._dev(M0, F32, (3,) + self.design_shape, "M0")
+            self._ck(self.L.tm_set_M0(self.h, _ptr(m), _lib.c_double3(0.0, 0.0, 0.0), _stream(self.device)))
+            self.M0 = m
+        else:
+            v = [float(x) for x in (M0.tolist() if isinstance(M0, torch.Tensor) else M0)]
+            self._ck(self.L.tm_set_M0(self.h, None, _lib.c_double3(*v), _stream(self.device)))
+            self.M0 = tuple(v)
+
+    def set_tensor(self):
+        self._ck(self.L.tm_set_tensor(self.h, _stream(self.device)))
+
+    # -- operators -----------------------------------------------------------
+    def stray_field(self, rho, out=None):
+        rho = self._dev(rho, F32, self.design_shape, "rho")
+        H = torch.empty((3,) + self.out_shape, dtype=F32, device=self.device) if out is None else out
+        self._ck(self.L.tm_stray_field(self.h, _ptr(rho), _ptr(H), _stream(self.device)))
+        return H
+
+    def stray_field_adjoint(self, rho, gH, out=None):
+        rho = self._dev(rho, F32, self.design_shape, "rho")
+        gH = self._dev(gH, F32, (3,) + self.out_shape, "gH")
+        G = torch.empty(self.design_shape, dtype=F32, device=self.device) if out is None else out
+        self._ck(self.L.tm_stray_field_adjoint(self.h, _ptr(rho), _ptr(gH), _ptr(G), _stream(self.device)))
+        return G
+
+    def objective_and_gradient(self, rho, mask, Ht=None, Ht_const=(0.0, 0.0, 0.0), w=(0.0, 0.0, 1.0), G=None,
+                               H_out=None, sync=True):
+        """(J, dJ/drho) of J = sum_mask sum_c w_c (H_c - Ht_c)^2. J is a float if sync else None."""
+        rho = self._dev(rho, F32, self.design_shape, "rho")
+        mask = self._dev(mask, U8, self.out_shape, "mask")
+        if Ht is not None:
+            Ht = self._dev(Ht, F32, (3,) + self.out_shape, "Ht")
+        if G is None:
+            G = torch.empty(self.design_shape, dtype=F32, device=self.device)
+        J = ctypes.c_double(0.0)
+        self._ck(self.L.tm_objective_and_gradient(
+            self.h, _ptr(rho), _ptr(mask), _ptr(Ht), _lib.c_float3(*[float(v) for v in Ht_const]),
+            _lib.c_float3(*[float(v) for v in w]), ctypes.byref(J) if sync else None, _ptr(G), _ptr(H_out),
+            _stream(self.device)))
+        return (J.value if sync else None), G
+
+    def objective(self):
+        J = ctypes.c_double(0.0)
+        self._ck(self.L.tm_get_objective(self.h, ctypes.byref(J), _stream(self.device)))
+        return J.value
+
+    def optimize_step(self, rho, G, alpha, normalize=True):
+        self._ck(self.L.tm_optimize_step(self.h, _ptr(rho), _ptr(G), float(alpha), int(bool(normalize)),
+                                         _stream(self.device)))
+        return rho
+
+    # -- per-kernel event timing ---------------------------------------------
+    KINDS = ("x_forward", "y_forward", "z_pass", "y_inverse", "x_inverse", "other")
+
+    def profile(self, on=True):
+        self._ck(self.L.tm_profile(self.h, int(bool(on))))
+
+    def profile_read(self):
+        """{kind: (total ms, launches)} over the launches recorded since profile(True)."""
+        ms = (ctypes.c_double * 6)()
+        n = (ctypes.c_int * 6)()
+        self._ck(self.L.tm_profile_read(self.h, ms, n))
+        return {k: (ms[i], n[i]) for i, k in enumerate(self.KINDS)}
+
+    # -- inspection (tests) --------------------------------------------------
+    def tensor_octant(self):
+        import numpy as np
+        nx, ny, nz = self.n_out
+        out = np.empty((6, nz, ny, nx), dtype=np.float64)
+        self._ck(self.L.tm_debug_tensor_octant(self.h, ctypes.c_void_p(out.ctypes.data), _stream(self.device)))
+        return out
+
+    def tensor_spectrum(self):
+        import numpy as np
+        Lx, Ly, Lz = self.fft_lengths()
+        out = np.empty((6, Lz // 2 + 1, Ly // 2 + 1, Lx // 2 + 1), dtype=np.float32)
+        self._ck(self.L.tm_debug_tensor_spectrum(self.h, ctypes.c_void_p(out.ctypes.data), _stream(self.device)))
+        return out
+
+
+class StrayField(torch.autograd.Function):
+    """H = D[rho^p M0]; backward: dL/drho = p rho^(p-1) M0 . D(dL/dH) (hand-written adjoint kernels)."""
+
+    @staticmethod
+    def forward(ctx, rho, magnet):
+        ctx.magnet = magnet
+        ctx.save_for_backward(rho)
+        return magnet.stray_field(rho.detach())
+
+    @staticmethod
+    def backward(ctx, gH):
+        (rho,) = ctx.saved_tensors
+        return ctx.magnet.stray_field_adjoint(rho.detach(), gH.contiguous()), None
+
+
+class TopoObjective(torch.autograd.Function):
+    """J(rho) = sum_mask sum_c w_c (H_c - Ht_c)^2 with its fused adjoint gradient."""
+
+    @staticmethod
+    def forward(ctx, rho, magnet, mask, Ht=None, Ht_const=(0.0, 0.0, 0.0), w=(0.0, 0.0, 1.0)):
+        J, G = magnet.objective_and_gradient(rho.detach(), mask, Ht, Ht_const, w)
+        ctx.save_for_backward(G)
+        return torch.tensor(J, dtype=torch.float64, device=rho.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (G,) = ctx.saved_tensors
+        return (gJ.to(G.dtype) * G), None, None, None, None, None
