@@ -130,6 +130,30 @@ int tm_get_objective(tm_ctx* ctx, double* J_host, void* stream);
 int tm_optimize_step(tm_ctx* ctx, float* rho, const float* dJdrho, float alpha, int normalize, void* stream);
 
 /*
+ * Allocation-free projected-gradient step (no context needed). For callers that
+ * must not allocate device memory when they call in: code running under a
+ * framework whose caching allocator has reserved the device memory (a fresh
+ * cudaMalloc may then fail), and time-critical loops that cannot absorb the
+ * device-wide synchronisation that cudaMalloc/cudaFree imply. The paper has no
+ * counterpart; this is an interface convenience around the update of
+ * tm_optimize_step and gives the same result.
+ *   rho [n] updated in place, dJdrho [n]: device pointers on the CURRENT device.
+ *   normalize != 0: rho <- clip(rho - alpha G / max|G|, 0, 1) (no change when
+ *   max|G| = 0); else rho <- clip(rho - alpha G, 0, 1).
+ * Scratch: a 64 KiB static device array in the library (held by every GPU that
+ * loads it until the process exits) stores the max|G| reduction, so at most
+ * n = 33,554,432 elements per call; larger n returns TM_ERR_SIZE without
+ * launching anything. Every call reuses that one array: calls that overlap on
+ * the GPU (other streams, other host threads) race and must be serialised by
+ * the caller. The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) once; make that first call before any stream
+ * capture. Returns TM_OK, TM_ERR_ARG, TM_ERR_SIZE or TM_ERR_CUDA; there is no
+ * context, so no message is kept for tm_last_error.
+ */
+int tm_optimize_step_noalloc(float* rho, const float* dJdrho, long long n, float alpha, int normalize,
+                             void* stream);
+
+/*
  * Per-kernel timing. tm_profile(ctx, 1) starts recording a CUDA event pair on
  * the launch stream around every kernel the context launches (and resets the
  * record); tm_profile(ctx, 0) stops. tm_profile_read synchronises on the

@@ -3,6 +3,9 @@
 // (box constraint 0 <= rho <= 1 of Sec. "Methodology", after Eq. 1).
 #include <stdint.h>
 
+#include <mutex>
+
+#include "../../include/topomag.h"
 #include "internal.h"
 
 namespace tmk {
@@ -64,6 +67,47 @@ int grid_for(long long n, int per) {
   return (int)b;
 }
 
+// ---------------------------------------------------------------------------
+// Scratch of tm_optimize_step_noalloc, a file-scope device array instead of an
+// allocation: slot 0 receives max|G|, slots 1..nb the maxima of the nb slices
+// of kNoallocSlice elements. Every call overwrites the slots it reads.
+constexpr int kNoallocSlice = 2048;
+constexpr int kNoallocMaxSlices = 16384;
+static __device__ __align__(256) float g_noalloc_scratch[1 + kNoallocMaxSlices];
+
+__global__ void k_slice_absmax(const float* G, long long n, float* scratch) {
+  __shared__ float red[8];
+  const long long base = (long long)blockIdx.x * kNoallocSlice;
+  float m = 0.0f;
+  for (int i = threadIdx.x; i < kNoallocSlice; i += blockDim.x) {
+    const long long k = base + i;
+    if (k < n) m = fmaxf(m, fabsf(G[k]));
+  }
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, red[w]);
+    scratch[1 + blockIdx.x] = m;
+  }
+}
+
+__global__ void k_reduce_slices(float* scratch, int nb) {
+  __shared__ float red[8];
+  float m = 0.0f;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) m = fmaxf(m, scratch[1 + i]);
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, red[w]);
+    scratch[0] = m;
+  }
+}
+
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[256] = {nullptr};  // device address of g_noalloc_scratch, per device ordinal
+
 }  // namespace
 
 int launch_j_finalize(const double* part, int n, double* J, cudaStream_t s) {
@@ -81,3 +125,40 @@ int launch_update(float* rho, const float* G, long long n, float alpha, int norm
 }
 
 }  // namespace tmk
+
+// A context-free projected-gradient step for callers that may not allocate
+// device memory. See include/topomag.h. The paper has no counterpart: this is
+// an interface convenience, not part of the method.
+extern "C" int tm_optimize_step_noalloc(float* rho, const float* dJdrho, long long n, float alpha, int normalize,
+                                        void* stream) {
+  using namespace tmk;
+  if (!rho || !dJdrho || n < 0 || !isfinite(alpha)) return TM_ERR_ARG;
+  if (n > (long long)kNoallocSlice * kNoallocMaxSlices) return TM_ERR_SIZE;
+  if (n == 0) return TM_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return TM_ERR_CUDA;
+  float* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      // once per device, with that device current: the host-side name of the
+      // array is not a device address; ask the runtime for the real one
+      if (cudaGetSymbolAddress(reinterpret_cast<void**>(&g_noalloc_ptr[dev]), g_noalloc_scratch) != cudaSuccess) {
+        g_noalloc_ptr[dev] = nullptr;
+        return TM_ERR_CUDA;
+      }
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  if (normalize) {
+    const int nb = (int)((n + kNoallocSlice - 1) / kNoallocSlice);
+    k_slice_absmax<<<nb, 256, 0, s>>>(dJdrho, n, scratch);
+    k_reduce_slices<<<1, 256, 0, s>>>(scratch, nb);
+    if (cudaPeekAtLastError() != cudaSuccess) return TM_ERR_CUDA;
+  }
+  // the update kernel of tm_optimize_step reads max|G| as float bits from slot 0
+  if (launch_update(rho, dJdrho, n, alpha, normalize, reinterpret_cast<const unsigned int*>(scratch), s) != 0)
+    return TM_ERR_CUDA;
+  return TM_OK;
+}
