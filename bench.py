@@ -142,26 +142,50 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def _need(v, u):
+    """unique tensor components with a nonzero coefficient in v^T N u"""
+    c = [v[0] * u[0], v[1] * u[1], v[2] * u[2], v[0] * u[1] + v[1] * u[0], v[0] * u[2] + v[2] * u[0],
+         v[1] * u[2] + v[2] * u[1]]
+    return sum(1 for x in c if x != 0)
+
+
 def alg_bytes(wl, L):
-    """Algorithmic bytes per launch of each kernel kind (half spectra kx = 0..L/2, no padding)."""
+    """Algorithmic bytes per launch of each kernel kind for the objective+gradient step.
+
+    Half spectra kx = 0..L/2 only (no padding); components actually carried: with a
+    constant M0 the magnetization enters as one spectrum (rho^p, contracted with M0 in
+    the z pass) and the adjoint leaves as one (contracted with M0); the forward carries
+    the weighted field components, the adjoint their dJ/dH.
+    """
     nx, ny, nz = wl.n_out
     nzd = wl.nzd
     Lx, Ly, Lz = L
     K = Lx // 2 + 1
-    c8 = 3 * 8
-    T = 6 * (Lz // 2 + 1) * (Ly // 2 + 1) * K * 4
-    # forward (zin = nzd, zout = nz) and adjoint (zin = nz, zout = nzd) launches alternate; average them
-    def yz(zin, zout):
+    const = wl.m0_kind == "const"
+    W = [c for c in range(3) if wl.w[c] != 0]
+    M0 = list(wl.M0_const()) if const else None
+    e = [[1, 0, 0], [0, 1, 0], [0, 0, 1]]
+    fin, fout = (1, len(W)) if const else (3, 3)
+    ain, aout = (len(W), 1) if const else (3, 3)
+    Tcomp = (Lz // 2 + 1) * (Ly // 2 + 1) * K * 4
+    if const:
+        tf = len({i for c in W for i in range(6) if _need(e[c], M0)}) if W else 0
+        tf = sum(_need(e[c], M0) for c in W)
+        ta = sum(_need(M0, e[c]) for c in W)
+    else:
+        tf = ta = 6
+    s8 = 8
+    def yz(nin, nout, zin, zout, tcomp):
         return {
-            "y_forward": c8 * zin * K * (ny + Ly),
-            "z_pass": c8 * K * Ly * (zin + zout) + T,
-            "y_inverse": c8 * zout * K * (Ly + ny),
+            "y_forward": s8 * nin * zin * K * (ny + Ly),
+            "z_pass": s8 * K * Ly * (nin * zin + nout * zout) + tcomp * Tcomp,
+            "y_inverse": s8 * nout * zout * K * (Ly + ny),
         }
-    f, a = yz(nzd, nz), yz(nz, nzd)
+    f, a = yz(fin, fout, nzd, nz, tf), yz(ain, aout, nz, nzd, ta)
     out = {k: (f[k] + a[k]) / 2 for k in f}
-    out["x_forward"] = 4 * nzd * ny * nx + c8 * nzd * ny * K
-    obj = c8 * nz * ny * K * 2 + nz * ny * nx  # spectra in, adjoint spectra out, mask
-    chain = c8 * nzd * ny * K + 8 * nzd * ny * nx
+    out["x_forward"] = 4 * nzd * ny * nx + s8 * fin * nzd * ny * K
+    obj = s8 * nz * ny * K * fout * 2 + nz * ny * nx  # spectra in, adjoint spectra out, mask
+    chain = s8 * aout * nzd * ny * K + 8 * nzd * ny * nx
     out["x_inverse"] = (obj + chain) / 2
     return out
 

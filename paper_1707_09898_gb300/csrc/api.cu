@@ -27,7 +27,7 @@ struct tm_ctx {
   float* M0v = nullptr;     // [3][nzd][ny][nx]
   float* T = nullptr;       // [6][Lz/2+1][Ly/2+1][P]
   float2* A = nullptr;      // [3][nz][ny][P]
-  float2* B = nullptr;      // [3][nz][Ly][P]
+  float2* B = nullptr;      // [4][nz][Ly][P]
   float2* tw = nullptr;     // twiddles: Lx | Ly | Lz
   int2* zcol = nullptr;     // [Ly]
   double* Jpart = nullptr;  // [ceil(nz*ny/rows_per_block)]
@@ -143,10 +143,31 @@ int check_ready(tm_ctx* ctx) {
   return TM_OK;
 }
 
-// Common middle: forward y, z (tensor), inverse y on A/B. Input planes zin, output planes zout.
-int conv_yz(tm_ctx* ctx, int zin, int zout, cudaStream_t s) {
+// coefficients of s = v^T N u over the unique components (xx, yy, zz, xy, xz, yz)
+void coef6(float c[6], const double v[3], const double u[3]) {
+  c[0] = (float)(v[0] * u[0]);
+  c[1] = (float)(v[1] * u[1]);
+  c[2] = (float)(v[2] * u[2]);
+  c[3] = (float)(v[0] * u[1] + v[1] * u[0]);
+  c[4] = (float)(v[0] * u[2] + v[2] * u[0]);
+  c[5] = (float)(v[1] * u[2] + v[2] * u[1]);
+}
+const double kUnit[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+// One application of the y / z / y passes. Inputs: nin spectra in A slots ain[]
+// (zin planes); outputs: nout spectra in A slots aout[] (zout planes) with
+// out_o = sum_i (v_o^T N u_i) in_i. B slots: inputs go to bin[], outputs to bout[].
+struct ConvSpec {
+  int nin, nout;
+  int ain[3], bin[3], bout[3], aout[3];
+  const double* u[3];  // per input
+  const double* v[3];  // per output
+};
+
+int conv_yz(tm_ctx* ctx, const ConvSpec& cs, int zin, int zout, cudaStream_t s) {
   const int Lx = ctx->L[0], Ly = ctx->L[1], Lz = ctx->L[2];
   const long long P = ctx->P;
+  const long long A_cs = (long long)ctx->nz * ctx->ny * P, B_cs = (long long)ctx->nz * Ly * P;
   YArgs y{};
   y.in = ctx->A;
   y.out = ctx->B;
@@ -158,22 +179,38 @@ int conv_yz(tm_ctx* ctx, int zin, int zout, cudaStream_t s) {
   y.out_pstride = P;
   y.in_zstride = (long long)ctx->ny * P;
   y.out_zstride = (long long)Ly * P;
-  y.in_cstride = (long long)ctx->nz * ctx->ny * P;
-  y.out_cstride = (long long)ctx->nz * Ly * P;
+  y.in_cstride = A_cs;
+  y.out_cstride = B_cs;
+  for (int i = 0; i < cs.nin; i++) {
+    y.in_slot[i] = cs.ain[i];
+    y.out_slot[i] = cs.bin[i];
+  }
   y.tw = ctx->tw + Lx;
   {
     Timed t(ctx, KIND_YFWD, s);
-    CKL(launch_yfwd(Ly, y, s));
+    CKL(launch_yfwd(Ly, y, cs.nin, s));
   }
 
   ZArgs z{};
   z.buf = ctx->B;
-  z.cstride = (long long)ctx->nz * Ly * P;
+  z.cstride = B_cs;
   z.zstride = (long long)Ly * P;
   z.n_in = zin;
   z.n_out = zout;
   z.Ly = Ly;
   z.P = ctx->P;
+  z.nin = cs.nin;
+  z.nout = cs.nout;
+  for (int i = 0; i < cs.nin; i++) z.in_slot[i] = cs.bin[i];
+  for (int o = 0; o < cs.nout; o++) {
+    z.out_slot[o] = cs.bout[o];
+    z.need[o] = 0;
+    for (int i = 0; i < cs.nin; i++) {
+      coef6(z.coef[o][i], cs.v[o], cs.u[i]);
+      for (int c = 0; c < 6; c++)
+        if (z.coef[o][i][c] != 0.0f) z.need[o] |= 1 << c;
+    }
+  }
   z.T = ctx->T;
   z.Tz = (long long)(Ly / 2 + 1) * P;
   z.Tc = (long long)(Lz / 2 + 1) * z.Tz;
@@ -195,52 +232,64 @@ int conv_yz(tm_ctx* ctx, int zin, int zout, cudaStream_t s) {
   yi.out_pstride = P;
   yi.in_zstride = (long long)Ly * P;
   yi.out_zstride = (long long)ctx->ny * P;
-  yi.in_cstride = (long long)ctx->nz * Ly * P;
-  yi.out_cstride = (long long)ctx->nz * ctx->ny * P;
+  yi.in_cstride = B_cs;
+  yi.out_cstride = A_cs;
+  for (int o = 0; o < cs.nout; o++) {
+    yi.in_slot[o] = cs.bout[o];
+    yi.out_slot[o] = cs.aout[o];
+  }
   yi.tw = ctx->tw + Lx;
   {
     Timed t(ctx, KIND_YINV, s);
-    CKL(launch_yinv(Ly, yi, s));
+    CKL(launch_yinv(Ly, yi, cs.nout, s));
   }
   return TM_OK;
 }
 
-void fill_m0(const tm_ctx* ctx, float* M0c, const float** M0v, long long* cs) {
-  for (int c = 0; c < 3; c++) M0c[c] = (float)ctx->M0c[c];
-  *M0v = ctx->m0_var ? ctx->M0v : nullptr;
-  *cs = design_cells(ctx);
-}
-
-// forward x pass from rho (design rows) into A
-int xfwd_rho(tm_ctx* ctx, const float* rho, cudaStream_t s) {
+// forward x pass of the magnetization: rho^p (constant M0, contracted later) -> A slot 0,
+// or rho^p M0_c (varying M0) -> A slots 0, 1, 2. Returns the number of slots written.
+int xfwd_rho(tm_ctx* ctx, const float* rho, cudaStream_t s, int* nslots) {
   XFwdArgs x{};
   x.rows = ctx->nzd * ctx->ny;
   x.nx = ctx->nx;
   x.P = ctx->P;
-  x.src = ctx->m0_var ? SRC_RHO_FIELD : SRC_RHO_CONST;
+  x.src = ctx->m0_var ? SRC_RHO_M0 : SRC_RHO_POW;
   x.rho = rho;
-  fill_m0(ctx, x.M0c, &x.M0v, &x.M0v_cstride);
   x.p = (float)ctx->p;
+  x.M0v = ctx->M0v;
+  x.M0v_cstride = design_cells(ctx);
+  for (int c = 0; c < 3; c++) {
+    x.comp[c] = c;
+    x.out_slot[c] = c;
+  }
   x.out = ctx->A;
   x.out_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
   x.tw = ctx->tw;
+  *nslots = ctx->m0_var ? 3 : 1;
   Timed t(ctx, KIND_XFWD, s);
-  CKL(launch_xfwd(ctx->L[0], x, s));
+  CKL(launch_xfwd(ctx->L[0], x, *nslots, s));
   return TM_OK;
 }
 
-// inverse x pass on design rows with the chain rule into G (+ max |G|)
-int xinv_chain(tm_ctx* ctx, const float* rho, float* G, cudaStream_t s) {
+// inverse x pass on design rows with the chain rule into G (+ max |G|); ncomp slots:
+// 1 = already contracted with the constant M0; 3 = components x, y, z (varying M0)
+int xinv_chain(tm_ctx* ctx, const float* rho, float* G, int ncomp, const int* slots, cudaStream_t s) {
   CK(cudaMemsetAsync(ctx->gmax, 0, sizeof(unsigned int), s));
   XInvArgs x{};
   x.rows = ctx->nzd * ctx->ny;
   x.nx = ctx->nx;
   x.P = ctx->P;
   x.sink = SINK_CHAIN;
+  x.ncomp = ncomp;
+  for (int j = 0; j < ncomp; j++) {
+    x.comp[j] = j;
+    x.in_slot[j] = slots[j];
+  }
   x.in = ctx->A;
   x.in_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
   x.rho = rho;
-  fill_m0(ctx, x.M0c, &x.M0v, &x.M0v_cstride);
+  x.M0v = ncomp > 1 ? ctx->M0v : nullptr;
+  x.M0v_cstride = design_cells(ctx);
   x.p = (float)ctx->p;
   x.G = G;
   x.gmax = ctx->gmax;
@@ -248,6 +297,33 @@ int xinv_chain(tm_ctx* ctx, const float* rho, float* G, cudaStream_t s) {
   Timed t(ctx, KIND_XINV, s);
   CKL(launch_xinv(ctx->L[0], x, s));
   return TM_OK;
+}
+
+// Forward convolution of the magnetization into the requested components F (A slots 0..nF-1).
+int forward_field(tm_ctx* ctx, const float* rho, int nF, const int* F, cudaStream_t s) {
+  int r, nsl;
+  if ((r = xfwd_rho(ctx, rho, s, &nsl))) return r;
+  ConvSpec cs{};
+  if (!ctx->m0_var) {  // one input rho^p with u = M0; outputs v = e_c
+    cs.nin = 1;
+    cs.ain[0] = 0;
+    cs.bin[0] = kSlotsB - 1;  // outputs use B slots 0..nF-1
+    cs.u[0] = ctx->M0c;
+  } else {
+    cs.nin = 3;
+    for (int i = 0; i < 3; i++) {
+      cs.ain[i] = i;
+      cs.bin[i] = i;
+      cs.u[i] = kUnit[i];
+    }
+  }
+  cs.nout = nF;
+  for (int o = 0; o < nF; o++) {
+    cs.bout[o] = o;
+    cs.aout[o] = o;
+    cs.v[o] = kUnit[F[o]];
+  }
+  return conv_yz(ctx, cs, ctx->nzd, ctx->nz, s);
 }
 
 }  // namespace
@@ -312,8 +388,8 @@ int tm_set_grid(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[
   const long long P = ctx->P;
   if (zpass_smem(Lz) > 227 * 1024) return fail(ctx, TM_ERR_SIZE, "Lz = %d too large for the z pass", Lz);
 
-  CK(cudaMalloc(&ctx->A, 3LL * ctx->nz * ctx->ny * P * sizeof(float2)));
-  CK(cudaMalloc(&ctx->B, 3LL * ctx->nz * Ly * P * sizeof(float2)));
+  CK(cudaMalloc(&ctx->A, (long long)kSlotsA * ctx->nz * ctx->ny * P * sizeof(float2)));
+  CK(cudaMalloc(&ctx->B, (long long)kSlotsB * ctx->nz * Ly * P * sizeof(float2)));
   CK(cudaMalloc(&ctx->T, 6LL * (Lz / 2 + 1) * (Ly / 2 + 1) * P * sizeof(float)));
   // twiddles W_L^m = exp(-2 pi i m / L) from float64 host values
   std::vector<float2> tw;
@@ -333,7 +409,7 @@ int tm_set_grid(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[
   CK(cudaMalloc(&ctx->zcol, zc.size() * sizeof(int2)));
   CK(cudaMemcpy(ctx->zcol, zc.data(), zc.size() * sizeof(int2), cudaMemcpyHostToDevice));
   const int rpb = xinv_rows_per_block();
-  ctx->nJpart = (ctx->nz * ctx->ny + rpb - 1) / rpb;
+  ctx->nJpart = 3 * ((ctx->nz * ctx->ny + rpb - 1) / rpb);
   CK(cudaMalloc(&ctx->Jpart, ctx->nJpart * sizeof(double)));
   ctx->have_grid = true;
   ctx->err[0] = 0;
@@ -392,13 +468,18 @@ int tm_stray_field(tm_ctx* ctx, const float* rho, float* H, void* stream) {
   if (r) return r;
   if (!rho || !H) return fail(ctx, TM_ERR_ARG, "null array");
   cudaStream_t s = S(stream);
-  if ((r = xfwd_rho(ctx, rho, s))) return r;
-  if ((r = conv_yz(ctx, ctx->nzd, ctx->nz, s))) return r;
+  const int F[3] = {0, 1, 2};
+  if ((r = forward_field(ctx, rho, 3, F, s))) return r;
   XInvArgs x{};
   x.rows = ctx->nz * ctx->ny;
   x.nx = ctx->nx;
   x.P = ctx->P;
   x.sink = SINK_FIELD;
+  x.ncomp = 3;
+  for (int j = 0; j < 3; j++) {
+    x.comp[j] = j;
+    x.in_slot[j] = j;
+  }
   x.in = ctx->A;
   x.in_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
   x.H = H;
@@ -423,15 +504,41 @@ int tm_stray_field_adjoint(tm_ctx* ctx, const float* rho, const float* gH, float
   x.src = SRC_VECTOR;
   x.vec = gH;
   x.vec_cstride = out_cells(ctx);
+  for (int c = 0; c < 3; c++) {
+    x.comp[c] = c;
+    x.out_slot[c] = c;
+  }
   x.out = ctx->A;
   x.out_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
   x.tw = ctx->tw;
   {
     Timed t(ctx, KIND_XFWD, s);
-    CKL(launch_xfwd(ctx->L[0], x, s));
+    CKL(launch_xfwd(ctx->L[0], x, 3, s));
   }
-  if ((r = conv_yz(ctx, ctx->nz, ctx->nzd, s))) return r;
-  return xinv_chain(ctx, rho, dJdrho, s);
+  ConvSpec cs{};
+  cs.nin = 3;
+  for (int i = 0; i < 3; i++) {
+    cs.ain[i] = i;
+    cs.bin[i] = i;
+    cs.u[i] = kUnit[i];
+  }
+  const int slots[3] = {0, 1, 2};
+  if (!ctx->m0_var) {  // contract the output with M0: one spectrum
+    cs.nout = 1;
+    cs.bout[0] = 0;
+    cs.aout[0] = 0;
+    cs.v[0] = ctx->M0c;
+    if ((r = conv_yz(ctx, cs, ctx->nz, ctx->nzd, s))) return r;
+    return xinv_chain(ctx, rho, dJdrho, 1, slots, s);
+  }
+  cs.nout = 3;
+  for (int o = 0; o < 3; o++) {
+    cs.bout[o] = o;
+    cs.aout[o] = o;
+    cs.v[o] = kUnit[o];
+  }
+  if ((r = conv_yz(ctx, cs, ctx->nz, ctx->nzd, s))) return r;
+  return xinv_chain(ctx, rho, dJdrho, 3, slots, s);
 }
 
 int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask, const float* H_target,
@@ -441,14 +548,29 @@ int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask
   if (r) return r;
   if (!rho || !mask || !w || !dJdrho) return fail(ctx, TM_ERR_ARG, "null array");
   if (!H_target && !Ht_const) return fail(ctx, TM_ERR_ARG, "H_target and Ht_const both null");
+  for (int c = 0; c < 3; c++)
+    if (!isfinite(w[c])) return fail(ctx, TM_ERR_ARG, "weights must be finite");
   cudaStream_t s = S(stream);
-  if ((r = xfwd_rho(ctx, rho, s))) return r;
-  if ((r = conv_yz(ctx, ctx->nzd, ctx->nz, s))) return r;
+  // components the objective weighs; the forward computes those (all three when H is
+  // requested or M0 varies, because the varying-M0 chain rule needs every component)
+  int W[3], nW = 0;
+  for (int c = 0; c < 3; c++)
+    if (w[c] != 0.0f) W[nW++] = c;
+  const bool all3 = H_out || ctx->m0_var || nW == 0;
+  int F[3], nF = 0;
+  for (int c = 0; c < 3; c++)
+    if (all3 || w[c] != 0.0f) F[nF++] = c;
+  if ((r = forward_field(ctx, rho, nF, F, s))) return r;
   XInvArgs x{};
   x.rows = ctx->nz * ctx->ny;
   x.nx = ctx->nx;
   x.P = ctx->P;
   x.sink = SINK_OBJECTIVE;
+  x.ncomp = nF;
+  for (int j = 0; j < nF; j++) {
+    x.comp[j] = F[j];
+    x.in_slot[j] = j;
+  }
   x.in = ctx->A;
   x.in_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
   x.H = H_out;
@@ -469,10 +591,40 @@ int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask
   }
   {
     Timed t(ctx, KIND_OTHER, s);
-    CKL(launch_j_finalize(ctx->Jpart, ctx->nJpart, ctx->Jdev, s));
+    const int nblk = (x.rows + xinv_rows_per_block() - 1) / xinv_rows_per_block();
+    CKL(launch_j_finalize(ctx->Jpart, nF * nblk, ctx->Jdev, s));
   }
-  if ((r = conv_yz(ctx, ctx->nz, ctx->nzd, s))) return r;
-  if ((r = xinv_chain(ctx, rho, dJdrho, s))) return r;
+  // adjoint: sources g_c in the A slots of the forward outputs
+  ConvSpec cs{};
+  int slots[3] = {0, 1, 2};
+  if (nW == 0) {
+    CK(cudaMemsetAsync(dJdrho, 0, design_cells(ctx) * sizeof(float), s));
+  } else if (!ctx->m0_var) {  // inputs: weighted components; output contracted with M0
+    cs.nin = nW;
+    for (int i = 0; i < nW; i++) {
+      int j = 0;
+      while (F[j] != W[i]) j++;
+      cs.ain[i] = j;
+      cs.bin[i] = j;
+      cs.u[i] = kUnit[W[i]];
+    }
+    cs.nout = 1;
+    cs.bout[0] = cs.bin[0];
+    cs.aout[0] = cs.ain[0];
+    cs.v[0] = ctx->M0c;
+    if ((r = conv_yz(ctx, cs, ctx->nz, ctx->nzd, s))) return r;
+    slots[0] = cs.aout[0];
+    if ((r = xinv_chain(ctx, rho, dJdrho, 1, slots, s))) return r;
+  } else {  // varying M0: all three components in and out
+    cs.nin = 3;
+    cs.nout = 3;
+    for (int i = 0; i < 3; i++) {
+      cs.ain[i] = cs.bin[i] = cs.bout[i] = cs.aout[i] = i;
+      cs.u[i] = cs.v[i] = kUnit[i];
+    }
+    if ((r = conv_yz(ctx, cs, ctx->nz, ctx->nzd, s))) return r;
+    if ((r = xinv_chain(ctx, rho, dJdrho, 3, slots, s))) return r;
+  }
   if (J_host) {
     CK(cudaMemcpyAsync(ctx->Jhost, ctx->Jdev, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -11,65 +11,85 @@ namespace tmk {
 constexpr int kMaxL = 576;
 constexpr int kNT = 256;  // threads per block of every FFT pass
 
-enum XSource { SRC_RHO_CONST = 0, SRC_RHO_FIELD = 1, SRC_VECTOR = 2 };
+enum XSource { SRC_RHO_POW = 0, SRC_RHO_M0 = 1, SRC_VECTOR = 2 };
 enum XSink { SINK_FIELD = 0, SINK_OBJECTIVE = 1, SINK_CHAIN = 2 };
 
-// Forward x pass: real rows -> half spectra [3][rows][P] (kx < Lx/2+1 valid, rest 0).
+// Spectral workspaces hold up to kSlots components ("slots"), component-major.
+constexpr int kSlotsA = 3;
+constexpr int kSlotsB = 4;
+
+// Forward x pass: real rows -> half spectra [slot][rows][P] (kx < Lx/2+1 valid, rest 0).
+// One block per (32-row tile, component); blockIdx.y indexes comp[] / out_slot[].
 struct XFwdArgs {
   int rows, nx, P;
   int src;                  // XSource
-  const float* rho;         // [rows][nx]                (RHO_*)
-  const float* M0v;         // [3][rows][nx]             (RHO_FIELD)
-  long long M0v_cstride;
-  float M0c[3];             // constant M0               (RHO_CONST)
+  const float* rho;         // [rows][nx]                       (RHO_*)
   float p;
-  const float* vec;         // [3][rows][nx]             (VECTOR)
+  const float* M0v;         // [3][rows][nx]                    (RHO_M0: rho^p M0_c)
+  long long M0v_cstride;
+  const float* vec;         // [3][rows][nx]                    (VECTOR)
   long long vec_cstride;
-  float2* out;              // [3][rows][P]
+  int comp[3];              // source component per blockIdx.y
+  int out_slot[3];
+  float2* out;              // [slot][rows][P]
   long long out_cstride;
   const float2* tw;         // W_L^m, m < L
 };
 
-// Inverse x pass: half spectra -> real rows, then one of three sinks.
+// Inverse x pass: half spectra -> real rows, then a sink.
+//  FIELD:     block (tile, j): H[comp[j]] = row of slot in_slot[j]
+//  OBJECTIVE: block (tile, j): H_c of slot in_slot[j], c = comp[j]; if w_c != 0:
+//             J partial, g_c = 2 w_c (H_c - Ht_c) on the mask, forward x transform
+//             of g_c written back into slot in_slot[j]
+//  CHAIN:     block (tile): G = p rho^(p-1) sum_j coef_j D_j over ncomp slots, where
+//             coef_j = M0v[comp[j]] (varying M0) or 1 (slot already contracted with M0)
 struct XInvArgs {
   int rows, nx, P;
   int sink;                 // XSink
-  const float2* in;         // [3][rows][P]
+  int ncomp;
+  int comp[3], in_slot[3];
+  const float2* in;         // [slot][rows][P]
   long long in_cstride;
   float* H;                 // [3][rows][nx] (FIELD; optional in OBJECTIVE)
   long long H_cstride;
-  // OBJECTIVE: J = sum_mask sum_c w_c (H_c - Ht_c)^2, g = 2 w (H - Ht) on the mask
   const uint8_t* mask;      // [rows][nx]
   const float* Ht;          // [3][rows][nx] or null -> Htc
   long long Ht_cstride;
   float Htc[3], w[3];
-  float2* adj_out;          // [3][rows][P], may alias in
-  double* Jpart;            // [gridDim.x]
-  // CHAIN: G = p rho^(p-1) M0 . (D g)
+  float2* adj_out;          // [slot][rows][P], aliases in
+  double* Jpart;            // [3][gridDim.x]
   const float* rho;         // [rows][nx]
-  const float* M0v;         // [3][rows][nx] or null -> M0c
+  const float* M0v;         // [3][rows][nx] or null (contracted slot)
   long long M0v_cstride;
-  float M0c[3];
   float p;
   float* G;                 // [rows][nx]
   unsigned int* gmax;       // max |G| as float bits
   const float2* tw;
 };
 
-// y pass over [3][planes][points][P] arrays, tiles of 16 kx columns.
+// y pass over [slot][planes][points][P] arrays, tiles of 16 kx columns; blockIdx.z -> in_slot[], out_slot[].
 struct YArgs {
   const float2* in;
   float2* out;
   int n_in, n_out, nplanes, P;
   long long in_pstride, out_pstride, in_zstride, out_zstride, in_cstride, out_cstride;
+  int in_slot[4], out_slot[4];
   const float2* tw;
 };
 
-// z pass: forward z FFT, tensor product, inverse z FFT, in place on [3][z][Ly][P].
+// z pass, in place on B[slot][z][Ly][P]: forward z transform of nin input slots,
+// out_o(k) = sum_i s_oi(k) in_i(k) with s_oi = sum_c coef[o][i][c] N^_c(k) over the six
+// unique tensor components (xx, yy, zz, xy, xz, yz), inverse z transform into out_slot[o].
+// nin == 1: one block per (tile, column, output). nin > 1: a cluster of nin blocks per
+// (tile, column); block r transforms input r and computes output r (r < nout).
 struct ZArgs {
   float2* buf;
-  long long cstride, zstride;  // between components, between z planes
-  int n_in, n_out, Ly, P;
+  long long cstride, zstride;  // between slots, between z planes
+  int n_in, n_out, Ly, P;      // input / output z planes
+  int nin, nout;
+  int in_slot[3], out_slot[3];
+  float coef[3][3][6];
+  int need[3];                 // per output: bit c set if tensor component c is used
   const float* T;              // [6][Lz/2+1][Ly/2+1][P]
   long long Tc;                // elements per tensor component
   long long Tz;                // (Ly/2+1) * P
@@ -77,10 +97,10 @@ struct ZArgs {
   const float2* tw;
 };
 
-int launch_xfwd(int L, const XFwdArgs& a, cudaStream_t s);
+int launch_xfwd(int L, const XFwdArgs& a, int ncomp, cudaStream_t s);
 int launch_xinv(int L, const XInvArgs& a, cudaStream_t s);
-int launch_yfwd(int L, const YArgs& a, cudaStream_t s);
-int launch_yinv(int L, const YArgs& a, cudaStream_t s);
+int launch_yfwd(int L, const YArgs& a, int ncomp, cudaStream_t s);
+int launch_yinv(int L, const YArgs& a, int ncomp, cudaStream_t s);
 int launch_zpass(int L, const ZArgs& a, cudaStream_t s);
 int xinv_rows_per_block();
 size_t zpass_smem(int L);
