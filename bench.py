@@ -149,13 +149,14 @@ def _need(v, u):
     return sum(1 for x in c if x != 0)
 
 
-def alg_bytes(wl, L):
+def alg_bytes(wl, L, direct=True):
     """Algorithmic bytes per launch of each kernel kind for the objective+gradient step.
 
     Half spectra kx = 0..L/2 only (no padding); components actually carried: with a
     constant M0 the magnetization enters as one spectrum (rho^p, contracted with M0 in
     the z pass) and the adjoint leaves as one (contracted with M0); the forward carries
-    the weighted field components, the adjoint their dJ/dH.
+    the weighted field components, the adjoint their dJ/dH. Only the np planes that hold
+    target cells carry the forward field after the z pass and the adjoint source before it.
     """
     nx, ny, nz = wl.n_out
     nzd = wl.nzd
@@ -169,25 +170,30 @@ def alg_bytes(wl, L):
     ain, aout = (len(W), 1) if const else (3, 3)
     Tcomp = (Lz // 2 + 1) * (Ly // 2 + 1) * K * 4
     if const:
-        tf = len({i for c in W for i in range(6) if _need(e[c], M0)}) if W else 0
         tf = sum(_need(e[c], M0) for c in W)
         ta = sum(_need(M0, e[c]) for c in W)
     else:
         tf = ta = 6
+    npl = int(wl.mask().any(axis=(1, 2)).sum())  # planes holding target cells
     s8 = 8
-    def yz(nin, nout, zin, zout, tcomp):
-        return {
-            "y_forward": s8 * nin * zin * K * (ny + Ly),
-            "z_pass": s8 * K * Ly * (nin * zin + nout * zout) + tcomp * Tcomp,
-            "y_inverse": s8 * nout * zout * K * (Ly + ny),
-        }
-    f, a = yz(fin, fout, nzd, nz, tf), yz(ain, aout, nz, nzd, ta)
-    out = {k: (f[k] + a[k]) / 2 for k in f}
-    out["x_forward"] = 4 * nzd * ny * nx + s8 * fin * nzd * ny * K
-    obj = s8 * nz * ny * K * fout * 2 + nz * ny * nx  # spectra in, adjoint spectra out, mask
+    if direct:  # z summed in (kx, ky, z) space: the x/y-transformed tensor over nzd offsets
+        Tzc = nzd * (Ly // 2 + 1) * K * 4
+        zf = s8 * K * Ly * (fin * nzd + fout * npl) + tf * Tzc
+        za = s8 * K * Ly * (ain * npl + aout * nzd) + ta * Tzc
+    else:
+        zf = s8 * K * Ly * (fin * nzd + fout * npl) + tf * Tcomp
+        za = s8 * K * Ly * (ain * npl + aout * nzd) + ta * Tcomp
+    yf = (s8 * fin * nzd * K * (ny + Ly) + s8 * ain * npl * K * (ny + Ly)) / 2
+    yi = (s8 * fout * npl * K * (Ly + ny) + s8 * aout * nzd * K * (Ly + ny)) / 2
+    obj = s8 * npl * ny * K * fout * 2 + npl * ny * nx  # spectra in, adjoint spectra out, mask
     chain = s8 * aout * nzd * ny * K + 8 * nzd * ny * nx
-    out["x_inverse"] = (obj + chain) / 2
-    return out
+    return {
+        "x_forward": 4 * nzd * ny * nx + s8 * fin * nzd * ny * K,
+        "y_forward": yf,
+        "z_pass": (zf + za) / 2,
+        "y_inverse": yi,
+        "x_inverse": (obj + chain) / 2,
+    }
 
 
 def sha1(path):
@@ -281,8 +287,15 @@ def run_native(args):
     Htc, w = tuple(float(v) for v in wl.Ht_const_vec()), wl.w
     G = torch.empty_like(rho)
 
+    prepared = hasattr(m, "set_target")
+    if prepared:
+        m.set_target(mask, Ht_const=Htc, w=w)
+
     def step():
-        m.objective_and_gradient(rho, mask, Ht_const=Htc, w=w, G=G, sync=False)
+        if prepared:
+            m.evaluate(rho, G=G, sync=False)
+        else:
+            m.objective_and_gradient(rho, mask, Ht_const=Htc, w=w, G=G, sync=False)
         m.optimize_step(rho, G, wl.alpha, True)
 
     for _ in range(max(3, args.warmup)):
@@ -322,13 +335,28 @@ def run_native(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             rho.copy_(rho_h, non_blocking=True)
-            m.objective_and_gradient(rho, mask, Ht_const=Htc, w=w, G=G, sync=False)
-            m.optimize_step(rho, G, wl.alpha, True)
+            step()
             Js.append(m.objective())  # 8-byte device-to-host read, synchronises
         dt = time.perf_counter() - t0
         dt = max_over_ranks(dt, dist)
         e2e = {"value": ws * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(rho.numel() * 4),
                "d2h_bytes_per_step": 8}
+
+    # the same step through the one-shot call (mask passed each time, full z transforms
+    # restricted to the target planes on the device)
+    oneshot = None
+    if prepared:
+        for _ in range(2):
+            m.objective_and_gradient(rho, mask, Ht_const=Htc, w=w, G=G, sync=False)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(args.steps):
+            m.objective_and_gradient(rho, mask, Ht_const=Htc, w=w, G=G, sync=False)
+            m.optimize_step(rho, G, wl.alpha, True)
+        e1.record(s)
+        torch.cuda.synchronize()
+        oneshot = {"value": args.steps / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
+                   "call": "tm_objective_and_gradient + tm_optimize_step"}
 
     if rank != 0:
         if dist is not None:
@@ -340,7 +368,7 @@ def run_native(args):
     L = m.fft_lengths()
     roof = None
     if prof:
-        ab = alg_bytes(wl, L)
+        ab = alg_bytes(wl, L, direct=prepared)
         kind = max((k for k in prof if prof[k][1] > 0 and k in ab), key=lambda k: prof[k][0])
         t_launch = prof[kind][0] / prof[kind][1] / 1e3
         achieved = ab[kind] / t_launch / 1e9
@@ -351,7 +379,9 @@ def run_native(args):
         roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                 "alg_bytes_per_launch": ab[kind], "ms_per_launch": t_launch * 1e3,
-                "per_kernel_ms_per_step": {k: prof[k][0] / args.steps for k in prof}}
+                "per_kernel_ms_per_step": {k: prof[k][0] / args.steps for k in prof},
+                "per_kernel_alg_gbs": {k: ab[k] / (prof[k][0] / prof[k][1] / 1e3) / 1e9
+                                       for k in ab if prof.get(k, (0, 0))[1] > 0}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -360,7 +390,8 @@ def run_native(args):
         "config": {"workload": wl.name, "cells": list(wl.n_out), "fft": list(L), "step": "objective+gradient+update",
                    "parallelism": f"replicas{ws}", "l2": "working set (>2 GB) larger than L2; no flush"},
         "clocks": ck, "gpu_launches": (int(round(launches_per_step * args.steps)) if launches_per_step else None),
-        "roofline": roof, "e2e": e2e, "J_first": J0,
+        "roofline": roof, "e2e": e2e, "J_first": J0, "oneshot": oneshot,
+        "call": "tm_set_target once; per step tm_evaluate + tm_optimize_step" if prepared else None,
     }
     if ws == 1 and not args.no_cpu_baseline and args.impl == "native":
         try:

@@ -118,7 +118,23 @@ int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask
                               const float Ht_const[3], const float w[3], double* J_host, float* dJdrho,
                               float* H_out, void* stream);
 
-/* J of the last tm_objective_and_gradient (synchronises `stream`). */
+/*
+ * Prepared objective for an optimisation loop (the same J and dJ/drho as
+ * tm_objective_and_gradient). tm_set_target copies mask [nz][ny][nx] and
+ * H_target (or the constant Ht_const) and the weights w into the context and
+ * finds the z planes that hold target cells (synchronises `stream`, once).
+ * tm_evaluate(rho) then returns J (as tm_objective_and_gradient, J_host may be
+ * NULL) and writes dJdrho. When the target occupies at most 8 planes, the z
+ * part of the convolution is summed directly in (kx, ky, z) space onto those
+ * planes (forward) and from them (adjoint), with the tensor transformed along
+ * x and y only -- the same discrete convolution (Eq. (convolution)) without the
+ * z transforms; otherwise it runs the full pipeline.
+ */
+int tm_set_target(tm_ctx* ctx, const uint8_t* mask, const float* H_target, const float Ht_const[3], const float w[3],
+                  void* stream);
+int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, void* stream);
+
+/* J of the last tm_objective_and_gradient or tm_evaluate (synchronises `stream`). */
 int tm_get_objective(tm_ctx* ctx, double* J_host, void* stream);
 
 /*

@@ -26,6 +26,13 @@ struct tm_ctx {
   double M0c[3] = {0, 0, 0};
   float* M0v = nullptr;     // [3][nzd][ny][nx]
   float* T = nullptr;       // [6][Lz/2+1][Ly/2+1][P]
+  float* Tz = nullptr;      // [6][nz][Ly/2+1][P] (x, y transformed; z offset)
+  // prepared target (tm_set_target)
+  bool have_target = false;
+  uint8_t* tmask = nullptr;  // [nz][ny][nx]
+  float* tHt = nullptr;      // [3][nz][ny][nx] or null
+  float tHtc[3] = {0, 0, 0}, tw_[3] = {0, 0, 0};
+  int tz0 = 0, tz1 = 0;      // planes holding target cells
   float2* A = nullptr;      // [3][nz][ny][P]
   float2* B = nullptr;      // [4][nz][Ly][P]
   float2* tw = nullptr;     // twiddles: Lx | Ly | Lz
@@ -34,6 +41,7 @@ struct tm_ctx {
   int nJpart = 0;
   double* Jdev = nullptr;
   unsigned int* gmax = nullptr;
+  int* ext = nullptr;       // [2]: z range of the target planes
   double* Jhost = nullptr;  // pinned
   // per-kernel event timing (tm_profile)
   bool prof_on = false;
@@ -87,6 +95,13 @@ int pick_length(int n) {
 void free_grid(tm_ctx* c) {
   cudaFree(c->M0v);
   cudaFree(c->T);
+  cudaFree(c->Tz);
+  cudaFree(c->tmask);
+  cudaFree(c->tHt);
+  c->Tz = nullptr;
+  c->tmask = nullptr;
+  c->tHt = nullptr;
+  c->have_target = false;
   cudaFree(c->A);
   cudaFree(c->B);
   cudaFree(c->tw);
@@ -162,6 +177,8 @@ struct ConvSpec {
   int ain[3], bin[3], bout[3], aout[3];
   const double* u[3];  // per input
   const double* v[3];  // per output
+  const int* ext;      // device z range of the target planes, used when in_ext / out_ext
+  int in_ext, out_ext;
 };
 
 int conv_yz(tm_ctx* ctx, const ConvSpec& cs, int zin, int zout, cudaStream_t s) {
@@ -185,6 +202,7 @@ int conv_yz(tm_ctx* ctx, const ConvSpec& cs, int zin, int zout, cudaStream_t s) 
     y.in_slot[i] = cs.ain[i];
     y.out_slot[i] = cs.bin[i];
   }
+  y.ext = cs.in_ext ? cs.ext : nullptr;
   y.tw = ctx->tw + Lx;
   {
     Timed t(ctx, KIND_YFWD, s);
@@ -215,6 +233,9 @@ int conv_yz(tm_ctx* ctx, const ConvSpec& cs, int zin, int zout, cudaStream_t s) 
   z.Tz = (long long)(Ly / 2 + 1) * P;
   z.Tc = (long long)(Lz / 2 + 1) * z.Tz;
   z.zcol = ctx->zcol;
+  z.ext = cs.ext;
+  z.in_ext = cs.in_ext;
+  z.out_ext = cs.out_ext;
   z.tw = ctx->tw + Lx + Ly;
   {
     Timed t(ctx, KIND_ZPASS, s);
@@ -238,11 +259,75 @@ int conv_yz(tm_ctx* ctx, const ConvSpec& cs, int zin, int zout, cudaStream_t s) 
     yi.in_slot[o] = cs.bout[o];
     yi.out_slot[o] = cs.aout[o];
   }
+  yi.ext = cs.out_ext ? cs.ext : nullptr;
   yi.tw = ctx->tw + Lx;
   {
     Timed t(ctx, KIND_YINV, s);
     CKL(launch_yinv(Ly, yi, cs.nout, s));
   }
+  return TM_OK;
+}
+
+// y pass (forward or inverse) over planes [z0, z0 + np) between A slots and B slots
+int ypass(tm_ctx* ctx, bool inv, int n, const int* aslot, const int* bslot, int z0, int np, cudaStream_t s) {
+  const int Lx = ctx->L[0], Ly = ctx->L[1];
+  const long long P = ctx->P;
+  YArgs y{};
+  y.in = inv ? ctx->B : ctx->A;
+  y.out = inv ? ctx->A : ctx->B;
+  y.n_in = inv ? Ly : ctx->ny;
+  y.n_out = inv ? ctx->ny : Ly;
+  y.nplanes = np;
+  y.P = ctx->P;
+  y.in_pstride = P;
+  y.out_pstride = P;
+  y.in_zstride = (inv ? (long long)Ly : (long long)ctx->ny) * P;
+  y.out_zstride = (inv ? (long long)ctx->ny : (long long)Ly) * P;
+  y.in_cstride = inv ? (long long)ctx->nz * Ly * P : (long long)ctx->nz * ctx->ny * P;
+  y.out_cstride = inv ? (long long)ctx->nz * ctx->ny * P : (long long)ctx->nz * Ly * P;
+  for (int i = 0; i < n; i++) {
+    y.in_slot[i] = inv ? bslot[i] : aslot[i];
+    y.out_slot[i] = inv ? aslot[i] : bslot[i];
+  }
+  y.z0 = z0;
+  y.tw = ctx->tw + Lx;
+  Timed t(ctx, inv ? KIND_YINV : KIND_YFWD, s);
+  CKL(inv ? launch_yinv(Ly, y, n, s) : launch_yfwd(Ly, y, n, s));
+  return TM_OK;
+}
+
+// direct z convolution between B slots: inputs planes [zi0, zi0 + nzi), outputs [zo0, zo0 + nzo)
+int zdirect(tm_ctx* ctx, const ConvSpec& cs, int zi0, int nzi, int zo0, int nzo, cudaStream_t s) {
+  const int Ly = ctx->L[1];
+  const long long P = ctx->P;
+  ZDirArgs z{};
+  z.buf = ctx->B;
+  z.cstride = (long long)ctx->nz * Ly * P;
+  z.zstride = (long long)Ly * P;
+  z.P = ctx->P;
+  z.Ly = Ly;
+  z.nin = cs.nin;
+  z.nout = cs.nout;
+  for (int i = 0; i < cs.nin; i++) z.in_slot[i] = cs.bin[i];
+  for (int o = 0; o < cs.nout; o++) {
+    z.out_slot[o] = cs.bout[o];
+    for (int i = 0; i < cs.nin; i++) {
+      coef6(z.coef[o][i], cs.v[o], cs.u[i]);
+      z.need[o][i] = 0;
+      for (int c = 0; c < 6; c++)
+        if (z.coef[o][i][c] != 0.0f) z.need[o][i] |= 1 << c;
+    }
+  }
+  z.Tz = ctx->Tz;
+  z.Tdz = (long long)(Ly / 2 + 1) * P;
+  z.Tc = (long long)ctx->nz * z.Tdz;
+  z.zcol = ctx->zcol;
+  z.zin0 = zi0;
+  z.nzin = nzi;
+  z.zout0 = zo0;
+  z.nzout = nzo;
+  Timed t(ctx, KIND_ZPASS, s);
+  CKL(launch_zdir(z, s));
   return TM_OK;
 }
 
@@ -300,7 +385,7 @@ int xinv_chain(tm_ctx* ctx, const float* rho, float* G, int ncomp, const int* sl
 }
 
 // Forward convolution of the magnetization into the requested components F (A slots 0..nF-1).
-int forward_field(tm_ctx* ctx, const float* rho, int nF, const int* F, cudaStream_t s) {
+int forward_field(tm_ctx* ctx, const float* rho, int nF, const int* F, const int* ext, cudaStream_t s) {
   int r, nsl;
   if ((r = xfwd_rho(ctx, rho, s, &nsl))) return r;
   ConvSpec cs{};
@@ -323,6 +408,8 @@ int forward_field(tm_ctx* ctx, const float* rho, int nF, const int* F, cudaStrea
     cs.aout[o] = o;
     cs.v[o] = kUnit[F[o]];
   }
+  cs.ext = ext;
+  cs.out_ext = ext != nullptr;
   return conv_yz(ctx, cs, ctx->nzd, ctx->nz, s);
 }
 
@@ -342,6 +429,7 @@ int tm_create(tm_ctx** out, int device) {
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->Jdev, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->gmax, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->ext, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->Jhost, sizeof(double));
   if (e != cudaSuccess) {
     tm_destroy(ctx);
@@ -358,6 +446,7 @@ void tm_destroy(tm_ctx* ctx) {
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   cudaFree(ctx->Jdev);
   cudaFree(ctx->gmax);
+  cudaFree(ctx->ext);
   if (ctx->Jhost) cudaFreeHost(ctx->Jhost);
   delete ctx;
 }
@@ -391,6 +480,7 @@ int tm_set_grid(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[
   CK(cudaMalloc(&ctx->A, (long long)kSlotsA * ctx->nz * ctx->ny * P * sizeof(float2)));
   CK(cudaMalloc(&ctx->B, (long long)kSlotsB * ctx->nz * Ly * P * sizeof(float2)));
   CK(cudaMalloc(&ctx->T, 6LL * (Lz / 2 + 1) * (Ly / 2 + 1) * P * sizeof(float)));
+  CK(cudaMalloc(&ctx->Tz, 6LL * ctx->nz * (Ly / 2 + 1) * P * sizeof(float)));
   // twiddles W_L^m = exp(-2 pi i m / L) from float64 host values
   std::vector<float2> tw;
   for (int a = 0; a < 3; a++)
@@ -456,8 +546,8 @@ int tm_set_tensor(tm_ctx* ctx, void* stream) {
   if (!ctx) return TM_ERR_ARG;
   if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
   CK(cudaSetDevice(ctx->device));
-  int r = tensor_setup(ctx->nx, ctx->ny, ctx->nz, ctx->d, ctx->L[0], ctx->L[1], ctx->L[2], ctx->P, ctx->T, nullptr,
-                       S(stream), ctx->err, sizeof(ctx->err));
+  int r = tensor_setup(ctx->nx, ctx->ny, ctx->nz, ctx->d, ctx->L[0], ctx->L[1], ctx->L[2], ctx->P, ctx->T, ctx->Tz,
+                       nullptr, S(stream), ctx->err, sizeof(ctx->err));
   if (r != 0) return TM_ERR_CUDA;
   ctx->have_tensor = true;
   return TM_OK;
@@ -469,7 +559,7 @@ int tm_stray_field(tm_ctx* ctx, const float* rho, float* H, void* stream) {
   if (!rho || !H) return fail(ctx, TM_ERR_ARG, "null array");
   cudaStream_t s = S(stream);
   const int F[3] = {0, 1, 2};
-  if ((r = forward_field(ctx, rho, 3, F, s))) return r;
+  if ((r = forward_field(ctx, rho, 3, F, nullptr, s))) return r;
   XInvArgs x{};
   x.rows = ctx->nz * ctx->ny;
   x.nx = ctx->nx;
@@ -560,7 +650,15 @@ int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask
   int F[3], nF = 0;
   for (int c = 0; c < 3; c++)
     if (all3 || w[c] != 0.0f) F[nF++] = c;
-  if ((r = forward_field(ctx, rho, nF, F, s))) return r;
+  // without H_out only the planes holding target cells are needed: the forward
+  // field is evaluated there alone and the adjoint source lives there alone
+  const int* ext = nullptr;
+  if (!H_out) {
+    Timed t(ctx, KIND_OTHER, s);
+    CKL(launch_mask_extent(mask, ctx->nz, (long long)ctx->ny * ctx->nx, ctx->ext, s));
+    ext = ctx->ext;
+  }
+  if ((r = forward_field(ctx, rho, nF, F, ext, s))) return r;
   XInvArgs x{};
   x.rows = ctx->nz * ctx->ny;
   x.nx = ctx->nx;
@@ -584,6 +682,8 @@ int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask
   }
   x.adj_out = ctx->A;
   x.Jpart = ctx->Jpart;
+  x.ext = ext;
+  x.ny = ctx->ny;
   x.tw = ctx->tw;
   {
     Timed t(ctx, KIND_XINV, s);
@@ -612,6 +712,8 @@ int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask
     cs.bout[0] = cs.bin[0];
     cs.aout[0] = cs.ain[0];
     cs.v[0] = ctx->M0c;
+    cs.ext = ext;
+    cs.in_ext = ext != nullptr;
     if ((r = conv_yz(ctx, cs, ctx->nz, ctx->nzd, s))) return r;
     slots[0] = cs.aout[0];
     if ((r = xinv_chain(ctx, rho, dJdrho, 1, slots, s))) return r;
@@ -622,8 +724,155 @@ int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask
       cs.ain[i] = cs.bin[i] = cs.bout[i] = cs.aout[i] = i;
       cs.u[i] = cs.v[i] = kUnit[i];
     }
+    cs.ext = ext;
+    cs.in_ext = ext != nullptr;
     if ((r = conv_yz(ctx, cs, ctx->nz, ctx->nzd, s))) return r;
     if ((r = xinv_chain(ctx, rho, dJdrho, 3, slots, s))) return r;
+  }
+  if (J_host) {
+    CK(cudaMemcpyAsync(ctx->Jhost, ctx->Jdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *J_host = *ctx->Jhost;
+  }
+  return TM_OK;
+}
+
+int tm_set_target(tm_ctx* ctx, const uint8_t* mask, const float* H_target, const float Ht_const[3], const float w[3],
+                  void* stream) {
+  if (!ctx) return TM_ERR_ARG;
+  if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
+  if (!mask || !w) return fail(ctx, TM_ERR_ARG, "null array");
+  if (!H_target && !Ht_const) return fail(ctx, TM_ERR_ARG, "H_target and Ht_const both null");
+  for (int c = 0; c < 3; c++)
+    if (!isfinite(w[c])) return fail(ctx, TM_ERR_ARG, "weights must be finite");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = S(stream);
+  const long long n = out_cells(ctx);
+  if (!ctx->tmask) CK(cudaMalloc(&ctx->tmask, n));
+  CK(cudaMemcpyAsync(ctx->tmask, mask, n, cudaMemcpyDeviceToDevice, s));
+  if (H_target) {
+    if (!ctx->tHt) CK(cudaMalloc(&ctx->tHt, 3 * n * sizeof(float)));
+    CK(cudaMemcpyAsync(ctx->tHt, H_target, 3 * n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  } else {
+    cudaFree(ctx->tHt);
+    ctx->tHt = nullptr;
+  }
+  for (int c = 0; c < 3; c++) {
+    ctx->tHtc[c] = Ht_const ? Ht_const[c] : 0.0f;
+    ctx->tw_[c] = w[c];
+  }
+  CKL(launch_mask_extent(ctx->tmask, ctx->nz, (long long)ctx->ny * ctx->nx, ctx->ext, s));
+  int ext[2];
+  CK(cudaMemcpyAsync(ext, ctx->ext, sizeof(ext), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  ctx->tz0 = ext[1] > ext[0] ? ext[0] : 0;
+  ctx->tz1 = ext[1] > ext[0] ? ext[1] : 0;
+  ctx->have_target = true;
+  return TM_OK;
+}
+
+int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, void* stream) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!ctx->have_target) return fail(ctx, TM_ERR_STATE, "no target: call tm_set_target first");
+  if (!rho || !dJdrho) return fail(ctx, TM_ERR_ARG, "null array");
+  const int np = ctx->tz1 - ctx->tz0;
+  if (np > kDirectPlanesMax)  // many target planes: the FFT z pass is cheaper
+    return tm_objective_and_gradient(ctx, rho, ctx->tmask, ctx->tHt, ctx->tHtc, ctx->tw_, J_host, dJdrho, nullptr,
+                                     stream);
+  cudaStream_t s = S(stream);
+  const float* w = ctx->tw_;
+  int W[3], nW = 0;
+  for (int c = 0; c < 3; c++)
+    if (w[c] != 0.0f) W[nW++] = c;
+  if (np == 0 || nW == 0) {
+    CK(cudaMemsetAsync(ctx->Jdev, 0, sizeof(double), s));
+    CK(cudaMemsetAsync(dJdrho, 0, design_cells(ctx) * sizeof(float), s));
+  } else {
+    // forward: x, y on the design planes; z summed directly onto the target planes
+    const bool all3 = ctx->m0_var;
+    int F[3], nF = 0;
+    for (int c = 0; c < 3; c++)
+      if (all3 || w[c] != 0.0f) F[nF++] = c;
+    int nsl;
+    if ((r = xfwd_rho(ctx, rho, s, &nsl))) return r;
+    ConvSpec cs{};
+    cs.nin = nsl;
+    for (int i = 0; i < nsl; i++) {
+      cs.ain[i] = i;
+      cs.bin[i] = i;
+      cs.u[i] = nsl == 1 ? ctx->M0c : kUnit[i];
+    }
+    cs.nout = nF;
+    for (int o = 0; o < nF; o++) {
+      cs.bout[o] = o;
+      cs.aout[o] = o;
+      cs.v[o] = kUnit[F[o]];
+    }
+    if ((r = ypass(ctx, false, cs.nin, cs.ain, cs.bin, 0, ctx->nzd, s))) return r;
+    if ((r = zdirect(ctx, cs, 0, ctx->nzd, ctx->tz0, np, s))) return r;
+    if ((r = ypass(ctx, true, cs.nout, cs.aout, cs.bout, ctx->tz0, np, s))) return r;
+    // objective on the target rows; dJ/dH transformed along x in place
+    XInvArgs x{};
+    x.row_base = ctx->tz0 * ctx->ny;
+    x.rows = ctx->tz1 * ctx->ny;
+    x.nx = ctx->nx;
+    x.P = ctx->P;
+    x.sink = SINK_OBJECTIVE;
+    x.ncomp = nF;
+    for (int j = 0; j < nF; j++) {
+      x.comp[j] = F[j];
+      x.in_slot[j] = j;
+    }
+    x.in = ctx->A;
+    x.in_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
+    x.H_cstride = out_cells(ctx);
+    x.mask = ctx->tmask;
+    x.Ht = ctx->tHt;
+    x.Ht_cstride = out_cells(ctx);
+    for (int c = 0; c < 3; c++) {
+      x.Htc[c] = ctx->tHtc[c];
+      x.w[c] = w[c];
+    }
+    x.adj_out = ctx->A;
+    x.Jpart = ctx->Jpart;
+    x.ny = ctx->ny;
+    x.tw = ctx->tw;
+    {
+      Timed t(ctx, KIND_XINV, s);
+      CKL(launch_xinv(ctx->L[0], x, s));
+    }
+    {
+      Timed t(ctx, KIND_OTHER, s);
+      const int nblk = (np * ctx->ny + xinv_rows_per_block() - 1) / xinv_rows_per_block();
+      CKL(launch_j_finalize(ctx->Jpart, nF * nblk, ctx->Jdev, s));
+    }
+    // adjoint: y on the target planes, z summed directly onto the design planes
+    ConvSpec ca{};
+    if (!ctx->m0_var) {
+      ca.nin = nW;
+      for (int i = 0; i < nW; i++) {
+        int j = 0;
+        while (F[j] != W[i]) j++;
+        ca.ain[i] = j;
+        ca.bin[i] = j;
+        ca.u[i] = kUnit[W[i]];
+      }
+      ca.nout = 1;
+      ca.bout[0] = ca.bin[0];
+      ca.aout[0] = ca.ain[0];
+      ca.v[0] = ctx->M0c;
+    } else {
+      ca.nin = ca.nout = 3;
+      for (int i = 0; i < 3; i++) {
+        ca.ain[i] = ca.bin[i] = ca.bout[i] = ca.aout[i] = i;
+        ca.u[i] = ca.v[i] = kUnit[i];
+      }
+    }
+    if ((r = ypass(ctx, false, ca.nin, ca.ain, ca.bin, ctx->tz0, np, s))) return r;
+    if ((r = zdirect(ctx, ca, ctx->tz0, np, 0, ctx->nzd, s))) return r;
+    if ((r = ypass(ctx, true, ca.nout, ca.aout, ca.bout, 0, ctx->nzd, s))) return r;
+    if ((r = xinv_chain(ctx, rho, dJdrho, ca.nout, ca.aout, s))) return r;
   }
   if (J_host) {
     CK(cudaMemcpyAsync(ctx->Jhost, ctx->Jdev, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -689,8 +938,8 @@ int tm_debug_tensor_octant(tm_ctx* ctx, double* host_out, void* stream) {
   CK(cudaSetDevice(ctx->device));
   float* tmp = nullptr;
   CK(cudaMalloc(&tmp, 6LL * (ctx->L[2] / 2 + 1) * (ctx->L[1] / 2 + 1) * ctx->P * sizeof(float)));
-  int r = tensor_setup(ctx->nx, ctx->ny, ctx->nz, ctx->d, ctx->L[0], ctx->L[1], ctx->L[2], ctx->P, tmp, host_out,
-                       S(stream), ctx->err, sizeof(ctx->err));
+  int r = tensor_setup(ctx->nx, ctx->ny, ctx->nz, ctx->d, ctx->L[0], ctx->L[1], ctx->L[2], ctx->P, tmp, nullptr,
+                       host_out, S(stream), ctx->err, sizeof(ctx->err));
   cudaFree(tmp);
   return r ? TM_ERR_CUDA : TM_OK;
 }

@@ -8,9 +8,11 @@
 // pass is ever made.
 //
 // A tile holds 16 lines of one length-L transform in shared memory, element
-// (pos, line) at tile[pos * 16 + line]. A half-warp covers the 16 lines of one
-// position, so every 8-byte shared access of a stage touches one 128-byte row:
-// bank-conflict free for any radix pattern. Radices are 32, 16, 8, 4, 2 and 3
+// (pos, line) in row pos at column line ^ swz(pos), swz(pos) = (pos ^ pos>>4) & 15.
+// A half-warp covering the 16 lines of one position touches one 128-byte row
+// (bank-conflict free for any radix pattern); the XOR swizzle also spreads a
+// half-warp covering 16 positions of one line (the x passes read and write rows
+// of the grid that way) over distinct banks. Radices are 32, 16, 8, 4, 2 and 3
 // (in-register DFTs); lengths are L = 2^a 3^b with b <= 2, 8 <= L <= 1024.
 #pragma once
 #include <cuda_runtime.h>
@@ -19,6 +21,14 @@
 namespace tmk {
 
 constexpr int TB = 16;  // lines per tile
+
+// tile index of (pos, line); SW selects the XOR-swizzled layout (x passes)
+template <bool SW>
+__device__ __forceinline__ int tidx(int pos, int line) {
+  if (SW) return pos * TB + (line ^ ((pos ^ (pos >> 4)) & 15));
+  return pos * TB + line;
+}
+__device__ __forceinline__ int tix(int pos, int line) { return tidx<true>(pos, line); }
 
 template <typename T>
 struct alignas(2 * sizeof(T)) cx {
@@ -222,7 +232,7 @@ __device__ __forceinline__ void apply_twiddles(cx<T>* v, int j, const cx<T>* tw)
 }
 
 // One forward DIF stage in place on the tile.
-template <typename T, int L, int s, int NT>
+template <typename T, int L, int s, int NT, bool SW = false>
 __device__ __forceinline__ void dif_stage(cx<T>* tile, const cx<T>* tw) {
   using S = StageShape<L, s>;
   constexpr int ITER = (S::NU + NT - 1) / NT;
@@ -234,17 +244,17 @@ __device__ __forceinline__ void dif_stage(cx<T>* tile, const cx<T>* tw) {
       const int base = g * S::G + j;
       cx<T> v[S::R];
 #pragma unroll
-      for (int q = 0; q < S::R; q++) v[q] = tile[(base + q * S::M) * TB + line];
+      for (int q = 0; q < S::R; q++) v[q] = tile[tidx<SW>(base + q * S::M, line)];
       Dft<T, S::R, false>::run(v);
       apply_twiddles<T, L, s, false>(v, j, tw);
 #pragma unroll
-      for (int q = 0; q < S::R; q++) tile[(base + q * S::M) * TB + line] = v[q];
+      for (int q = 0; q < S::R; q++) tile[tidx<SW>(base + q * S::M, line)] = v[q];
     }
   }
 }
 
 // One inverse DIT stage in place on the tile.
-template <typename T, int L, int s, int NT>
+template <typename T, int L, int s, int NT, bool SW = false>
 __device__ __forceinline__ void dit_stage(cx<T>* tile, const cx<T>* tw) {
   using S = StageShape<L, s>;
   constexpr int ITER = (S::NU + NT - 1) / NT;
@@ -256,11 +266,11 @@ __device__ __forceinline__ void dit_stage(cx<T>* tile, const cx<T>* tw) {
       const int base = g * S::G + j;
       cx<T> v[S::R];
 #pragma unroll
-      for (int q = 0; q < S::R; q++) v[q] = tile[(base + q * S::M) * TB + line];
+      for (int q = 0; q < S::R; q++) v[q] = tile[tidx<SW>(base + q * S::M, line)];
       apply_twiddles<T, L, s, true>(v, j, tw);
       Dft<T, S::R, true>::run(v);
 #pragma unroll
-      for (int q = 0; q < S::R; q++) tile[(base + q * S::M) * TB + line] = v[q];
+      for (int q = 0; q < S::R; q++) tile[tidx<SW>(base + q * S::M, line)] = v[q];
     }
   }
 }
@@ -268,7 +278,7 @@ __device__ __forceinline__ void dit_stage(cx<T>* tile, const cx<T>* tw) {
 // Stage 0 forward, reading its inputs through ld(pos, line) (zero beyond the
 // valid range is the loader's job) and writing the tile. All loads of a thread
 // are issued before any arithmetic.
-template <typename T, int L, int NT, typename LD>
+template <typename T, int L, int NT, typename LD, bool SW = false>
 __device__ __forceinline__ void dif_stage0_load(cx<T>* tile, const cx<T>* tw, LD ld) {
   using S = StageShape<L, 0>;
   constexpr int ITER = (S::NU + NT - 1) / NT;
@@ -290,13 +300,13 @@ __device__ __forceinline__ void dif_stage0_load(cx<T>* tile, const cx<T>* tw, LD
       Dft<T, S::R, false>::run(v[it]);
       apply_twiddles<T, L, 0, false>(v[it], j, tw);
 #pragma unroll
-      for (int q = 0; q < S::R; q++) tile[(j + q * S::M) * TB + line] = v[it][q];
+      for (int q = 0; q < S::R; q++) tile[tidx<SW>(j + q * S::M, line)] = v[it][q];
     }
   }
 }
 
 // Last forward stage (M = 1), writing its outputs through st(pos, line, v).
-template <typename T, int L, int NT, typename ST>
+template <typename T, int L, int NT, typename ST, bool SW = false>
 __device__ __forceinline__ void dif_last_store(const cx<T>* tile, ST st) {
   constexpr int s = plan_stages(L) - 1;
   using S = StageShape<L, s>;
@@ -309,7 +319,7 @@ __device__ __forceinline__ void dif_last_store(const cx<T>* tile, ST st) {
       const int line = u % TB, g = u / TB;
       cx<T> v[S::R];
 #pragma unroll
-      for (int q = 0; q < S::R; q++) v[q] = tile[(g * S::R + q) * TB + line];
+      for (int q = 0; q < S::R; q++) v[q] = tile[tidx<SW>(g * S::R + q, line)];
       Dft<T, S::R, false>::run(v);
 #pragma unroll
       for (int q = 0; q < S::R; q++) st(g * S::R + q, line, v[q]);
@@ -318,7 +328,7 @@ __device__ __forceinline__ void dif_last_store(const cx<T>* tile, ST st) {
 }
 
 // First inverse stage (the last plan stage, M = 1) reading ld(pos, line).
-template <typename T, int L, int NT, typename LD>
+template <typename T, int L, int NT, typename LD, bool SW = false>
 __device__ __forceinline__ void dit_last_load(cx<T>* tile, LD ld) {
   constexpr int s = plan_stages(L) - 1;
   using S = StageShape<L, s>;
@@ -341,13 +351,13 @@ __device__ __forceinline__ void dit_last_load(cx<T>* tile, LD ld) {
       const int line = u % TB, g = u / TB;
       Dft<T, S::R, true>::run(v[it]);
 #pragma unroll
-      for (int q = 0; q < S::R; q++) tile[(g * S::R + q) * TB + line] = v[it][q];
+      for (int q = 0; q < S::R; q++) tile[tidx<SW>(g * S::R + q, line)] = v[it][q];
     }
   }
 }
 
 // Last inverse stage (plan stage 0), natural-order outputs through st(pos, line, v).
-template <typename T, int L, int NT, typename ST>
+template <typename T, int L, int NT, typename ST, bool SW = false>
 __device__ __forceinline__ void dit_stage0_store(const cx<T>* tile, const cx<T>* tw, ST st) {
   using S = StageShape<L, 0>;
   constexpr int ITER = (S::NU + NT - 1) / NT;
@@ -358,7 +368,7 @@ __device__ __forceinline__ void dit_stage0_store(const cx<T>* tile, const cx<T>*
       const int line = u % TB, j = u / TB;
       cx<T> v[S::R];
 #pragma unroll
-      for (int q = 0; q < S::R; q++) v[q] = tile[(j + q * S::M) * TB + line];
+      for (int q = 0; q < S::R; q++) v[q] = tile[tidx<SW>(j + q * S::M, line)];
       apply_twiddles<T, L, 0, true>(v, j, tw);
       Dft<T, S::R, true>::run(v);
 #pragma unroll
@@ -368,27 +378,35 @@ __device__ __forceinline__ void dit_stage0_store(const cx<T>* tile, const cx<T>*
 }
 
 // Helpers running stage ranges with a block barrier after each stage.
-template <typename T, int L, int NT, int s, int e>
+template <typename T, int L, int NT, int s, int e, bool SW = false>
 struct DifRange {
   static __device__ __forceinline__ void run(cx<T>* tile, const cx<T>* tw) {
     if constexpr (s < e) {
-      dif_stage<T, L, s, NT>(tile, tw);
+      dif_stage<T, L, s, NT, SW>(tile, tw);
       __syncthreads();
-      DifRange<T, L, NT, s + 1, e>::run(tile, tw);
+      DifRange<T, L, NT, s + 1, e, SW>::run(tile, tw);
     }
   }
 };
 // inverse stages s = hi-1 down to lo
-template <typename T, int L, int NT, int lo, int hi>
+template <typename T, int L, int NT, int lo, int hi, bool SW = false>
 struct DitRange {
   static __device__ __forceinline__ void run(cx<T>* tile, const cx<T>* tw) {
     if constexpr (hi > lo) {
-      dit_stage<T, L, hi - 1, NT>(tile, tw);
+      dit_stage<T, L, hi - 1, NT, SW>(tile, tw);
       __syncthreads();
-      DitRange<T, L, NT, lo, hi - 1>::run(tile, tw);
+      DitRange<T, L, NT, lo, hi - 1, SW>::run(tile, tw);
     }
   }
 };
+
+// frequency of the R consecutive positions g*R + q of the last stage (radix R):
+// k = k_of_pos(g*R) + q * (L / R)
+template <int L>
+__device__ __forceinline__ int k_of_group(int g) {
+  constexpr int S = plan_stages(L);
+  return k_of_pos<L>(g * plan_radix(L, S - 1));
+}
 
 // Cooperative copy of the length-L twiddle table W_L^m into shared memory.
 template <typename T, int NT>

@@ -64,6 +64,9 @@ struct XInvArgs {
   float p;
   float* G;                 // [rows][nx]
   unsigned int* gmax;       // max |G| as float bits
+  const int* ext;           // OBJECTIVE: device [zlo, zhi); blocks outside rows [zlo*ny, zhi*ny) skip
+  int ny;
+  int row_base;             // first row of block 0 (host-known); rows < `rows` are valid
   const float2* tw;
 };
 
@@ -74,6 +77,8 @@ struct YArgs {
   int n_in, n_out, nplanes, P;
   long long in_pstride, out_pstride, in_zstride, out_zstride, in_cstride, out_cstride;
   int in_slot[4], out_slot[4];
+  int z0;                   // first plane (host-known offset); planes z0 .. z0 + nplanes - 1
+  const int* ext;           // device [zlo, zhi): process only those planes (null: all nplanes)
   const float2* tw;
 };
 
@@ -94,8 +99,27 @@ struct ZArgs {
   long long Tc;                // elements per tensor component
   long long Tz;                // (Ly/2+1) * P
   const int2* zcol;            // launch order of columns: (ky position, ky)
+  const int* ext;              // device [zlo, zhi) of the target planes
+  int in_ext, out_ext;         // input / output planes restricted to ext (else 0..n_in / 0..n_out)
   const float2* tw;
 };
+constexpr int kDirectPlanes = 4;  // at most this many planes: direct DFT instead of the z FFT
+
+// Direct z convolution (few planes on one side), in place on B[slot][z][Ly][P].
+constexpr int kDirectPlanesMax = 8;
+struct ZDirArgs {
+  float2* buf;
+  long long cstride, zstride;
+  int P, Ly;
+  int nin, nout, in_slot[3], out_slot[3];
+  float coef[3][3][6];
+  int need[3][3];
+  const float* Tz;        // [6][nz][Ly/2+1][P], x/y transformed, z offset
+  long long Tc, Tdz;      // per component, per offset
+  const int2* zcol;
+  int zin0, nzin, zout0, nzout;
+};
+int launch_zdir(const ZDirArgs& a, cudaStream_t s);
 
 int launch_xfwd(int L, const XFwdArgs& a, int ncomp, cudaStream_t s);
 int launch_xinv(int L, const XInvArgs& a, cudaStream_t s);
@@ -107,11 +131,13 @@ size_t zpass_smem(int L);
 
 // Tensor setup (float64) -- tensor.cu
 int tensor_setup(int nx, int ny, int nz, const double d[3], int Lx, int Ly, int Lz, int P, float* T_out,
-                 double* octant_host /* optional [6][nz][ny][nx] */, cudaStream_t s, char* err, int errlen);
+                 float* Tz_out /* optional [6][nz][Ly/2+1][P] */, double* octant_host /* optional [6][nz][ny][nx] */,
+                 cudaStream_t s, char* err, int errlen);
 
 // Small kernels -- misc.cu
 int launch_j_finalize(const double* part, int n, double* J, cudaStream_t s);
 int launch_absmax(const float* G, long long n, unsigned int* gmax, cudaStream_t s);
+int launch_mask_extent(const uint8_t* mask, int nz, long long plane, int* ext, cudaStream_t s);
 int launch_update(float* rho, const float* G, long long n, float alpha, int normalize, const unsigned int* gmax,
                   cudaStream_t s);
 

@@ -1,16 +1,20 @@
 // x-axis passes of the stray-field convolution (Sec. "Discretization", Eq. (convolution)).
 //
 // Forward: real rows (rho^p, rho^p M0_c of Sec. "Methodology" Eq. 2, or a given
-// vector component) are zero padded from nx to L (implicitly: the first DIF
-// stage reads only x < nx) and transformed two rows at a time (row a + i row b),
-// then separated into the half spectra kx = 0..L/2. One block per (32-row tile,
-// component).
+// vector component) are zero padded from nx to L (the first DIF stage reads only
+// x < nx) and transformed two rows at a time (row a + i row b), then separated
+// into the half spectra kx = 0..L/2. One block per (32-row tile, component).
 // Inverse: half spectra are extended by Hermitian symmetry, two rows are
 // recovered from one complex inverse transform, cropped to nx, and handed to a
-// sink: write H; the least-squares objective and dJ/dH fused with the forward x
-// transform of the adjoint source (per component: both are separable in c); or
-// the chain rule dJ/drho = p rho^(p-1) M0 . (D g) (Sec. "Methodology",
+// sink: write H; the least-squares objective and dJ/dH, whose zero-padded
+// forward x transform (the adjoint source) starts in the same registers; or the
+// chain rule dJ/drho = p rho^(p-1) M0 . (D g) (Sec. "Methodology",
 // Eqs. (adjoint1)-(adjoint2)).
+// The first forward and the last inverse stage map consecutive threads to
+// consecutive x of one row pair, so global rows are read and written in
+// 64-byte runs straight from registers; the half-spectrum rows are read and
+// written with consecutive threads on consecutive kx. The swizzled tile keeps
+// both orientations free of bank conflicts, and no staging buffer is needed.
 #include "fft.cuh"
 #include "internal.h"
 
@@ -19,15 +23,6 @@ namespace tmk {
 namespace {
 
 constexpr int ROWS = 2 * TB;  // real rows per block
-constexpr int CK = 32;        // kx columns per output chunk
-constexpr int CKP = CK + 1;   // odd pitch of the chunk staging
-
-template <int L>
-struct XSmem {
-  static constexpr int SP = (L / 2) | 1;  // odd pitch of a staged real row (>= nx)
-  static constexpr size_t base = (size_t)(L + L * TB + 2 * TB * CKP) * sizeof(float2);
-  static constexpr size_t rows = (size_t)ROWS * SP * sizeof(float);
-};
 
 __device__ __forceinline__ float ipow(float r, float p) {
   if (p == 3.0f) return r * r * r;
@@ -42,203 +37,305 @@ __device__ __forceinline__ float dpow(float r, float p) {  // p r^(p-1)
   return p * powf(r, p - 1.0f);
 }
 
-// Forward x transform of 2*TB staged real rows (stage[rr * SP + x], x < nx) and
-// write of the half spectra through out(rr, k, value) for k < P (zero beyond L/2).
-template <int L, typename OUT>
-__device__ __forceinline__ void xfwd_from_stage(cx<float>* tile, const cx<float>* tw, const float* stage, int nx,
-                                                int P, cx<float>* chA, cx<float>* chB, OUT out) {
-  constexpr int SP = XSmem<L>::SP;
-  constexpr int S = plan_stages(L);
-  dif_stage0_load<float, L, kNT>(tile, tw, [&](int pos, int line) {
-    return pos < nx ? mk(stage[(2 * line) * SP + pos], stage[(2 * line + 1) * SP + pos]) : zero<float>();
-  });
-  __syncthreads();
-  DifRange<float, L, kNT, 1, S>::run(tile, tw);
-  for (int k0 = 0; k0 < P; k0 += CK) {
-    for (int i = threadIdx.x; i < TB * CK; i += kNT) {
-      const int line = i % TB, kk = i / TB, k = k0 + kk;
-      cx<float> A = zero<float>(), B = zero<float>();
-      if (k <= L / 2) {
-        const cx<float> Z = tile[pos_of_k<L>(k) * TB + line];
-        const cx<float> Zm = tile[pos_of_k<L>((L - k) % L) * TB + line];
-        A = mk(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));  // (Z + conj Zm) / 2
-        B = mk(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x));  // (Z - conj Zm) / 2i
-      }
-      chA[line * CKP + kk] = A;
-      chB[line * CKP + kk] = B;
+// Units of plan stage 0 with x fastest: unit u -> (j = u % M, line = u / M),
+// positions j + q M (q < R). Forward reads go through ld(x, line).
+template <int L, typename LD>
+__device__ __forceinline__ void xdif0(cx<float>* tile, const cx<float>* tw, LD ld) {
+  using S0 = StageShape<L, 0>;
+  constexpr int R = S0::R, M = S0::M, NU = M * TB, ITER = (NU + kNT - 1) / kNT;
+  cx<float> v[ITER][R];
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * kNT + threadIdx.x;
+    if (NU % kNT == 0 || u < NU) {
+      const int j = u % M, line = u / M;
+#pragma unroll
+      for (int q = 0; q < R; q++) v[it][q] = ld(j + q * M, line);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < ROWS * CK; i += kNT) {
-      const int rr = i / CK, kk = i % CK, k = k0 + kk;
-      if (k < P) out(rr, k, (rr & 1) ? chB[(rr >> 1) * CKP + kk] : chA[(rr >> 1) * CKP + kk]);
+  }
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * kNT + threadIdx.x;
+    if (NU % kNT == 0 || u < NU) {
+      const int j = u % M, line = u / M;
+      Dft<float, R, false>::run(v[it]);
+      apply_twiddles<float, L, 0, false>(v[it], j, tw);
+#pragma unroll
+      for (int q = 0; q < R; q++) tile[tix(j + q * M, line)] = v[it][q];
     }
-    __syncthreads();
   }
 }
 
-// Inverse x transform of the spectra of 2*TB rows (slot pointer `in`, row pitch P)
-// into staged real rows dst[rr * SP + x], x < nx.
-template <int L>
-__device__ __forceinline__ void xinv_to_stage(cx<float>* tile, const cx<float>* tw, const cx<float>* in, int row0,
-                                              int rows, int nx, int P, cx<float>* chA, cx<float>* chB, float* dst) {
-  constexpr int SP = XSmem<L>::SP;
-  constexpr int S = plan_stages(L);
-  for (int k0 = 0; k0 <= L / 2; k0 += CK) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < ROWS * CK; i += kNT) {
-      const int rr = i / CK, kk = i % CK, k = k0 + kk, row = row0 + rr;
-      cx<float> v = zero<float>();
-      if (row < rows && k <= L / 2) v = in[(long long)row * P + k];
-      ((rr & 1) ? chB : chA)[(rr >> 1) * CKP + kk] = v;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < TB * CK; i += kNT) {
-      const int line = i % TB, kk = i / TB, k = k0 + kk;
-      if (k > L / 2) continue;
-      const cx<float> A = chA[line * CKP + kk], B = chB[line * CKP + kk];
-      if (k == 0 || k == L / 2) {
-        tile[pos_of_k<L>(k) * TB + line] = mk(A.x, B.x);
-      } else {
-        tile[pos_of_k<L>(k) * TB + line] = mk(A.x - B.y, A.y + B.x);      // A + iB
-        tile[pos_of_k<L>(L - k) * TB + line] = mk(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
+// Last inverse stage (plan stage 0) with x fastest; fn(it, j, line, v[R]) receives the
+// natural-order outputs at x = j + q M and may write new stage-0 inputs back into v
+// and return true, in which case the forward stage 0 is applied to v in place.
+template <int L, typename FN>
+__device__ __forceinline__ void xdit0(cx<float>* tile, const cx<float>* tw, FN fn) {
+  using S0 = StageShape<L, 0>;
+  constexpr int R = S0::R, M = S0::M, NU = M * TB, ITER = (NU + kNT - 1) / kNT;
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * kNT + threadIdx.x;
+    if (NU % kNT == 0 || u < NU) {
+      const int j = u % M, line = u / M;
+      cx<float> v[R];
+#pragma unroll
+      for (int q = 0; q < R; q++) v[q] = tile[tix(j + q * M, line)];
+      apply_twiddles<float, L, 0, true>(v, j, tw);
+      Dft<float, R, true>::run(v);
+      if (fn(it, j, line, v)) {
+        Dft<float, R, false>::run(v);
+        apply_twiddles<float, L, 0, false>(v, j, tw);
+#pragma unroll
+        for (int q = 0; q < R; q++) tile[tix(j + q * M, line)] = v[q];
       }
     }
   }
-  __syncthreads();
-  DitRange<float, L, kNT, 1, S>::run(tile, tw);
-  dit_stage0_store<float, L, kNT>(tile, tw, [&](int pos, int line, cx<float> v) {
-    if (pos < nx) {
-      dst[(2 * line) * SP + pos] = v.x;
-      dst[(2 * line + 1) * SP + pos] = v.y;
+}
+
+// Half spectra of the 2*TB rows from the finished forward transform: kx fastest.
+template <int L, typename OUT>
+__device__ __forceinline__ void xseparate(const cx<float>* tile, int P, OUT out) {
+  for (int i = threadIdx.x; i < TB * P; i += kNT) {
+    const int line = i / P, k = i - line * P;
+    cx<float> A = zero<float>(), B = zero<float>();
+    if (k <= L / 2) {
+      const cx<float> Z = tile[tix(pos_of_k<L>(k), line)];
+      const cx<float> Zm = tile[tix(pos_of_k<L>((L - k) % L), line)];
+      A = mk(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));  // (Z + conj Zm) / 2
+      B = mk(0.5f * (Z.y + Zm.y), 0.5f * (Zm.x - Z.x));  // (Z - conj Zm) / 2i
     }
-  });
-  __syncthreads();
+    out(2 * line, k, A);
+    out(2 * line + 1, k, B);
+  }
+}
+
+// Hermitian extension of the half spectra of 2*TB rows into the tile (DIF positions).
+template <int L>
+__device__ __forceinline__ void xhermitian(cx<float>* tile, const cx<float>* in, int row0, int rows, int P) {
+  constexpr int K = L / 2 + 1;
+  for (int i = threadIdx.x; i < TB * K; i += kNT) {
+    const int line = i / K, k = i - line * K;
+    const int ra = row0 + 2 * line, rb = ra + 1;
+    const cx<float> A = ra < rows ? in[(long long)ra * P + k] : zero<float>();
+    const cx<float> B = rb < rows ? in[(long long)rb * P + k] : zero<float>();
+    if (k == 0 || k == L / 2) {
+      tile[tix(pos_of_k<L>(k), line)] = mk(A.x, B.x);
+    } else {
+      tile[tix(pos_of_k<L>(k), line)] = mk(A.x - B.y, A.y + B.x);      // A + iB
+      tile[tix(pos_of_k<L>(L - k), line)] = mk(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
+    }
+  }
 }
 
 template <int L>
 __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
-  constexpr int SP = XSmem<L>::SP;
+  constexpr int S = plan_stages(L);
   extern __shared__ __align__(16) unsigned char smem[];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
   cx<float>* tile = tw + L;
-  cx<float>* chA = tile + L * TB;
-  cx<float>* chB = chA + TB * CKP;
-  float* stage = reinterpret_cast<float*>(chB + TB * CKP);
   load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
-
+  __syncthreads();
   const int row0 = blockIdx.x * ROWS;
   const int c = a.comp[blockIdx.y];
-  cx<float>* out = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[blockIdx.y] * a.out_cstride;
-  for (int i = threadIdx.x; i < ROWS * a.nx; i += kNT) {
-    const int rr = i / a.nx, x = i - rr * a.nx, row = row0 + rr;
-    float v = 0.0f;
-    if (row < a.rows) {
-      const long long o = (long long)row * a.nx + x;
+  xdif0<L>(tile, tw, [&](int x, int line) {
+    const int ra = row0 + 2 * line, rb = ra + 1;
+    float va = 0.0f, vb = 0.0f;
+    if (x < a.nx) {
+      const long long oa = (long long)ra * a.nx + x, ob = oa + a.nx;
       if (a.src == SRC_VECTOR) {
-        v = a.vec[c * a.vec_cstride + o];
+        if (ra < a.rows) va = a.vec[c * a.vec_cstride + oa];
+        if (rb < a.rows) vb = a.vec[c * a.vec_cstride + ob];
       } else {
-        v = ipow(a.rho[o], a.p);
-        if (a.src == SRC_RHO_M0) v *= a.M0v[c * a.M0v_cstride + o];
+        if (ra < a.rows) va = ipow(a.rho[oa], a.p);
+        if (rb < a.rows) vb = ipow(a.rho[ob], a.p);
+        if (a.src == SRC_RHO_M0) {
+          if (ra < a.rows) va *= a.M0v[c * a.M0v_cstride + oa];
+          if (rb < a.rows) vb *= a.M0v[c * a.M0v_cstride + ob];
+        }
       }
     }
-    stage[rr * SP + x] = v;
-  }
+    return mk(va, vb);
+  });
   __syncthreads();
-  xfwd_from_stage<L>(tile, tw, stage, a.nx, a.P, chA, chB, [&](int rr, int k, cx<float> v) {
+  DifRange<float, L, kNT, 1, S, true>::run(tile, tw);
+  cx<float>* out = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[blockIdx.y] * a.out_cstride;
+  xseparate<L>(tile, a.P, [&](int rr, int k, cx<float> v) {
     const int row = row0 + rr;
     if (row < a.rows) out[(long long)row * a.P + k] = v;
   });
 }
 
-template <int L>
-__global__ void __launch_bounds__(kNT, 2) k_xinv(XInvArgs a) {
-  constexpr int SP = XSmem<L>::SP;
+template <int L, int SINK, int MINB>
+__global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
+  constexpr int S = plan_stages(L);
   extern __shared__ __align__(16) unsigned char smem[];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
   cx<float>* tile = tw + L;
-  cx<float>* chA = tile + L * TB;
-  cx<float>* chB = chA + TB * CKP;
-  float* rows = reinterpret_cast<float*>(chB + TB * CKP);  // [ROWS][SP]
-  float* acc = rows + ROWS * SP;                            // [ROWS][SP], CHAIN with ncomp > 1
   __shared__ double red[kNT / 32];
-  __shared__ int any_mask;
   load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
-  const int row0 = blockIdx.x * ROWS;
+  const int row0 = a.row_base + blockIdx.x * ROWS;
   const cx<float>* in0 = reinterpret_cast<const cx<float>*>(a.in);
 
-  if (a.sink == SINK_CHAIN) {
-    for (int j = 0; j < a.ncomp; j++) {
-      xinv_to_stage<L>(tile, tw, in0 + a.in_slot[j] * a.in_cstride, row0, a.rows, a.nx, a.P, chA, chB, rows);
-      if (a.ncomp > 1) {  // acc += M0_c . D_c (varying M0, uncontracted slots)
-        for (int i = threadIdx.x; i < ROWS * a.nx; i += kNT) {
-          const int rr = i / a.nx, x = i - rr * a.nx, row = row0 + rr;
-          float m = 0.0f;
-          if (row < a.rows) m = a.M0v[a.comp[j] * a.M0v_cstride + (long long)row * a.nx + x];
-          const float t = m * rows[rr * SP + x];
-          acc[rr * SP + x] = (j == 0) ? t : acc[rr * SP + x] + t;
+  if constexpr (SINK == SINK_CHAIN && MINB == 3) {
+    // one slot, already contracted with the constant M0: G = p rho^(p-1) D
+    __syncthreads();
+    xhermitian<L>(tile, in0 + a.in_slot[0] * a.in_cstride, row0, a.rows, a.P);
+    __syncthreads();
+    DitRange<float, L, kNT, 1, S, true>::run(tile, tw);
+    float gm = 0.0f;
+    xdit0<L>(tile, tw, [&](int, int j, int line, cx<float>* v) {
+      constexpr int R = StageShape<L, 0>::R, M = StageShape<L, 0>::M;
+      const int ra = row0 + 2 * line;
+#pragma unroll
+      for (int q = 0; q < R; q++) {
+        const int x = j + q * M;
+        if (x >= a.nx) continue;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int row = ra + h;
+          if (row >= a.rows) continue;
+          const long long o = (long long)row * a.nx + x;
+          const float G = dpow(a.rho[o], a.p) * (h ? v[q].y : v[q].x);
+          a.G[o] = G;
+          gm = fmaxf(gm, fabsf(G));
         }
       }
+      return false;
+    });
+    for (int off = 16; off > 0; off >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, off));
+    if ((threadIdx.x & 31) == 0 && gm > 0.0f) atomicMax(a.gmax, __float_as_uint(gm));
+    return;
+  } else if constexpr (SINK == SINK_CHAIN) {
+    using S0 = StageShape<L, 0>;
+    constexpr int R = S0::R, M = S0::M, NU = M * TB, ITER = (NU + kNT - 1) / kNT;
+    float acc[ITER][R][2];
+#pragma unroll
+    for (int it = 0; it < ITER; it++)
+#pragma unroll
+      for (int q = 0; q < R; q++) acc[it][q][0] = acc[it][q][1] = 0.0f;
+    for (int jc = 0; jc < a.ncomp; jc++) {
+      __syncthreads();
+      xhermitian<L>(tile, in0 + a.in_slot[jc] * a.in_cstride, row0, a.rows, a.P);
+      __syncthreads();
+      DitRange<float, L, kNT, 1, S, true>::run(tile, tw);
+      const int c = a.comp[jc];
+      xdit0<L>(tile, tw, [&](int it, int j, int line, cx<float>* v) {
+        const int ra = row0 + 2 * line, rb = ra + 1;
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+          const int x = j + q * M;
+          float ma = 1.0f, mb = 1.0f;  // contracted slot: coefficient 1
+          if (a.M0v && x < a.nx) {
+            if (ra < a.rows) ma = a.M0v[c * a.M0v_cstride + (long long)ra * a.nx + x];
+            if (rb < a.rows) mb = a.M0v[c * a.M0v_cstride + (long long)rb * a.nx + x];
+          }
+          acc[it][q][0] += ma * v[q].x;
+          acc[it][q][1] += mb * v[q].y;
+        }
+        return false;
+      });
     }
-    const float* dot = a.ncomp > 1 ? acc : rows;
     float gm = 0.0f;
-    for (int i = threadIdx.x; i < ROWS * a.nx; i += kNT) {
-      const int rr = i / a.nx, x = i - rr * a.nx, row = row0 + rr;
-      if (row >= a.rows) continue;
-      const long long o = (long long)row * a.nx + x;
-      const float G = dpow(a.rho[o], a.p) * dot[rr * SP + x];
-      a.G[o] = G;
-      gm = fmaxf(gm, fabsf(G));
+#pragma unroll
+    for (int it = 0; it < ITER; it++) {
+      const int u = it * kNT + threadIdx.x;
+      if (NU % kNT == 0 || u < NU) {
+        const int j = u % M, line = u / M;
+        const int ra = row0 + 2 * line;
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+          const int x = j + q * M;
+          if (x >= a.nx) continue;
+#pragma unroll
+          for (int h = 0; h < 2; h++) {
+            const int row = ra + h;
+            if (row >= a.rows) continue;
+            const long long o = (long long)row * a.nx + x;
+            const float G = dpow(a.rho[o], a.p) * acc[it][q][h];
+            a.G[o] = G;
+            gm = fmaxf(gm, fabsf(G));
+          }
+        }
+      }
     }
     for (int off = 16; off > 0; off >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, off));
     if ((threadIdx.x & 31) == 0 && gm > 0.0f) atomicMax(a.gmax, __float_as_uint(gm));
     return;
-  }
-
-  const int j = blockIdx.y, c = a.comp[j];
-  const cx<float>* in = in0 + a.in_slot[j] * a.in_cstride;
-  xinv_to_stage<L>(tile, tw, in, row0, a.rows, a.nx, a.P, chA, chB, rows);
-
-  if (a.sink == SINK_FIELD) {
-    for (int i = threadIdx.x; i < ROWS * a.nx; i += kNT) {
-      const int rr = i / a.nx, x = i - rr * a.nx, row = row0 + rr;
-      if (row < a.rows) a.H[c * a.H_cstride + (long long)row * a.nx + x] = rows[rr * SP + x];
-    }
-    return;
-  }
-
-  // SINK_OBJECTIVE: J partial and g_c = 2 w_c (H_c - Ht_c) on the mask, in place in rows
-  const float wc = a.w[c];
-  if (threadIdx.x == 0) any_mask = 0;
-  __syncthreads();
-  double jacc = 0.0;
-  int mine = 0;
-  for (int i = threadIdx.x; i < ROWS * a.nx; i += kNT) {
-    const int rr = i / a.nx, x = i - rr * a.nx, row = row0 + rr;
-    float g = 0.0f;
-    if (row < a.rows) {
-      const long long o = (long long)row * a.nx + x;
-      const float h = rows[rr * SP + x];
-      if (a.H) a.H[c * a.H_cstride + o] = h;
-      if (wc != 0.0f && a.mask[o]) {
-        mine = 1;
-        const float r = h - (a.Ht ? a.Ht[c * a.Ht_cstride + o] : a.Htc[c]);
-        jacc += (double)wc * (double)r * (double)r;
-        g = 2.0f * wc * r;
+  } else {
+  const int jc = blockIdx.y, c = a.comp[jc];
+  const cx<float>* in = in0 + a.in_slot[jc] * a.in_cstride;
+  if constexpr (SINK == SINK_OBJECTIVE) {
+    if (a.ext) {  // only the rows of the target planes carry H (and the adjoint source)
+      const long long lo = (long long)a.ext[0] * a.ny, hi = (long long)a.ext[1] * a.ny;
+      if (row0 + ROWS <= lo || row0 >= hi) {
+        if (threadIdx.x == 0) a.Jpart[jc * gridDim.x + blockIdx.x] = 0.0;
+        return;
       }
     }
-    rows[rr * SP + x] = g;
   }
+  __syncthreads();
+  xhermitian<L>(tile, in, row0, a.rows, a.P);
+  __syncthreads();
+  DitRange<float, L, kNT, 1, S, true>::run(tile, tw);
+
+  if constexpr (SINK == SINK_FIELD) {
+    xdit0<L>(tile, tw, [&](int, int j, int line, cx<float>* v) {
+      const int ra = row0 + 2 * line, rb = ra + 1;
+      constexpr int R = StageShape<L, 0>::R, M = StageShape<L, 0>::M;
+#pragma unroll
+      for (int q = 0; q < R; q++) {
+        const int x = j + q * M;
+        if (x >= a.nx) continue;
+        if (ra < a.rows) a.H[c * a.H_cstride + (long long)ra * a.nx + x] = v[q].x;
+        if (rb < a.rows) a.H[c * a.H_cstride + (long long)rb * a.nx + x] = v[q].y;
+      }
+      return false;
+    });
+    return;
+  } else {
+  // SINK_OBJECTIVE: J partial; g_c = 2 w_c (H_c - Ht_c) on the mask, zero elsewhere and
+  // for x >= nx (the padding); the forward stage 0 of the adjoint source runs on g
+  const float wc = a.w[c];
+  double jacc = 0.0;
+  int mine = 0;
+  xdit0<L>(tile, tw, [&](int, int j, int line, cx<float>* v) {
+    const int ra = row0 + 2 * line, rb = ra + 1;
+    constexpr int R = StageShape<L, 0>::R, M = StageShape<L, 0>::M;
+#pragma unroll
+    for (int q = 0; q < R; q++) {
+      const int x = j + q * M;
+      float g[2] = {0.0f, 0.0f};
+      if (x < a.nx) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int row = ra + h;
+          if (row >= a.rows) continue;
+          const long long o = (long long)row * a.nx + x;
+          const float hv = h ? v[q].y : v[q].x;
+          if (a.H) a.H[c * a.H_cstride + o] = hv;
+          if (wc != 0.0f && a.mask[o]) {
+            mine = 1;
+            const float r = hv - (a.Ht ? a.Ht[c * a.Ht_cstride + o] : a.Htc[c]);
+            jacc += (double)wc * (double)r * (double)r;
+            g[h] = 2.0f * wc * r;
+          }
+        }
+      }
+      v[q] = mk(g[0], g[1]);
+    }
+    return true;
+  });
   for (int off = 16; off > 0; off >>= 1) jacc += __shfl_xor_sync(0xffffffffu, jacc, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = jacc;
-  if (mine) any_mask = 1;
-  __syncthreads();
+  const int any_mask = __syncthreads_or(mine);
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < kNT / 32; w++) s += red[w];
-    a.Jpart[j * gridDim.x + blockIdx.x] = s;
+    a.Jpart[jc * gridDim.x + blockIdx.x] = s;
   }
   if (!a.adj_out) return;
-  cx<float>* adj = reinterpret_cast<cx<float>*>(a.adj_out) + a.in_slot[j] * a.in_cstride;
+  cx<float>* adj = reinterpret_cast<cx<float>*>(a.adj_out) + a.in_slot[jc] * a.in_cstride;
   if (!any_mask) {  // the adjoint source vanishes on all rows of this block
     for (int i = threadIdx.x; i < ROWS * a.P; i += kNT) {
       const int rr = i / a.P, k = i - rr * a.P, row = row0 + rr;
@@ -246,15 +343,23 @@ __global__ void __launch_bounds__(kNT, 2) k_xinv(XInvArgs a) {
     }
     return;
   }
-  xfwd_from_stage<L>(tile, tw, rows, a.nx, a.P, chA, chB, [&](int rr, int k, cx<float> v) {
+  DifRange<float, L, kNT, 1, S, true>::run(tile, tw);
+  xseparate<L>(tile, a.P, [&](int rr, int k, cx<float> v) {
     const int row = row0 + rr;
     if (row < a.rows) adj[(long long)row * a.P + k] = v;
   });
+  }
+  }
+}
+
+template <int L>
+size_t xsmem() {
+  return (size_t)(L + L * TB) * sizeof(float2);
 }
 
 template <int L>
 int run_xfwd(const XFwdArgs& a, int ncomp, cudaStream_t s) {
-  const size_t sm = XSmem<L>::base + XSmem<L>::rows;
+  const size_t sm = xsmem<L>();
   static bool init = false;
   if (!init) {
     if (cudaFuncSetAttribute(k_xfwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
@@ -266,21 +371,28 @@ int run_xfwd(const XFwdArgs& a, int ncomp, cudaStream_t s) {
   k_xfwd<L><<<dim3(blocks, ncomp), kNT, sm, s>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
-template <int L>
-int run_xinv(const XInvArgs& a, cudaStream_t s) {
-  const size_t smax = XSmem<L>::base + 2 * XSmem<L>::rows;
-  const size_t sm = XSmem<L>::base + ((a.sink == SINK_CHAIN && a.ncomp > 1) ? 2 : 1) * XSmem<L>::rows;
+template <int L, int SINK, int MINB>
+int run_xinv_sink(const XInvArgs& a, cudaStream_t s) {
+  const size_t sm = xsmem<L>();
   static bool init = false;
   if (!init) {
-    if (cudaFuncSetAttribute(k_xinv<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_xinv<L, SINK, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        cudaSuccess)
       return -1;
     init = true;
   }
-  const int blocks = (a.rows + ROWS - 1) / ROWS;
-  if (blocks == 0 || a.ncomp == 0) return 0;
-  const int gy = a.sink == SINK_CHAIN ? 1 : a.ncomp;
-  k_xinv<L><<<dim3(blocks, gy), kNT, sm, s>>>(a);
+  const int blocks = (a.rows - a.row_base + ROWS - 1) / ROWS;
+  if (blocks <= 0 || a.ncomp == 0) return 0;
+  const int gy = SINK == SINK_CHAIN ? 1 : a.ncomp;
+  k_xinv<L, SINK, MINB><<<dim3(blocks, gy), kNT, sm, s>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+template <int L>
+int run_xinv(const XInvArgs& a, cudaStream_t s) {
+  if (a.sink == SINK_FIELD) return run_xinv_sink<L, SINK_FIELD, 3>(a, s);
+  if (a.sink == SINK_OBJECTIVE) return run_xinv_sink<L, SINK_OBJECTIVE, 2>(a, s);
+  if (a.ncomp == 1 && a.M0v == nullptr) return run_xinv_sink<L, SINK_CHAIN, 3>(a, s);  // contracted slot
+  return run_xinv_sink<L, SINK_CHAIN, 1>(a, s);
 }
 
 }  // namespace

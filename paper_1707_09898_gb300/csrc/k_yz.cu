@@ -32,7 +32,12 @@ __global__ void __launch_bounds__(kNT, 3) k_ypass(YArgs a) {
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
   cx<float>* tile = tw + L;
   load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
-  const int chunk = blockIdx.x, z = blockIdx.y;
+  const int chunk = blockIdx.x;
+  int z = a.z0 + blockIdx.y;
+  if (a.ext) {
+    z += a.ext[0];
+    if (z >= a.ext[1]) return;
+  }
   const cx<float>* in = reinterpret_cast<const cx<float>*>(a.in) + a.in_slot[blockIdx.z] * a.in_cstride +
                         z * a.in_zstride + chunk * TB;
   cx<float>* out = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[blockIdx.z] * a.out_cstride +
@@ -55,34 +60,103 @@ __global__ void __launch_bounds__(kNT, 3) k_ypass(YArgs a) {
   }
 }
 
-// The needed unique components of N^ at (kz, ky, kx) with the parity signs of
-// the folded storage applied (kx <= L/2 always, so only ky and kz flip signs).
-struct TensorAt {
-  const float* T;  // at (kyf, kx): T + kyf * P + kx
+// Tensor factor s(k) = sum_c coef[c] N^_c(k) for the column (ky, kx): the folded
+// storage holds kx, ky, kz in [0, L/2]; odd components change sign under
+// ky -> Ly - ky and kz -> Lz - kz (kx <= Lx/2 always).
+struct TensorCol {
+  const float* T;  // T + kyf * P + kx
   long long Tc, Tz;
-  __device__ __forceinline__ void load(int kzf, float sy, float sz, int need, float n[6]) const {
+  float sy;
+  int need, single;  // bitmask of components; index if exactly one is needed, else -1
+  float coef[6];
+  __device__ __forceinline__ float at(int kz, int Lz) const {
+    const bool lo = kz <= Lz / 2;
+    const int kzf = lo ? kz : Lz - kz;
+    const float sz = lo ? 1.0f : -1.0f;
     const float* t = T + kzf * Tz;
-    n[0] = (need & 1) ? t[0] : 0.0f;
-    n[1] = (need & 2) ? t[Tc] : 0.0f;
-    n[2] = (need & 4) ? t[2 * Tc] : 0.0f;
-    n[3] = (need & 8) ? sy * t[3 * Tc] : 0.0f;
-    n[4] = (need & 16) ? sz * t[4 * Tc] : 0.0f;
-    n[5] = (need & 32) ? sy * sz * t[5 * Tc] : 0.0f;
+    if (single >= 0) {
+      const float sg = single == 3 ? sy : single == 4 ? sz : single == 5 ? sy * sz : 1.0f;
+      return coef[single] * sg * t[single * Tc];
+    }
+    float r = 0.0f;
+    if (need & 1) r += coef[0] * t[0];
+    if (need & 2) r += coef[1] * t[Tc];
+    if (need & 4) r += coef[2] * t[2 * Tc];
+    if (need & 8) r += coef[3] * sy * t[3 * Tc];
+    if (need & 16) r += coef[4] * sz * t[4 * Tc];
+    if (need & 32) r += coef[5] * sy * sz * t[5 * Tc];
+    return r;
   }
 };
 
-__device__ __forceinline__ float contract6(const float* c, const float* n) {
-  return c[0] * n[0] + c[1] * n[1] + c[2] * n[2] + c[3] * n[3] + c[4] * n[4] + c[5] * n[5];
+__device__ __forceinline__ TensorCol make_tcol(const ZArgs& a, int o, int i, int kyf, float sy, long long kx0) {
+  TensorCol t;
+  t.T = a.T + kyf * (long long)a.P + kx0;
+  t.Tc = a.Tc;
+  t.Tz = a.Tz;
+  t.sy = sy;
+  t.need = 0;
+#pragma unroll
+  for (int c = 0; c < 6; c++) {
+    t.coef[c] = a.coef[o][i][c];
+    if (t.coef[c] != 0.0f) t.need |= 1 << c;
+  }
+  t.single = (t.need != 0 && (t.need & (t.need - 1)) == 0) ? __ffs(t.need) - 1 : -1;
+  return t;
+}
+
+// Whole forward spectrum from the few nonzero planes z in [lo, hi) by direct
+// DFT: X(kz) = sum_z x(z) W_L^(kz z), written at the DIF positions of the tile.
+template <int L>
+__device__ __forceinline__ void direct_in(cx<float>* tile, const cx<float>* tw, const cx<float>* col,
+                                          long long zstride, int lo, int hi, cx<float> (*mz)[TB]) {
+  const int np = hi - lo;
+  if (threadIdx.x < kDirectPlanes * TB) {
+    const int p = threadIdx.x / TB, line = threadIdx.x % TB;
+    mz[p][line] = p < np ? col[(long long)(lo + p) * zstride + line] : zero<float>();
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < L * TB; i += kNT) {
+    const int pos = i / TB, line = i % TB;
+    const int kz = k_of_pos<L>(pos);
+    cx<float> acc = zero<float>();
+    for (int p = 0; p < np; p++) acc = acc + cmul(mz[p][line], tw[(kz * (lo + p)) % L]);
+    tile[i] = acc;
+  }
+}
+
+// Inverse transform evaluated only at the few planes z in [lo, hi):
+// x(z) = sum_kz X(kz) W_L^(-kz z), from the whole spectrum in the tile.
+template <int L>
+__device__ __forceinline__ void direct_out(const cx<float>* tile, const cx<float>* tw, cx<float>* col,
+                                           long long zstride, int lo, int hi, cx<float> (*part)[TB]) {
+  constexpr int PARTS = kNT / TB;
+  const int line = threadIdx.x % TB, pr = threadIdx.x / TB;
+  for (int z = lo; z < hi; z++) {
+    cx<float> acc = zero<float>();
+    for (int pos = pr; pos < L; pos += PARTS) {
+      const int kz = k_of_pos<L>(pos);
+      acc = acc + cmulc(tile[pos * TB + line], tw[(kz * z) % L]);
+    }
+    part[pr][line] = acc;
+    __syncthreads();
+    if (threadIdx.x < TB) {
+      cx<float> s = zero<float>();
+      for (int q = 0; q < PARTS; q++) s = s + part[q][threadIdx.x];
+      col[(long long)z * zstride + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
 }
 
 // One input slot, one output per block (grid.z = output index).
 template <int L>
 __global__ void __launch_bounds__(kNT, 3) k_z1(ZArgs a) {
   constexpr int S = plan_stages(L);
-  constexpr int LH = L / 2;
   extern __shared__ __align__(16) unsigned char smem[];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
   cx<float>* tile = tw + L;
+  __shared__ cx<float> small[kNT / TB][TB];
   load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
   const int chunk = blockIdx.x, o = blockIdx.z;
   const int2 col = a.zcol[blockIdx.y];  // (ky position, ky)
@@ -91,21 +165,34 @@ __global__ void __launch_bounds__(kNT, 3) k_z1(ZArgs a) {
   const long long colo = (long long)col.x * a.P + chunk * TB;
   const cx<float>* in = reinterpret_cast<const cx<float>*>(a.buf) + a.in_slot[0] * a.cstride + colo;
   cx<float>* out = reinterpret_cast<cx<float>*>(a.buf) + a.out_slot[o] * a.cstride + colo;
-  float coef[6];
-#pragma unroll
-  for (int c = 0; c < 6; c++) coef[c] = a.coef[o][0][c];
-  const int need = a.need[o];
+  int ilo = 0, ihi = a.n_in, olo = 0, ohi = a.n_out;
+  if (a.in_ext) {
+    ilo = max(a.ext[0], 0);
+    ihi = min(a.ext[1], a.n_in);
+  }
+  if (a.out_ext) {
+    olo = max(a.ext[0], 0);
+    ohi = min(a.ext[1], a.n_out);
+  }
+  ihi = max(ihi, ilo);
+  ohi = max(ohi, olo);
+  const bool din = ihi - ilo <= kDirectPlanes, dout = ohi - olo <= kDirectPlanes;
+  const TensorCol tcol = make_tcol(a, o, 0, kyf, sy, chunk * TB);
   __syncthreads();
-  dif_stage0_load<float, L, kNT>(tile, tw, [&](int pos, int line) {
-    return pos < a.n_in ? in[pos * a.zstride + line] : zero<float>();
-  });
+  if (din) {
+    direct_in<L>(tile, tw, in, a.zstride, ilo, ihi, small);
+  } else {
+    dif_stage0_load<float, L, kNT>(tile, tw, [&](int pos, int line) {
+      return (pos >= ilo && pos < ihi) ? in[pos * a.zstride + line] : zero<float>();
+    });
+    __syncthreads();
+    DifRange<float, L, kNT, 1, S - 1>::run(tile, tw);
+  }
   __syncthreads();
-  DifRange<float, L, kNT, 1, S - 1>::run(tile, tw);
-  {
+  {  // last forward stage, tensor product, first inverse stage (M = 1: R consecutive positions)
     using SS = StageShape<L, S - 1>;
     constexpr int R = SS::R;
     constexpr int ITER = (SS::NU + kNT - 1) / kNT;
-    TensorAt ta{a.T + kyf * (long long)a.P + chunk * TB, a.Tc, a.Tz};
 #pragma unroll 1
     for (int it = 0; it < ITER; it++) {
       const int u = it * kNT + threadIdx.x;
@@ -114,39 +201,37 @@ __global__ void __launch_bounds__(kNT, 3) k_z1(ZArgs a) {
         cx<float> v[R];
 #pragma unroll
         for (int q = 0; q < R; q++) v[q] = tile[(g * R + q) * TB + line];
-        Dft<float, R, false>::run(v);
-        TensorAt tl = ta;
+        if (!din) Dft<float, R, false>::run(v);
+        TensorCol tl = tcol;
         tl.T += line;
+        const int kb = k_of_group<L>(g);
 #pragma unroll
-        for (int q = 0; q < R; q++) {
-          const int kz = k_of_pos<L>(g * R + q);
-          const int kzf = kz <= LH ? kz : L - kz;
-          const float sz = kz <= LH ? 1.0f : -1.0f;
-          float n[6];
-          tl.load(kzf, sy, sz, need, n);
-          v[q] = scale(v[q], contract6(coef, n));
-        }
-        Dft<float, R, true>::run(v);
+        for (int q = 0; q < R; q++) v[q] = scale(v[q], tl.at(kb + q * (L / R), L));
+        if (!dout) Dft<float, R, true>::run(v);
 #pragma unroll
         for (int q = 0; q < R; q++) tile[(g * R + q) * TB + line] = v[q];
       }
     }
   }
   __syncthreads();
-  DitRange<float, L, kNT, 1, S - 1>::run(tile, tw);
-  dit_stage0_store<float, L, kNT>(tile, tw, [&](int pos, int line, cx<float> v) {
-    if (pos < a.n_out) out[pos * a.zstride + line] = v;
-  });
+  if (dout) {
+    direct_out<L>(tile, tw, out, a.zstride, olo, ohi, small);
+  } else {
+    DitRange<float, L, kNT, 1, S - 1>::run(tile, tw);
+    dit_stage0_store<float, L, kNT>(tile, tw, [&](int pos, int line, cx<float> v) {
+      if (pos >= olo && pos < ohi) out[pos * a.zstride + line] = v;
+    });
+  }
 }
 
 // Several input slots: a cluster of nin blocks per (column tile, column).
 template <int L>
 __global__ void __launch_bounds__(kNT, 2) k_z3(ZArgs a) {
   constexpr int S = plan_stages(L);
-  constexpr int LH = L / 2;
   extern __shared__ __align__(16) unsigned char smem[];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
   cx<float>* tile = tw + L;
+  __shared__ cx<float> small[kNT / TB][TB];
   cg::cluster_group cluster = cg::this_cluster();
   const int r = (int)cluster.block_rank();
   load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
@@ -156,12 +241,28 @@ __global__ void __launch_bounds__(kNT, 2) k_z3(ZArgs a) {
   const float sy = col.y <= a.Ly / 2 ? 1.0f : -1.0f;
   const long long colo = (long long)col.x * a.P + chunk * TB;
   const cx<float>* in = reinterpret_cast<const cx<float>*>(a.buf) + a.in_slot[r] * a.cstride + colo;
+  int ilo = 0, ihi = a.n_in, olo = 0, ohi = a.n_out;
+  if (a.in_ext) {
+    ilo = max(a.ext[0], 0);
+    ihi = min(a.ext[1], a.n_in);
+  }
+  if (a.out_ext) {
+    olo = max(a.ext[0], 0);
+    ohi = min(a.ext[1], a.n_out);
+  }
+  ihi = max(ihi, ilo);
+  ohi = max(ohi, olo);
+  const bool din = ihi - ilo <= kDirectPlanes, dout = ohi - olo <= kDirectPlanes;
   __syncthreads();
-  dif_stage0_load<float, L, kNT>(tile, tw, [&](int pos, int line) {
-    return pos < a.n_in ? in[pos * a.zstride + line] : zero<float>();
-  });
-  __syncthreads();
-  DifRange<float, L, kNT, 1, S>::run(tile, tw);
+  if (din) {
+    direct_in<L>(tile, tw, in, a.zstride, ilo, ihi, small);
+  } else {
+    dif_stage0_load<float, L, kNT>(tile, tw, [&](int pos, int line) {
+      return (pos >= ilo && pos < ihi) ? in[pos * a.zstride + line] : zero<float>();
+    });
+    __syncthreads();
+    DifRange<float, L, kNT, 1, S>::run(tile, tw);
+  }
   cluster.sync();  // every input spectrum of the cluster is complete
 
   using SS = StageShape<L, S - 1>;
@@ -171,38 +272,34 @@ __global__ void __launch_bounds__(kNT, 2) k_z3(ZArgs a) {
   const bool active = r < a.nout;
   if (active) {
     const cx<float>* src[3];
+    TensorCol tc[3];
 #pragma unroll
-    for (int i = 0; i < 3; i++) src[i] = i < a.nin ? cluster.map_shared_rank(tile, i) : tile;
-    float coef[3][6];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-      for (int c = 0; c < 6; c++) coef[i][c] = a.coef[r][i][c];
-    const int need = a.need[r];
-    TensorAt ta{a.T + kyf * (long long)a.P + chunk * TB, a.Tc, a.Tz};
+    for (int i = 0; i < 3; i++) {
+      src[i] = i < a.nin ? cluster.map_shared_rank(tile, i) : tile;
+      tc[i] = make_tcol(a, r, i < a.nin ? i : 0, kyf, sy, chunk * TB);
+    }
 #pragma unroll
     for (int it = 0; it < ITER; it++) {
       const int u = it * kNT + threadIdx.x;
       if (SS::NU % kNT == 0 || u < SS::NU) {
         const int line = u % TB, g = u / TB;
-        TensorAt tl = ta;
-        tl.T += line;
+        const int kb = k_of_group<L>(g);
 #pragma unroll
         for (int q = 0; q < R; q++) {
           const int pos = (g * R + q) * TB + line;
-          const int kz = k_of_pos<L>(g * R + q);
-          const int kzf = kz <= LH ? kz : L - kz;
-          const float sz = kz <= LH ? 1.0f : -1.0f;
-          float n[6];
-          tl.load(kzf, sy, sz, need, n);
+          const int kz = kb + q * (L / R);
           cx<float> acc = zero<float>();
 #pragma unroll
           for (int i = 0; i < 3; i++) {
-            if (i < a.nin) acc = acc + scale(src[i][pos], contract6(coef[i], n));
+            if (i < a.nin) {
+              TensorCol tl = tc[i];
+              tl.T += line;
+              acc = acc + scale(src[i][pos], tl.at(kz, L));
+            }
           }
           res[it][q] = acc;
         }
-        Dft<float, R, true>::run(res[it]);
+        if (!dout) Dft<float, R, true>::run(res[it]);
       }
     }
   }
@@ -218,11 +315,15 @@ __global__ void __launch_bounds__(kNT, 2) k_z3(ZArgs a) {
     }
   }
   __syncthreads();
-  DitRange<float, L, kNT, 1, S - 1>::run(tile, tw);
   cx<float>* out = reinterpret_cast<cx<float>*>(a.buf) + a.out_slot[r] * a.cstride + colo;
-  dit_stage0_store<float, L, kNT>(tile, tw, [&](int pos, int line, cx<float> v) {
-    if (pos < a.n_out) out[pos * a.zstride + line] = v;
-  });
+  if (dout) {
+    direct_out<L>(tile, tw, out, a.zstride, olo, ohi, small);
+  } else {
+    DitRange<float, L, kNT, 1, S - 1>::run(tile, tw);
+    dit_stage0_store<float, L, kNT>(tile, tw, [&](int pos, int line, cx<float> v) {
+      if (pos >= olo && pos < ohi) out[pos * a.zstride + line] = v;
+    });
+  }
 }
 
 template <int L>

@@ -1,0 +1,144 @@
+// Direct z convolution in (kx, ky, z) space for targets that occupy a few planes.
+//
+// After the x and y transforms the convolution of Sec. "Discretization",
+// Eq. (convolution) is, per column (kx, ky), a 1-D convolution along z with the
+// tensor transformed along x and y only:
+//     out_o(z) = sum_{z'} sum_i s_oi(z - z') in_i(z'),   s_oi = v_o^T N~(z - z') u_i.
+// When the outputs (forward field on the target planes) or the inputs (adjoint
+// source on the target planes) occupy at most a few planes, summing this
+// directly costs a few multiply-adds per complex value streamed from memory,
+// instead of a forward and an inverse z FFT. The result is the same
+// convolution (no approximation). Columns are read with consecutive threads on
+// consecutive kx.
+#include "fft.cuh"
+#include "internal.h"
+
+namespace tmk {
+
+namespace {
+
+// s = a - i b for one (o, i) pair at offset dz: a from the real components
+// (xx, yy, zz, xy), b from the imaginary ones (xz, yz: stored r with N~ = -i r).
+struct ZTensor {
+  const float* T;  // Tz + kyf * P + kx
+  long long Tc, Tdz;
+  float sy;
+  __device__ __forceinline__ void at(int dz, const float* coef, int need, float& a, float& b) const {
+    const int adz = dz < 0 ? -dz : dz;
+    const float sz = dz < 0 ? -1.0f : 1.0f;
+    const float* t = T + adz * Tdz;
+    a = 0.0f;
+    b = 0.0f;
+    if (need & 1) a += coef[0] * t[0];
+    if (need & 2) a += coef[1] * t[Tc];
+    if (need & 4) a += coef[2] * t[2 * Tc];
+    if (need & 8) a += coef[3] * sy * t[3 * Tc];
+    if (need & 16) b += coef[4] * sz * t[4 * Tc];
+    if (need & 32) b += coef[5] * sy * sz * t[5 * Tc];
+  }
+};
+
+__device__ __forceinline__ cx<float> apply_s(cx<float> v, float a, float b) {
+  // (a - i b) v
+  return mk(a * v.x + b * v.y, a * v.y - b * v.x);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(256) k_zdir(ZDirArgs a) {
+  const int kx = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int zc = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (kx >= a.P || zc >= a.Ly) return;
+  const int2 col = a.zcol[zc];
+  const int kyf = col.y <= a.Ly / 2 ? col.y : a.Ly - col.y;
+  ZTensor zt{a.Tz + kyf * (long long)a.P + kx, a.Tc, a.Tdz, col.y <= a.Ly / 2 ? 1.0f : -1.0f};
+  const long long colo = (long long)col.x * a.P + kx;
+  const cx<float>* buf = reinterpret_cast<const cx<float>*>(a.buf);
+  cx<float>* obuf = reinterpret_cast<cx<float>*>(a.buf);
+
+  if (a.nzout <= a.nzin) {  // few outputs: stream the inputs, keep NP x nout sums
+    cx<float> acc[3][NP];
+#pragma unroll
+    for (int o = 0; o < 3; o++)
+#pragma unroll
+      for (int p = 0; p < NP; p++) acc[o][p] = zero<float>();
+    for (int z = a.zin0; z < a.zin0 + a.nzin; z++) {
+      cx<float> in[3];
+#pragma unroll
+      for (int i = 0; i < 3; i++)
+        if (i < a.nin) in[i] = buf[a.in_slot[i] * a.cstride + z * a.zstride + colo];
+#pragma unroll
+      for (int p = 0; p < NP; p++) {
+        if (p >= a.nzout) break;
+        const int dz = a.zout0 + p - z;
+#pragma unroll
+        for (int o = 0; o < 3; o++) {
+          if (o >= a.nout) break;
+#pragma unroll
+          for (int i = 0; i < 3; i++) {
+            if (i >= a.nin) break;
+            float sa, sb;
+            zt.at(dz, a.coef[o][i], a.need[o][i], sa, sb);
+            acc[o][p] = acc[o][p] + apply_s(in[i], sa, sb);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+      if (p >= a.nzout) break;
+#pragma unroll
+      for (int o = 0; o < 3; o++)
+        if (o < a.nout) obuf[a.out_slot[o] * a.cstride + (a.zout0 + p) * a.zstride + colo] = acc[o][p];
+    }
+  } else {  // few inputs: keep them, stream the outputs
+    cx<float> in[3][NP];
+#pragma unroll
+    for (int p = 0; p < NP; p++)
+#pragma unroll
+      for (int i = 0; i < 3; i++)
+        in[i][p] = (p < a.nzin && i < a.nin) ? buf[a.in_slot[i] * a.cstride + (a.zin0 + p) * a.zstride + colo]
+                                               : zero<float>();
+    for (int z = a.zout0; z < a.zout0 + a.nzout; z++) {
+      cx<float> acc[3] = {zero<float>(), zero<float>(), zero<float>()};
+#pragma unroll
+      for (int p = 0; p < NP; p++) {
+        if (p >= a.nzin) break;
+        const int dz = z - (a.zin0 + p);
+#pragma unroll
+        for (int o = 0; o < 3; o++) {
+          if (o >= a.nout) break;
+#pragma unroll
+          for (int i = 0; i < 3; i++) {
+            if (i >= a.nin) break;
+            float sa, sb;
+            zt.at(dz, a.coef[o][i], a.need[o][i], sa, sb);
+            acc[o] = acc[o] + apply_s(in[i][p], sa, sb);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < 3; o++)
+        if (o < a.nout) obuf[a.out_slot[o] * a.cstride + z * a.zstride + colo] = acc[o];
+    }
+  }
+}
+
+}  // namespace
+
+int launch_zdir(const ZDirArgs& a, cudaStream_t s) {
+  const int small = a.nzout <= a.nzin ? a.nzout : a.nzin;
+  if (small < 0 || small > kDirectPlanesMax) return -2;
+  if (small == 0) return 0;
+  dim3 grid((a.P + 31) / 32, (a.Ly + 7) / 8);
+  if (small == 1)
+    k_zdir<1><<<grid, 256, 0, s>>>(a);
+  else if (small == 2)
+    k_zdir<2><<<grid, 256, 0, s>>>(a);
+  else if (small <= 4)
+    k_zdir<4><<<grid, 256, 0, s>>>(a);
+  else
+    k_zdir<kDirectPlanesMax><<<grid, 256, 0, s>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace tmk

@@ -60,6 +60,22 @@ __global__ void k_update(float* rho, const float* G, long long n, float alpha, i
     rho[i] = fminf(fmaxf(rho[i] - step * G[i], 0.0f), 1.0f);
 }
 
+// [zlo, zhi) of the planes that hold a nonzero mask entry (ext preset to (INT_MAX-ish, 0))
+__global__ void k_mask_extent(const uint8_t* mask, int nz, long long plane, int* ext) {
+  for (int z = blockIdx.y; z < nz; z += gridDim.y) {
+    const uint8_t* m = mask + (long long)z * plane;
+    int any = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < plane && !any;
+         i += (long long)gridDim.x * blockDim.x)
+      any = m[i] != 0;
+    any = __syncthreads_or(any);
+    if (any && threadIdx.x == 0) {
+      atomicMin(&ext[0], z);
+      atomicMax(&ext[1], z + 1);
+    }
+  }
+}
+
 int grid_for(long long n, int per) {
   long long b = (n + per - 1) / per;
   if (b < 1) b = 1;
@@ -112,6 +128,13 @@ float* g_noalloc_ptr[256] = {nullptr};  // device address of g_noalloc_scratch, 
 
 int launch_j_finalize(const double* part, int n, double* J, cudaStream_t s) {
   k_j_finalize<<<1, 256, 0, s>>>(part, n, J);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+int launch_mask_extent(const uint8_t* mask, int nz, long long plane, int* ext, cudaStream_t s) {
+  if (cudaMemsetAsync(ext, 0x7f, sizeof(int), s) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(ext + 1, 0, sizeof(int), s) != cudaSuccess) return -1;
+  const int gx = (int)((plane + 1023) / 1024 < 8 ? (plane + 1023) / 1024 : 8);
+  k_mask_extent<<<dim3(gx, nz < 65535 ? nz : 65535), 256, 0, s>>>(mask, nz, plane, ext);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 int launch_absmax(const float* G, long long n, unsigned int* gmax, cudaStream_t s) {

@@ -18,6 +18,11 @@
 // 3. Scaling by -1/(Lx Ly Lz) (the minus of H = -N*M and the normalisation of
 //    the unnormalised inverse transforms), rounding to float32 and storage as
 //    [6][Lz/2+1][Ly/2+1][P] with kx padded to P by zeros.
+// 4. The same tensor transformed along x and y only (z kept as the offset
+//    0 <= dz < nz), scaled by -1/(Lx Ly), float32 [6][nz][Ly/2+1][P]: the z
+//    convolution can then be summed directly when one side of it occupies only
+//    a few planes. Components odd along exactly one of x, y (xz, yz) are
+//    imaginary there; the stored value r means N~ = -i r for them.
 #include <math.h>
 #include <stdio.h>
 
@@ -194,8 +199,9 @@ __global__ void k_trig_strided(const double* in, double* out, int outer, int n, 
   }
 }
 
-// spec[6][KZ][KY][KX] (float64) -> T[6][KZ][KY][P] (float32), scaled and signed
-__global__ void k_pack(const double* spec, float* T, int KZ, int KY, int KX, int P, double scale) {
+// spec[6][KZ][KY][KX] (float64) -> T[6][KZ][KY][P] (float32), scaled; component c
+// multiplied by sgn[c] (the product of the -i factors of its odd axes, real part)
+__global__ void k_pack(const double* spec, float* T, int KZ, int KY, int KX, int P, double scale, int neg_mask) {
   const long long n = 6LL * KZ * KY * P;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(i % P);
@@ -203,7 +209,7 @@ __global__ void k_pack(const double* spec, float* T, int KZ, int KY, int KX, int
     const int c = (int)(r / ((long long)KZ * KY));
     float v = 0.0f;
     if (k < KX) {
-      const double sgn = c >= 3 ? -1.0 : 1.0;
+      const double sgn = ((neg_mask >> c) & 1) ? -1.0 : 1.0;
       v = (float)(sgn * scale * spec[r * KX + k]);
     }
     T[i] = v;
@@ -223,7 +229,7 @@ __global__ void k_pack(const double* spec, float* T, int KZ, int KY, int KX, int
 }  // namespace
 
 int tensor_setup(int nx, int ny, int nz, const double d_in[3], int Lx, int Ly, int Lz, int P, float* T_out,
-                 double* octant_host, cudaStream_t s, char* err, int errlen) {
+                 float* Tz_out, double* octant_host, cudaStream_t s, char* err, int errlen) {
   int rc = 0;
   double dmax = fmax(d_in[0], fmax(d_in[1], d_in[2]));
   const double d[3] = {d_in[0] / dmax, d_in[1] / dmax, d_in[2] / dmax};
@@ -280,6 +286,12 @@ int tensor_setup(int nx, int ny, int nz, const double d_in[3], int Lx, int Ly, i
   TCK(cudaStreamSynchronize(s));
   cudaFree(b1);
   b1 = nullptr;
+  if (Tz_out) {  // x, y transformed; z as offset: xy carries (-i)^2 = -1, xz and yz one -i (kept implicit)
+    const long long n = 6LL * nz * KY * P;
+    k_pack<<<(int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192), 256, 0, s>>>(
+        b2, Tz_out, nz, KY, KX, P, -1.0 / ((double)Lx * (double)Ly), 1 << 3);
+    TCK(cudaPeekAtLastError());
+  }
   // z: b2[6][1][nz][KY*KX] -> b3[6][KZ][KY*KX]
   TCK(cudaMalloc(&b1, 6 * n3 * sizeof(double)));
   {
@@ -292,7 +304,7 @@ int tensor_setup(int nx, int ny, int nz, const double d_in[3], int Lx, int Ly, i
   {
     const long long n = 6LL * KZ * KY * P;
     k_pack<<<(int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192), 256, 0, s>>>(
-        b1, T_out, KZ, KY, KX, P, -1.0 / ((double)Lx * (double)Ly * (double)Lz));
+        b1, T_out, KZ, KY, KX, P, -1.0 / ((double)Lx * (double)Ly * (double)Lz), (1 << 3) | (1 << 4) | (1 << 5));
     TCK(cudaPeekAtLastError());
   }
   TCK(cudaStreamSynchronize(s));

@@ -128,6 +128,24 @@ class Magnet:
             _stream(self.device)))
         return (J.value if sync else None), G
 
+    def set_target(self, mask, Ht=None, Ht_const=(0.0, 0.0, 0.0), w=(0.0, 0.0, 1.0)):
+        """Prepare J = sum_mask sum_c w_c (H_c - Ht_c)^2 for repeated evaluate() calls."""
+        mask = self._dev(mask, U8, self.out_shape, "mask")
+        if Ht is not None:
+            Ht = self._dev(Ht, F32, (3,) + self.out_shape, "Ht")
+        self._ck(self.L.tm_set_target(self.h, _ptr(mask), _ptr(Ht), _lib.c_float3(*[float(v) for v in Ht_const]),
+                                      _lib.c_float3(*[float(v) for v in w]), _stream(self.device)))
+
+    def evaluate(self, rho, G=None, sync=True):
+        """(J, dJ/drho) for the prepared target. J is a float if sync else None."""
+        rho = self._dev(rho, F32, self.design_shape, "rho")
+        if G is None:
+            G = torch.empty(self.design_shape, dtype=F32, device=self.device)
+        J = ctypes.c_double(0.0)
+        self._ck(self.L.tm_evaluate(self.h, _ptr(rho), ctypes.byref(J) if sync else None, _ptr(G),
+                                    _stream(self.device)))
+        return (J.value if sync else None), G
+
     def objective(self):
         J = ctypes.c_double(0.0)
         self._ck(self.L.tm_get_objective(self.h, ctypes.byref(J), _stream(self.device)))

@@ -205,3 +205,41 @@ def test_errors_are_reported():
         m.stray_field(torch.zeros(m.design_shape, device=DEV))
     with pytest.raises(TopomagError, match="TM_ERR_ARG"):
         m._ck(m.L.tm_set_penalty(m.h, 0.5))
+
+
+@pytest.mark.parametrize("n_out,nzd,d,planes,m0", [
+    ((16, 16, 17), 16, (1e-3, 1e-3, 1e-3), (16,), "const"),          # config 1 layout, one plane above
+    ((40, 23, 30), 19, (1e-3, 0.8e-3, 1.3e-3), (22, 24, 25), "vmf"),  # three planes, gap, varying M0
+    ((33, 50, 12), 7, (2e-3, 1e-3, 1e-3), (3, 9), "const"),          # a plane inside the design box
+    ((24, 20, 26), 14, (1e-3, 1e-3, 1e-3), tuple(range(14, 24)), "const"),  # 10 planes: full pipeline
+])
+@pytest.mark.parametrize("w", [(0.0, 0.0, 1.0), (1.0, 0.5, 2.0)])
+def test_prepared_target_matches_oracle(n_out, nzd, d, planes, m0, w):
+    """tm_set_target + tm_evaluate (direct z sums for <= 8 target planes) against the oracle."""
+    wl = W.small(n_out, nzd, cellsize=d, m0_kind=m0, w=w, ht_kind="normal")
+    m = magnet(wl)
+    mask = np.zeros(wl.out_shape, dtype=np.uint8)
+    rng = np.random.default_rng(21)
+    for z in planes:
+        mask[z] = rng.random(wl.out_shape[1:]) < 0.3
+    Htf = wl.Ht_field()
+    m.set_target(torch.from_numpy(mask).to(DEV), Ht=torch.from_numpy(Htf).to(DEV), w=w)
+    rho = torch.from_numpy(wl.rho()).to(DEV)
+    for _ in range(2):  # repeated evaluations reuse the prepared target
+        J, G = m.evaluate(rho)
+    op = oracle_op(wl)
+    Jr, Gr, _ = O.objective_and_gradient(op, wl.rho(), wl.M0_field(), wl.p, mask, Htf, w)
+    assert abs(J - Jr) <= 1e-5 * abs(Jr)
+    assert rel_l2(G.cpu().numpy(), Gr) <= 1e-4
+    # the one-shot call agrees with the prepared one
+    J2, G2 = m.objective_and_gradient(rho, torch.from_numpy(mask).to(DEV), Ht=torch.from_numpy(Htf).to(DEV), w=w)
+    assert abs(J2 - Jr) <= 1e-5 * abs(Jr)
+    assert rel_l2(G2.cpu().numpy(), Gr) <= 1e-4
+
+
+def test_prepared_target_empty_mask_gives_zero():
+    wl = W.small((16, 12, 10), 8)
+    m = magnet(wl)
+    m.set_target(torch.zeros(wl.out_shape, dtype=torch.uint8, device=DEV), Ht_const=(0, 0, 1e5))
+    J, G = m.evaluate(torch.from_numpy(wl.rho()).to(DEV))
+    assert J == 0.0 and float(G.abs().max()) == 0.0
