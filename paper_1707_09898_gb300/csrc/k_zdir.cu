@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(256) k_zdir(ZDirArgs a) {
     for (int o = 0; o < 3; o++)
 #pragma unroll
       for (int p = 0; p < NP; p++) acc[o][p] = zero<float>();
+#pragma unroll 8
     for (int z = a.zin0; z < a.zin0 + a.nzin; z++) {
       cx<float> in[3];
 #pragma unroll
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(256) k_zdir(ZDirArgs a) {
       for (int i = 0; i < 3; i++)
         in[i][p] = (p < a.nzin && i < a.nin) ? buf[a.in_slot[i] * a.cstride + (a.zin0 + p) * a.zstride + colo]
                                                : zero<float>();
+#pragma unroll 8
     for (int z = a.zout0; z < a.zout0 + a.nzout; z++) {
       cx<float> acc[3] = {zero<float>(), zero<float>(), zero<float>()};
 #pragma unroll

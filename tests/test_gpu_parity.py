@@ -243,3 +243,18 @@ def test_prepared_target_empty_mask_gives_zero():
     m.set_target(torch.zeros(wl.out_shape, dtype=torch.uint8, device=DEV), Ht_const=(0, 0, 1e5))
     J, G = m.evaluate(torch.from_numpy(wl.rho()).to(DEV))
     assert J == 0.0 and float(G.abs().max()) == 0.0
+
+
+def test_cufft_comparison_pipeline_matches_oracle():
+    """The plain cuFFT comparison pipeline computes the same J and gradient (so its timing is comparable)."""
+    from paper_1707_09898_gb300.cufft_pipeline import CufftMagnet
+
+    wl = W.small((20, 18, 22), 16)
+    b = CufftMagnet(wl.n_out, wl.nzd, wl.cellsize, M0=wl.M0_const(), p=wl.p)
+    rho, mask = wl.rho(), wl.mask()
+    J, G = b.objective_and_gradient(torch.from_numpy(rho).to(DEV), torch.from_numpy(mask).to(DEV),
+                                    Ht_const=tuple(wl.Ht_const_vec()), w=wl.w)
+    op = oracle_op(wl)
+    Jr, Gr, _ = O.objective_and_gradient(op, rho, wl.M0_const(), wl.p, mask, wl.Ht_const_vec(), wl.w)
+    assert abs(J - Jr) <= 1e-5 * abs(Jr)
+    assert rel_l2(G.cpu().numpy(), Gr) <= 1e-4
