@@ -111,59 +111,121 @@ __device__ __forceinline__ void xseparate(const cx<float>* tile, int P, OUT out)
 }
 
 // Hermitian extension of the half spectra of 2*TB rows into the tile (DIF positions).
+// Every global load of the block is issued before the first shared store.
 template <int L>
 __device__ __forceinline__ void xhermitian(cx<float>* tile, const cx<float>* in, int row0, int rows, int P) {
   constexpr int K = L / 2 + 1;
-  for (int i = threadIdx.x; i < TB * K; i += kNT) {
+  constexpr int N = TB * K, ITER = (N + kNT - 1) / kNT;
+  cx<float> A[ITER], B[ITER];
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int i = it * kNT + threadIdx.x;
     const int line = i / K, k = i - line * K;
     const int ra = row0 + 2 * line, rb = ra + 1;
-    const cx<float> A = ra < rows ? in[(long long)ra * P + k] : zero<float>();
-    const cx<float> B = rb < rows ? in[(long long)rb * P + k] : zero<float>();
+    const bool ok = N % kNT == 0 || i < N;
+    A[it] = (ok && ra < rows) ? in[(long long)ra * P + k] : zero<float>();
+    B[it] = (ok && rb < rows) ? in[(long long)rb * P + k] : zero<float>();
+  }
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int i = it * kNT + threadIdx.x;
+    if (N % kNT != 0 && i >= N) continue;
+    const int line = i / K, k = i - line * K;
+    const cx<float> a = A[it], b = B[it];
     if (k == 0 || k == L / 2) {
-      tile[tix(pos_of_k<L>(k), line)] = mk(A.x, B.x);
+      tile[tix(pos_of_k<L>(k), line)] = mk(a.x, b.x);
     } else {
-      tile[tix(pos_of_k<L>(k), line)] = mk(A.x - B.y, A.y + B.x);      // A + iB
-      tile[tix(pos_of_k<L>(L - k), line)] = mk(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
+      tile[tix(pos_of_k<L>(k), line)] = mk(a.x - b.y, a.y + b.x);      // A + iB
+      tile[tix(pos_of_k<L>(L - k), line)] = mk(a.x + b.y, b.x - a.y);  // conj(A) + i conj(B)
     }
   }
 }
 
-template <int L>
+// Persistent forward x pass: a block loops over 32-row tiles; the raw inputs of
+// the next tile are loaded into registers while the current tile is separated
+// and stored, so global latency overlaps the shared-memory work.
+template <int L, int SRC>
 __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
   constexpr int S = plan_stages(L);
+  using S0 = StageShape<L, 0>;
+  constexpr bool withM0 = SRC == SRC_RHO_M0;
+  constexpr int RM = withM0 ? 1 : 0;
+  constexpr int R = S0::R, M = S0::M, NU = M * TB, ITER = (NU + kNT - 1) / kNT;
+  // nx <= L/2, so the stage-0 inputs x = j + q M with q >= R/2 are always padding
+  constexpr int RH = R / 2 > 0 ? R / 2 : 1;
   extern __shared__ __align__(16) unsigned char smem[];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
   cx<float>* tile = tw + L;
   load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
-  __syncthreads();
-  const int row0 = blockIdx.x * ROWS;
   const int c = a.comp[blockIdx.y];
-  xdif0<L>(tile, tw, [&](int x, int line) {
-    const int ra = row0 + 2 * line, rb = ra + 1;
-    float va = 0.0f, vb = 0.0f;
-    if (x < a.nx) {
-      const long long oa = (long long)ra * a.nx + x, ob = oa + a.nx;
-      if (a.src == SRC_VECTOR) {
-        if (ra < a.rows) va = a.vec[c * a.vec_cstride + oa];
-        if (rb < a.rows) vb = a.vec[c * a.vec_cstride + ob];
-      } else {
-        if (ra < a.rows) va = ipow(a.rho[oa], a.p);
-        if (rb < a.rows) vb = ipow(a.rho[ob], a.p);
-        if (a.src == SRC_RHO_M0) {
-          if (ra < a.rows) va *= a.M0v[c * a.M0v_cstride + oa];
-          if (rb < a.rows) vb *= a.M0v[c * a.M0v_cstride + ob];
+  cx<float>* out = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[blockIdx.y] * a.out_cstride;
+  const int ntiles = (a.rows + ROWS - 1) / ROWS;
+  const float* src = SRC == SRC_VECTOR ? a.vec + c * a.vec_cstride : a.rho;
+  const float* m0 = withM0 ? a.M0v + c * a.M0v_cstride : nullptr;
+  float ra[ITER][RH], rb[ITER][RH], ma[ITER][RM ? RH : 1], mb[ITER][RM ? RH : 1];
+  auto fetch = [&](int t) {
+    const int row0 = t * ROWS;
+#pragma unroll
+    for (int it = 0; it < ITER; it++) {
+      const int u = it * kNT + threadIdx.x;
+      const int j = u % M, line = u / M;
+      const int ra_ = row0 + 2 * line, rb_ = ra_ + 1;
+      const bool ok = NU % kNT == 0 || u < NU;
+#pragma unroll
+      for (int q = 0; q < RH; q++) {
+        const int x = j + q * M;
+        const long long oa = (long long)ra_ * a.nx + x;
+        const bool in_x = ok && x < a.nx;
+        ra[it][q] = (in_x && ra_ < a.rows) ? src[oa] : 0.0f;
+        rb[it][q] = (in_x && rb_ < a.rows) ? src[oa + a.nx] : 0.0f;
+        if constexpr (withM0) {
+          ma[it][q] = (in_x && ra_ < a.rows) ? m0[oa] : 0.0f;
+          mb[it][q] = (in_x && rb_ < a.rows) ? m0[oa + a.nx] : 0.0f;
         }
       }
     }
-    return mk(va, vb);
-  });
+  };
+  int t = blockIdx.x;
+  if (t < ntiles) fetch(t);
   __syncthreads();
-  DifRange<float, L, kNT, 1, S, true>::run(tile, tw);
-  cx<float>* out = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[blockIdx.y] * a.out_cstride;
-  xseparate<L>(tile, a.P, [&](int rr, int k, cx<float> v) {
-    const int row = row0 + rr;
-    if (row < a.rows) out[(long long)row * a.P + k] = v;
-  });
+  for (; t < ntiles; t += gridDim.x) {
+    const int row0 = t * ROWS;
+#pragma unroll
+    for (int it = 0; it < ITER; it++) {
+      const int u = it * kNT + threadIdx.x;
+      if (NU % kNT == 0 || u < NU) {
+        const int j = u % M, line = u / M;
+        cx<float> v[R];
+#pragma unroll
+        for (int q = RH; q < R; q++) v[q] = zero<float>();
+#pragma unroll
+        for (int q = 0; q < RH; q++) {
+          float va = ra[it][q], vb = rb[it][q];
+          if constexpr (SRC != SRC_VECTOR) {
+            va = ipow(va, a.p);
+            vb = ipow(vb, a.p);
+            if constexpr (withM0) {
+              va *= ma[it][q];
+              vb *= mb[it][q];
+            }
+          }
+          v[q] = mk(va, vb);
+        }
+        Dft<float, R, false>::run(v);
+        apply_twiddles<float, L, 0, false>(v, j, tw);
+#pragma unroll
+        for (int q = 0; q < R; q++) tile[tix(j + q * M, line)] = v[q];
+      }
+    }
+    __syncthreads();
+    DifRange<float, L, kNT, 1, S, true>::run(tile, tw);
+    if (t + (int)gridDim.x < ntiles) fetch(t + gridDim.x);
+    xseparate<L>(tile, a.P, [&](int rr, int k, cx<float> v) {
+      const int row = row0 + rr;
+      if (row < a.rows) out[(long long)row * a.P + k] = v;
+    });
+    __syncthreads();
+  }
 }
 
 template <int L, int SINK, int MINB>
@@ -177,7 +239,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
   const int row0 = a.row_base + blockIdx.x * ROWS;
   const cx<float>* in0 = reinterpret_cast<const cx<float>*>(a.in);
 
-  if constexpr (SINK == SINK_CHAIN && MINB == 3) {
+  if constexpr (SINK == SINK_CHAIN && MINB == 2) {
     // one slot, already contracted with the constant M0: G = p rho^(p-1) D
     __syncthreads();
     xhermitian<L>(tile, in0 + a.in_slot[0] * a.in_cstride, row0, a.rows, a.P);
@@ -357,19 +419,34 @@ size_t xsmem() {
   return (size_t)(L + L * TB) * sizeof(float2);
 }
 
-template <int L>
-int run_xfwd(const XFwdArgs& a, int ncomp, cudaStream_t s) {
+template <int L, int SRC>
+int run_xfwd_src(const XFwdArgs& a, int ncomp, cudaStream_t s) {
   const size_t sm = xsmem<L>();
   static bool init = false;
   if (!init) {
-    if (cudaFuncSetAttribute(k_xfwd<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_xfwd<L, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
       return -1;
     init = true;
   }
-  const int blocks = (a.rows + ROWS - 1) / ROWS;
-  if (blocks == 0 || ncomp == 0) return 0;
-  k_xfwd<L><<<dim3(blocks, ncomp), kNT, sm, s>>>(a);
+  const int tiles = (a.rows + ROWS - 1) / ROWS;
+  if (tiles == 0 || ncomp == 0) return 0;
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+  }
+  const int per_comp = (2 * nsm + ncomp - 1) / ncomp;  // two resident blocks per SM in total
+  const int blocks = tiles < per_comp ? tiles : per_comp;
+  k_xfwd<L, SRC><<<dim3(blocks, ncomp), kNT, sm, s>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+template <int L>
+int run_xfwd(const XFwdArgs& a, int ncomp, cudaStream_t s) {
+  if (a.src == SRC_RHO_POW) return run_xfwd_src<L, SRC_RHO_POW>(a, ncomp, s);
+  if (a.src == SRC_RHO_M0) return run_xfwd_src<L, SRC_RHO_M0>(a, ncomp, s);
+  return run_xfwd_src<L, SRC_VECTOR>(a, ncomp, s);
 }
 template <int L, int SINK, int MINB>
 int run_xinv_sink(const XInvArgs& a, cudaStream_t s) {
@@ -389,9 +466,9 @@ int run_xinv_sink(const XInvArgs& a, cudaStream_t s) {
 }
 template <int L>
 int run_xinv(const XInvArgs& a, cudaStream_t s) {
-  if (a.sink == SINK_FIELD) return run_xinv_sink<L, SINK_FIELD, 3>(a, s);
+  if (a.sink == SINK_FIELD) return run_xinv_sink<L, SINK_FIELD, 2>(a, s);
   if (a.sink == SINK_OBJECTIVE) return run_xinv_sink<L, SINK_OBJECTIVE, 2>(a, s);
-  if (a.ncomp == 1 && a.M0v == nullptr) return run_xinv_sink<L, SINK_CHAIN, 3>(a, s);  // contracted slot
+  if (a.ncomp == 1 && a.M0v == nullptr) return run_xinv_sink<L, SINK_CHAIN, 2>(a, s);  // contracted slot
   return run_xinv_sink<L, SINK_CHAIN, 1>(a, s);
 }
 

@@ -43,6 +43,62 @@ __device__ __forceinline__ cx<float> apply_s(cx<float> v, float a, float b) {
   return mk(a * v.x + b * v.y, a * v.y - b * v.x);
 }
 
+// One input, one output, one tensor component (the common case: constant M0 and
+// one weighted field component, or an axis-aligned M0): per streamed value one
+// load, one tensor load and one complex multiply-add, with running pointers.
+// c: the component; its coefficient and the column's sign are folded into `scale`.
+__global__ void __launch_bounds__(256) k_zdir_simple(ZDirArgs a, int c) {
+  const int kx = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int zc = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (kx >= a.P || zc >= a.Ly) return;
+  const int2 col = a.zcol[zc];
+  const bool lo = col.y <= a.Ly / 2;
+  const int kyf = lo ? col.y : a.Ly - col.y;
+  const bool imag = c >= 4;                 // xz, yz: N~ = -i r
+  const bool odd_z = c >= 4;                // xz, yz change sign with dz
+  float scale = a.coef[0][0][c];
+  if ((c == 3 || c == 5) && !lo) scale = -scale;  // odd in y
+  const float* t = a.Tz + c * a.Tc + kyf * (long long)a.P + kx;
+  const long long colo = (long long)col.x * a.P + kx;
+  const cx<float>* in = reinterpret_cast<const cx<float>*>(a.buf) + a.in_slot[0] * a.cstride + colo;
+  cx<float>* out = reinterpret_cast<cx<float>*>(a.buf) + a.out_slot[0] * a.cstride + colo;
+  auto fac = [&](int dz) {
+    const int adz = dz < 0 ? -dz : dz;
+    float v = scale * t[adz * a.Tdz];
+    if (odd_z && dz < 0) v = -v;
+    return v;
+  };
+  if (a.nzout == 1) {  // stream the inputs onto one output plane
+    const int zo = a.zout0;
+    const cx<float>* ip = in + (long long)a.zin0 * a.zstride;
+    float ar = 0.0f, ai = 0.0f;
+#pragma unroll 8
+    for (int z = a.zin0; z < a.zin0 + a.nzin; z++) {
+      const cx<float> v = *ip;
+      ip += a.zstride;
+      const float f = fac(zo - z);
+      if (imag) {  // (-i f) v
+        ar += f * v.y;
+        ai -= f * v.x;
+      } else {
+        ar += f * v.x;
+        ai += f * v.y;
+      }
+    }
+    out[(long long)zo * a.zstride] = mk(ar, ai);
+  } else {  // one input plane streamed onto every output plane
+    const int zi = a.zin0;
+    const cx<float> v = in[(long long)zi * a.zstride];
+    cx<float>* op = out + (long long)a.zout0 * a.zstride;
+#pragma unroll 8
+    for (int z = a.zout0; z < a.zout0 + a.nzout; z++) {
+      const float f = fac(z - zi);
+      *op = imag ? mk(f * v.y, -f * v.x) : mk(f * v.x, f * v.y);
+      op += a.zstride;
+    }
+  }
+}
+
 template <int NP>
 __global__ void __launch_bounds__(256) k_zdir(ZDirArgs a) {
   const int kx = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -132,6 +188,13 @@ int launch_zdir(const ZDirArgs& a, cudaStream_t s) {
   if (small < 0 || small > kDirectPlanesMax) return -2;
   if (small == 0) return 0;
   dim3 grid((a.P + 31) / 32, (a.Ly + 7) / 8);
+  if (a.nin == 1 && a.nout == 1 && small == 1) {
+    const int need = a.need[0][0];
+    if (need != 0 && (need & (need - 1)) == 0) {
+      k_zdir_simple<<<grid, 256, 0, s>>>(a, __builtin_ctz(need));
+      return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+    }
+  }
   if (small == 1)
     k_zdir<1><<<grid, 256, 0, s>>>(a);
   else if (small == 2)
