@@ -241,16 +241,35 @@ __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
 
   if constexpr (SINK == SINK_CHAIN && MINB == 2) {
     // one slot, already contracted with the constant M0: G = p rho^(p-1) D
+    using S0 = StageShape<L, 0>;
+    constexpr int R = S0::R, M = S0::M, NU = M * TB, ITER = (NU + kNT - 1) / kNT;
+    constexpr int RH = R / 2 > 0 ? R / 2 : 1;  // x = j + q M < nx <= L/2 needs q < R/2
+    __shared__ float wmax[kNT / 32];
     __syncthreads();
     xhermitian<L>(tile, in0 + a.in_slot[0] * a.in_cstride, row0, a.rows, a.P);
+    // rho of this tile, fetched while the inverse stages run
+    float pa[ITER][RH], pb[ITER][RH];
+#pragma unroll
+    for (int it = 0; it < ITER; it++) {
+      const int u = it * kNT + threadIdx.x;
+      const int j = u % M, line = u / M;
+      const int ra = row0 + 2 * line, rb = ra + 1;
+      const bool ok = NU % kNT == 0 || u < NU;
+#pragma unroll
+      for (int q = 0; q < RH; q++) {
+        const int x = j + q * M;
+        const long long o = (long long)ra * a.nx + x;
+        pa[it][q] = (ok && x < a.nx && ra < a.rows) ? a.rho[o] : 0.0f;
+        pb[it][q] = (ok && x < a.nx && rb < a.rows) ? a.rho[o + a.nx] : 0.0f;
+      }
+    }
     __syncthreads();
     DitRange<float, L, kNT, 1, S, true>::run(tile, tw);
     float gm = 0.0f;
-    xdit0<L>(tile, tw, [&](int, int j, int line, cx<float>* v) {
-      constexpr int R = StageShape<L, 0>::R, M = StageShape<L, 0>::M;
+    xdit0<L>(tile, tw, [&](int it, int j, int line, cx<float>* v) {
       const int ra = row0 + 2 * line;
 #pragma unroll
-      for (int q = 0; q < R; q++) {
+      for (int q = 0; q < RH; q++) {
         const int x = j + q * M;
         if (x >= a.nx) continue;
 #pragma unroll
@@ -258,7 +277,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
           const int row = ra + h;
           if (row >= a.rows) continue;
           const long long o = (long long)row * a.nx + x;
-          const float G = dpow(a.rho[o], a.p) * (h ? v[q].y : v[q].x);
+          const float G = dpow(h ? pb[it][q] : pa[it][q], a.p) * (h ? v[q].y : v[q].x);
           a.G[o] = G;
           gm = fmaxf(gm, fabsf(G));
         }
@@ -266,7 +285,12 @@ __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
       return false;
     });
     for (int off = 16; off > 0; off >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, off));
-    if ((threadIdx.x & 31) == 0 && gm > 0.0f) atomicMax(a.gmax, __float_as_uint(gm));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = gm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kNT / 32; w++) gm = fmaxf(gm, wmax[w]);
+      if (gm > 0.0f) atomicMax(a.gmax, __float_as_uint(gm));
+    }
     return;
   } else if constexpr (SINK == SINK_CHAIN) {
     using S0 = StageShape<L, 0>;

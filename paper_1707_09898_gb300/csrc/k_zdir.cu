@@ -48,14 +48,18 @@ __device__ __forceinline__ cx<float> apply_s(cx<float> v, float a, float b) {
 // load, one tensor load and one complex multiply-add, with running pointers.
 // c: the component; its coefficient and the column's sign are folded into `scale`.
 __global__ void __launch_bounds__(256) k_zdir_simple(ZDirArgs a, int c) {
+  // 32 kx x 2 columns x 4 z quarters per block
+  constexpr int ZS = 4;
   const int kx = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int zc = blockIdx.y * 8 + (threadIdx.x >> 5);
-  if (kx >= a.P || zc >= a.Ly) return;
-  const int2 col = a.zcol[zc];
+  const int part = (threadIdx.x >> 5) & (ZS - 1);
+  const int zc = blockIdx.y * 2 + (threadIdx.x >> 7);
+  __shared__ cx<float> red[2][ZS][32];
+  const bool valid = kx < a.P && zc < a.Ly;
+  const int2 col = valid ? a.zcol[zc] : make_int2(0, 0);
   const bool lo = col.y <= a.Ly / 2;
   const int kyf = lo ? col.y : a.Ly - col.y;
-  const bool imag = c >= 4;                 // xz, yz: N~ = -i r
-  const bool odd_z = c >= 4;                // xz, yz change sign with dz
+  const bool imag = c >= 4;   // xz, yz: N~ = -i r
+  const bool odd_z = c >= 4;  // xz, yz change sign with dz
   float scale = a.coef[0][0][c];
   if ((c == 3 || c == 5) && !lo) scale = -scale;  // odd in y
   const float* t = a.Tz + c * a.Tc + kyf * (long long)a.P + kx;
@@ -68,30 +72,43 @@ __global__ void __launch_bounds__(256) k_zdir_simple(ZDirArgs a, int c) {
     if (odd_z && dz < 0) v = -v;
     return v;
   };
-  if (a.nzout == 1) {  // stream the inputs onto one output plane
+  if (a.nzout == 1) {  // stream the inputs onto one output plane; quarters summed in order
     const int zo = a.zout0;
-    const cx<float>* ip = in + (long long)a.zin0 * a.zstride;
+    const int per = (a.nzin + ZS - 1) / ZS;
+    const int z0 = a.zin0 + part * per, z1 = min(z0 + per, a.zin0 + a.nzin);
     float ar = 0.0f, ai = 0.0f;
+    if (valid) {
+      const cx<float>* ip = in + (long long)z0 * a.zstride;
 #pragma unroll 8
-    for (int z = a.zin0; z < a.zin0 + a.nzin; z++) {
-      const cx<float> v = *ip;
-      ip += a.zstride;
-      const float f = fac(zo - z);
-      if (imag) {  // (-i f) v
-        ar += f * v.y;
-        ai -= f * v.x;
-      } else {
-        ar += f * v.x;
-        ai += f * v.y;
+      for (int z = z0; z < z1; z++) {
+        const cx<float> v = *ip;
+        ip += a.zstride;
+        const float f = fac(zo - z);
+        if (imag) {  // (-i f) v
+          ar += f * v.y;
+          ai -= f * v.x;
+        } else {
+          ar += f * v.x;
+          ai += f * v.y;
+        }
       }
     }
-    out[(long long)zo * a.zstride] = mk(ar, ai);
-  } else {  // one input plane streamed onto every output plane
+    red[threadIdx.x >> 7][part][threadIdx.x & 31] = mk(ar, ai);
+    __syncthreads();
+    if (part == 0 && valid) {
+      cx<float> s = red[threadIdx.x >> 7][0][threadIdx.x & 31];
+      for (int q = 1; q < ZS; q++) s = s + red[threadIdx.x >> 7][q][threadIdx.x & 31];
+      out[(long long)zo * a.zstride] = s;
+    }
+  } else {  // one input plane streamed onto every output plane; quarters of the planes
+    if (!valid) return;
     const int zi = a.zin0;
     const cx<float> v = in[(long long)zi * a.zstride];
-    cx<float>* op = out + (long long)a.zout0 * a.zstride;
+    const int per = (a.nzout + ZS - 1) / ZS;
+    const int z0 = a.zout0 + part * per, z1 = min(z0 + per, a.zout0 + a.nzout);
+    cx<float>* op = out + (long long)z0 * a.zstride;
 #pragma unroll 8
-    for (int z = a.zout0; z < a.zout0 + a.nzout; z++) {
+    for (int z = z0; z < z1; z++) {
       const float f = fac(z - zi);
       *op = imag ? mk(f * v.y, -f * v.x) : mk(f * v.x, f * v.y);
       op += a.zstride;
@@ -191,7 +208,7 @@ int launch_zdir(const ZDirArgs& a, cudaStream_t s) {
   if (a.nin == 1 && a.nout == 1 && small == 1) {
     const int need = a.need[0][0];
     if (need != 0 && (need & (need - 1)) == 0) {
-      k_zdir_simple<<<grid, 256, 0, s>>>(a, __builtin_ctz(need));
+      k_zdir_simple<<<dim3((a.P + 31) / 32, (a.Ly + 1) / 2), 256, 0, s>>>(a, __builtin_ctz(need));
       return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
     }
   }

@@ -27,11 +27,17 @@ __global__ void k_j_finalize(const double* part, int n, double* J) {
 }
 
 __global__ void k_absmax(const float* G, long long n, unsigned int* gmax) {
+  __shared__ float wm[32];
   float m = 0.0f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     m = fmaxf(m, fabsf(G[i]));
   for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-  if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(gmax, __float_as_uint(m));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {  // one atomic per block
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, wm[w]);
+    if (m > 0.0f) atomicMax(gmax, __float_as_uint(m));
+  }
 }
 
 __global__ void k_update(float* rho, const float* G, long long n, float alpha, int normalize,
