@@ -33,9 +33,11 @@ sys.path.insert(0, ROOT)
 METRIC = "adjoint-gradient evals/s at 256^3 cells, FP32 vs FP64 oracle; % of HBM peak"
 UNIT = "evals/s"
 
-# DRAM bytes per launch of the z pass at 256^3 from one ncu capture
-# (profiles/zpass_256cube_ncu.md); valid only while the kernel source is unchanged.
-ZPASS_TRAFFIC = {"bytes": None, "source_sha1": None}
+# DRAM bytes (read + write) per launch of the dominant kernel kind at 256^3 from one ncu
+# capture (profiles/zdir_c4_256cube_ncu.md: the direct z sum, forward and adjoint launch
+# averaged); valid only while its source file is unchanged.
+ZPASS_TRAFFIC = {"bytes": 330.5e6, "source": "paper_1707_09898_gb300/csrc/k_zdir.cu",
+                 "source_sha1": "1e01034aaa7e24a5aeb9221956bd20b7f6d468eb"}
 
 
 def parse():
@@ -47,6 +49,7 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-oneshot", action="store_true", help="skip timing the one-shot call")
     return ap.parse_args()
 
 
@@ -345,7 +348,7 @@ def run_native(args):
     # the same step through the one-shot call (mask passed each time, full z transforms
     # restricted to the target planes on the device)
     oneshot = None
-    if prepared:
+    if prepared and not args.no_oneshot:
         for _ in range(2):
             m.objective_and_gradient(rho, mask, Ht_const=Htc, w=w, G=G, sync=False)
         torch.cuda.synchronize()
@@ -373,8 +376,8 @@ def run_native(args):
         t_launch = prof[kind][0] / prof[kind][1] / 1e3
         achieved = ab[kind] / t_launch / 1e9
         traffic = None
-        src = os.path.join(ROOT, "paper_1707_09898_gb300", "csrc", "k_yz.cu")
-        if kind == "z_pass" and ZPASS_TRAFFIC["bytes"] and ZPASS_TRAFFIC["source_sha1"] == sha1(src):
+        src = os.path.join(ROOT, ZPASS_TRAFFIC["source"])
+        if prepared and kind == "z_pass" and ZPASS_TRAFFIC["source_sha1"] == sha1(src):
             traffic = ZPASS_TRAFFIC["bytes"]
         roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
