@@ -74,13 +74,20 @@ def barrier(dist):
 
 
 def max_over_ranks(x, dist):
+    """Slowest rank's value (the job's time); works on NCCL (cuda) and gloo (cpu) groups."""
     if dist is None:
         return x
     import torch
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(ws, steps, ms_max):
+    """Whole-job evals/s of ws independent replicas that each ran `steps` in ms_max (slowest rank)."""
+    return ws * steps / (ms_max / 1e3)
 
 
 class Clocks:
@@ -366,7 +373,7 @@ def run_native(args):
             dist.destroy_process_group()
         return
 
-    value = ws * args.steps / (ms_max / 1e3)
+    value = job_throughput(ws, args.steps, ms_max)
     hbm, peak_kind = peaks()
     L = m.fft_lengths()
     roof = None
