@@ -11,6 +11,7 @@ import re
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtopomag.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "topomag.h")
+NET_HEADER = os.path.join(os.path.dirname(HERE), "include", "topomag_net.h")
 
 TM_OK = 0
 ERRORS = {-1: "TM_ERR_ARG", -2: "TM_ERR_SIZE", -3: "TM_ERR_STATE", -4: "TM_ERR_CUDA", -5: "TM_ERR_NOMEM"}
@@ -45,14 +46,32 @@ _SIGS = {
     "tm_profile_read": (ctypes.c_int, [vp, ctypes.c_double * 6, ctypes.c_int * 6]),
     "tm_debug_tensor_octant": (ctypes.c_int, [vp, vp, vp]),
     "tm_debug_tensor_spectrum": (ctypes.c_int, [vp, vp, vp]),
+    # warm-start network kernels (include/topomag_net.h)
+    "tmn_conv3d_forward": (ctypes.c_int, [vp, vp, vp, vp] + [ctypes.c_int] * 7 + [vp]),
+    "tmn_conv3d_backward_data": (ctypes.c_int, [vp, vp, vp] + [ctypes.c_int] * 7 + [vp]),
+    "tmn_conv3d_backward_weight": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_longlong] + [ctypes.c_int] * 6 + [vp]),
+    "tmn_relu_backward": (ctypes.c_int, [vp, vp, ctypes.c_longlong, vp]),
+    "tmn_pool": (ctypes.c_int, [vp, vp] + [ctypes.c_int] * 5 + [vp]),
+    "tmn_pool_backward": (ctypes.c_int, [vp, vp] + [ctypes.c_int] * 6 + [vp]),
+    "tmn_upcat": (ctypes.c_int, [vp, vp, vp] + [ctypes.c_int] * 6 + [vp]),
+    "tmn_upcat_backward": (ctypes.c_int, [vp, vp, vp] + [ctypes.c_int] * 6 + [vp]),
+    "tmn_head_forward": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_longlong, ctypes.c_int, vp]),
+    "tmn_head_backward": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_longlong, ctypes.c_int, vp, vp, vp, vp]),
+    "tmn_adamw": (ctypes.c_int, [vp, vp, vp, vp, ctypes.c_longlong] + [ctypes.c_float] * 5 + [ctypes.c_int, vp, vp,
+                                                                                             ctypes.c_int, ctypes.c_int,
+                                                                                             vp]),
+    "tmn_pack_conv_weights": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
+    "tmn_spec_input": (ctypes.c_int, [vp, vp, vp, vp] + [ctypes.c_int] * 5 + [vp]),
 }
 
 
 def header_functions():
-    """Names of the functions declared in include/topomag.h."""
-    txt = open(HEADER).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(tm_\w+)\s*\(", txt)))
+    """Names of the functions declared in include/topomag.h and include/topomag_net.h."""
+    names = set()
+    for path in (HEADER, NET_HEADER):
+        txt = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+        names |= set(re.findall(r"\b(tmn?_\w+)\s*\(", txt))
+    return sorted(names)
 
 
 def lib():

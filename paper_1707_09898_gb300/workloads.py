@@ -158,3 +158,27 @@ def small(n_out, nzd, cellsize=(1e-3, 1e-3, 1e-3), seed=11, m0_kind="const", w=(
         name=f"small_{nx}x{ny}x{nz}_{nzd}", n_out=tuple(n_out), nzd=nzd, cellsize=tuple(cellsize),
         rho_seed=seed, m0_kind=m0_kind, m0_seed=seed + 1, mask_z=mask_z, mask_xy=mask_xy,
         ht_kind=ht_kind, ht_seed=seed + 2, ht_const=(0.0, 0.0, 0.1), w=tuple(w))
+
+
+# Warm-start specifications: the target of each optimisation drawn from a seed.
+CONFIG5_TRAIN_SEEDS = range(10000, 12000)
+CONFIG5_HELDOUT_SEEDS = range(20000, 20200)
+
+
+def config5(seed):
+    """64^3 design on a 64 x 64 x 72 grid, rho = 0.5, 200 steps of 0.1; the target is a
+    centred square of width U{8..32} on the plane z = 63 + h, h ~ U{1..8} cells above the
+    top face, with H_t,z ~ U[0.05, 0.3] Ms on it."""
+    rng = np.random.default_rng(seed)
+    h = int(rng.integers(1, 9))
+    width = int(rng.integers(8, 33))
+    ht = float(rng.uniform(0.05, 0.3))
+    x0, x1 = _centered(64, width)
+    return Workload(
+        name=f"c5_spec{seed}", n_out=(64, 64, 72), nzd=64, rho_kind="const", rho_const=0.5,
+        mask_z=63 + h, mask_xy=(x0, x1, x0, x1), ht_const=(0.0, 0.0, ht), iters=200, alpha=0.1)
+
+
+def config5_spec(wl):
+    """(footprint [ny][nx] uint8, H_t,z / Ms, height above the top face in cells) of a config5 workload."""
+    return wl.mask()[wl.mask_z], float(wl.ht_const[2]), wl.mask_z - (wl.nzd - 1)
