@@ -12,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtopomag.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "topomag.h")
 NET_HEADER = os.path.join(os.path.dirname(HERE), "include", "topomag_net.h")
+LBFGSB_HEADER = os.path.join(os.path.dirname(HERE), "include", "topomag_lbfgsb.h")
 
 TM_OK = 0
 ERRORS = {-1: "TM_ERR_ARG", -2: "TM_ERR_SIZE", -3: "TM_ERR_STATE", -4: "TM_ERR_CUDA", -5: "TM_ERR_NOMEM"}
@@ -62,13 +63,22 @@ _SIGS = {
                                                                                              vp]),
     "tmn_pack_conv_weights": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
     "tmn_spec_input": (ctypes.c_int, [vp, vp, vp, vp] + [ctypes.c_int] * 5 + [vp]),
+    # L-BFGS-B (include/topomag_lbfgsb.h)
+    "tm_lbfgsb_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_longlong, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int]),
+    "tm_lbfgsb_destroy": (None, [vp]),
+    "tm_lbfgsb_last_error": (ctypes.c_char_p, [vp]),
+    "tm_lbfgsb_start": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int), vp]),
+    "tm_lbfgsb_iterate": (ctypes.c_int, [vp, ctypes.c_double, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int), vp]),
+    "tm_lbfgsb_info": (ctypes.c_int, [vp, ctypes.c_longlong * 5, ctypes.c_double * 3]),
 }
 
 
 def header_functions():
-    """Names of the functions declared in include/topomag.h and include/topomag_net.h."""
+    """Names of the functions declared in include/topomag.h, topomag_net.h and topomag_lbfgsb.h."""
     names = set()
-    for path in (HEADER, NET_HEADER):
+    for path in (HEADER, NET_HEADER, LBFGSB_HEADER):
         txt = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
         names |= set(re.findall(r"\b(tmn?_\w+)\s*\(", txt))
     return sorted(names)

@@ -34,11 +34,13 @@ class Workload:
     m0_dir: Tuple[float, float, float] = (0.0, 0.0, 1.0)
     m0_seed: int = 0
     vmf_kappa: float = 10.0
-    mask_z: int = 0                      # target plane z index
+    mask_z: int = 0                      # target plane z index (the first of mask_nz planes)
+    mask_nz: int = 1                     # number of target planes
+    ms: float = MS                       # magnetization magnitude of M0 (A/m)
     mask_xy: Tuple[int, int, int, int] = (0, 0, 0, 0)  # x0, x1, y0, y1 (half-open)
     ht_kind: str = "const"               # "const" or "normal"
-    ht_const: Tuple[float, float, float] = (0.0, 0.0, 0.0)  # in units of MS
-    ht_sigma: float = 0.05               # in units of MS (normal)
+    ht_const: Tuple[float, float, float] = (0.0, 0.0, 0.0)  # in units of ms
+    ht_sigma: float = 0.05               # in units of ms (normal)
     ht_seed: int = 0
     w: Tuple[float, float, float] = (0.0, 0.0, 1.0)
     iters: int = 0
@@ -68,7 +70,7 @@ class Workload:
         if self.m0_kind != "const":
             return None
         d = np.asarray(self.m0_dir, dtype=np.float64)
-        return MS * d
+        return self.ms * d
 
     def M0_field(self):
         """(3, nzd, ny, nx) float32 magnetization in A/m (constant or von Mises-Fisher)."""
@@ -82,19 +84,19 @@ class Workload:
         k = self.vmf_kappa
         wz = 1.0 + np.log(u + (1.0 - u) * np.exp(-2.0 * k)) / k  # vMF inverse CDF about +z
         s = np.sqrt(np.maximum(0.0, 1.0 - wz * wz))
-        return (MS * np.stack([s * np.cos(phi), s * np.sin(phi), wz])).astype(np.float32)
+        return (self.ms * np.stack([s * np.cos(phi), s * np.sin(phi), wz])).astype(np.float32)
 
     def mask(self):
         m = np.zeros(self.out_shape, dtype=np.uint8)
         x0, x1, y0, y1 = self.mask_xy
-        m[self.mask_z, y0:y1, x0:x1] = 1
+        m[self.mask_z:self.mask_z + self.mask_nz, y0:y1, x0:x1] = 1
         return m
 
     def Ht_const_vec(self):
         """(3,) float32 constant target field in A/m, or None when a full field is used."""
         if self.ht_kind != "const":
             return None
-        return (MS * np.asarray(self.ht_const, dtype=np.float64)).astype(np.float32)
+        return (self.ms * np.asarray(self.ht_const, dtype=np.float64)).astype(np.float32)
 
     def Ht_field(self):
         """(3, nz, ny, nx) float32 target field (zero off the mask for the random kind)."""
@@ -104,7 +106,7 @@ class Workload:
         rng = np.random.default_rng(self.ht_seed)
         out = np.zeros((3,) + self.out_shape, dtype=np.float32)
         m = self.mask().astype(bool)
-        vals = rng.normal(0.0, self.ht_sigma * MS, size=(3, int(m.sum())))
+        vals = rng.normal(0.0, self.ht_sigma * self.ms, size=(3, int(m.sum())))
         out[:, m] = vals.astype(np.float32)
         return out
 
@@ -158,6 +160,19 @@ def small(n_out, nzd, cellsize=(1e-3, 1e-3, 1e-3), seed=11, m0_kind="const", w=(
         name=f"small_{nx}x{ny}x{nz}_{nzd}", n_out=tuple(n_out), nzd=nzd, cellsize=tuple(cellsize),
         rho_seed=seed, m0_kind=m0_kind, m0_seed=seed + 1, mask_z=mask_z, mask_xy=mask_xy,
         ht_kind=ht_kind, ht_seed=seed + 2, ht_const=(0.0, 0.0, 0.1), w=tuple(w))
+
+
+def paper_problem(box=5):
+    """The paper's validation problem (Sec. "Validation and Benchmarks"): a unit cube of
+    39^3 cells magnetized along +z (M0 = (0, 0, 1)) with two layers of cells above it
+    (39 x 39 x 41 = 62,361 cells, the size of its finite-difference mesh), rho = 1 at the
+    start; maximise the z field on a centred box x box area of those two layers:
+    J = -1/2 sum_box H_z^2 (w_z = -1/2, H_t = 0)."""
+    x0, x1 = _centered(39, box)
+    return Workload(
+        name=f"paper_39cube_box{box}", n_out=(39, 39, 41), nzd=39, cellsize=(1.0 / 39,) * 3,
+        rho_kind="const", rho_const=1.0, ms=1.0, mask_z=39, mask_nz=2, mask_xy=(x0, x1, x0, x1),
+        ht_const=(0.0, 0.0, 0.0), w=(0.0, 0.0, -0.5))
 
 
 # Warm-start specifications: the target of each optimisation drawn from a seed.
