@@ -134,6 +134,25 @@ int tm_set_target(tm_ctx* ctx, const uint8_t* mask, const float* H_target, const
                   void* stream);
 int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, void* stream);
 
+/*
+ * Prepared quadratic stencil objective for tm_evaluate (instead of tm_set_target):
+ *   J = sum_k c_k r_k^2,   r_k = sum_{e in row k} a_e H[comp_e][cell_e],
+ * a quadratic form in linear combinations of field values. It expresses the
+ * field-and-gradient objective of Sec. "Optimization of field and gradient"
+ * (rows of one field value with c = -1/2, and rows of a finite-difference normal
+ * derivative with c = -beta/2); dJ/dH = 2 S^T diag(c) S H is its exact partial
+ * derivative, and dJ/drho follows by the adjoint as for tm_set_target.
+ * HOST arrays, copied: row_ptr [K+1] (row k holds entries row_ptr[k] ..
+ * row_ptr[k+1]-1, row_ptr[0] = 0), per entry comp (0..2), cell (z*ny*nx + y*nx + x
+ * on the output grid) and coefficient a; per row the weight c. A cell may appear
+ * in several rows and twice in one row. K = 0 gives J = 0. When the referenced
+ * cells lie on at most 8 consecutive z planes, tm_evaluate computes H only there
+ * (direct z sums as for tm_set_target); otherwise on the whole grid. Synchronises
+ * `stream`. TM_ERR_ARG for indices out of range or non-finite coefficients.
+ */
+int tm_set_stencil_objective(tm_ctx* ctx, long long K, const long long* row_ptr, const int* comp,
+                             const long long* cell, const double* a, const double* c, void* stream);
+
 /* J of the last tm_objective_and_gradient or tm_evaluate (synchronises `stream`). */
 int tm_get_objective(tm_ctx* ctx, double* J_host, void* stream);
 

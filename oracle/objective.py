@@ -10,6 +10,9 @@ Sec. "Methodology":
       J = sum_{i in Omega} sum_c w_c (H_{i,c} - Ht_{i,c})^2 ;
   its partial derivative g = dJ/dH = 2 w_c (H_c - Ht_c) on Omega, 0 elsewhere;
   dJ/drho at fixed H is zero for this J.
+* the field-and-gradient objective of Sec. "Optimization of field and gradient"
+  and, generally, quadratic forms in linear combinations of field values
+  (stencil_objective), with their exact partial derivatives dJ/dH.
 * gradient by the adjoint method (Eqs. (adjoint1)-(adjoint2) and the
   operator form after them): with H = D M and D self-adjoint, the chain rule
   gives dJ/drho_j = p rho_j^(p-1) M0_j . (D g)_j. The paper's operator form
@@ -69,3 +72,49 @@ def objective_and_gradient(op, rho, M0, p, mask, Ht, w):
     g = dJ_dH(H, mask, Ht, w)
     G = chain_rule(rho, M0, p, op.adjoint(g))
     return J, G, H
+
+
+def stencil_objective(H, rows):
+    """J = sum_k c_k r_k^2 with r_k = sum_e a_e H[comp_e, z_e, y_e, x_e] (a quadratic form in
+    linear combinations of field values), and g = dJ/dH. rows: sequence of
+    (c_k, [(comp, z, y, x, a), ...]). Plain loops, float64."""
+    H = np.asarray(H, dtype=np.float64)
+    g = np.zeros_like(H)
+    J = 0.0
+    for c, ents in rows:
+        r = 0.0
+        for comp, z, y, x, a in ents:
+            r += a * H[comp, z, y, x]
+        J += c * r * r
+        for comp, z, y, x, a in ents:
+            g[comp, z, y, x] += 2.0 * c * r * a
+    return float(J), g
+
+
+def field_gradient_objective(H, plane, field, strip, h, beta):
+    """Sec. "Optimization of field and gradient": maximise the z field on a region and its
+    normal derivative on a strip around three of its sides,
+        J = -1/2 sum_{field} H_z^2 - beta/2 sum_{strip} (dH_z/dn)^2 ,
+    on the plane z = plane (cell sums stand for the integrals). dH_z/dn at strip cell
+    (y, x) with outward normal n: the central difference (H_z(c+n) - H_z(c-n)) / (2 h).
+    field: (ny, nx) bool; strip: (y, x, axis, sign) with axis 0 = y, 1 = x. Returns (J, g)."""
+    H = np.asarray(H, dtype=np.float64)
+    Hz = H[2, plane]
+    f = np.asarray(field, dtype=bool)
+    g = np.zeros_like(H)
+    J = -0.5 * float(np.sum(Hz[f] ** 2))
+    g[2, plane][f] = -Hz[f]
+    for y, x, axis, sgn in strip:
+        dy, dx = (sgn, 0) if axis == 0 else (0, sgn)
+        D = (Hz[y + dy, x + dx] - Hz[y - dy, x - dx]) / (2.0 * h)
+        J += -0.5 * beta * D * D
+        g[2, plane, y + dy, x + dx] += -beta * D / (2.0 * h)
+        g[2, plane, y - dy, x - dx] += beta * D / (2.0 * h)
+    return float(J), g
+
+
+def general_objective_and_gradient(op, rho, M0, p, obj):
+    """(J, dJ/drho, H) for any objective obj(H) -> (J, dJ/dH) of the field alone."""
+    H = op.forward(magnetization(rho, M0, p))
+    J, g = obj(H)
+    return J, chain_rule(rho, M0, p, op.adjoint(g)), H

@@ -41,6 +41,7 @@ _SIGS = {
     "tm_get_objective": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), vp]),
     "tm_set_target": (ctypes.c_int, [vp, vp, vp, c_float3, c_float3, vp]),
     "tm_evaluate": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp]),
+    "tm_set_stencil_objective": (ctypes.c_int, [vp, ctypes.c_longlong, vp, vp, vp, vp, vp, vp]),
     "tm_optimize_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_float, ctypes.c_int, vp]),
     "tm_optimize_step_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_longlong, ctypes.c_float, ctypes.c_int, vp]),
     "tm_profile": (ctypes.c_int, [vp, ctypes.c_int]),

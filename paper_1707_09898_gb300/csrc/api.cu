@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "../../include/topomag.h"
@@ -33,6 +34,14 @@ struct tm_ctx {
   float* tHt = nullptr;      // [3][nz][ny][nx] or null
   float tHtc[3] = {0, 0, 0}, tw_[3] = {0, 0, 0};
   int tz0 = 0, tz1 = 0;      // planes holding target cells
+  // prepared stencil objective (tm_set_stencil_objective): target_kind 1
+  int target_kind = 0;
+  long long sK = 0, sU = 0;
+  long long *s_rp = nullptr, *s_idx = nullptr, *s_cp = nullptr, *s_cidx = nullptr;
+  double *s_a = nullptr, *s_c = nullptr, *s_ca = nullptr, *s_r = nullptr, *s_part = nullptr;
+  int* s_crow = nullptr;
+  int s_comps = 0;                      // bit c set: component c is referenced
+  float *sH = nullptr, *sgH = nullptr;  // [3][nz][ny][nx] field / dJ/dH buffers
   float2* A = nullptr;      // [3][nz][ny][P]
   float2* B = nullptr;      // [4][nz][Ly][P]
   float2* tw = nullptr;     // twiddles: Lx | Ly | Lz
@@ -92,7 +101,21 @@ int pick_length(int n) {
   return 0;
 }
 
+void free_stencil(tm_ctx* c) {
+  void* ps[] = {c->s_rp, c->s_idx, c->s_cp, c->s_cidx, c->s_a, c->s_c, c->s_ca, c->s_r, c->s_part, c->s_crow};
+  for (void* p : ps) cudaFree(p);
+  c->s_rp = c->s_idx = c->s_cp = c->s_cidx = nullptr;
+  c->s_a = c->s_c = c->s_ca = c->s_r = c->s_part = nullptr;
+  c->s_crow = nullptr;
+  c->sK = c->sU = 0;
+}
+
 void free_grid(tm_ctx* c) {
+  free_stencil(c);
+  cudaFree(c->sH);
+  cudaFree(c->sgH);
+  c->sH = c->sgH = nullptr;
+  c->target_kind = 0;
   cudaFree(c->M0v);
   cudaFree(c->T);
   cudaFree(c->Tz);
@@ -768,6 +791,240 @@ int tm_set_target(tm_ctx* ctx, const uint8_t* mask, const float* H_target, const
   ctx->tz0 = ext[1] > ext[0] ? ext[0] : 0;
   ctx->tz1 = ext[1] > ext[0] ? ext[1] : 0;
   ctx->have_target = true;
+  ctx->target_kind = 0;
+  return TM_OK;
+}
+
+namespace {
+
+// Forward restricted to the target planes [tz0, tz1): x and y on the design planes,
+// z summed directly onto the target planes, inverse y there. Field components F
+// end up in A slots 0..nF-1 (half spectra along x).
+int forward_planes(tm_ctx* ctx, const float* rho, const int* F, int nF, cudaStream_t s) {
+  int r, nsl;
+  const int np = ctx->tz1 - ctx->tz0;
+  if ((r = xfwd_rho(ctx, rho, s, &nsl))) return r;
+  ConvSpec cs{};
+  cs.nin = nsl;
+  for (int i = 0; i < nsl; i++) {
+    cs.ain[i] = i;
+    cs.bin[i] = i;
+    cs.u[i] = nsl == 1 ? ctx->M0c : kUnit[i];
+  }
+  cs.nout = nF;
+  for (int o = 0; o < nF; o++) {
+    cs.bout[o] = o;
+    cs.aout[o] = o;
+    cs.v[o] = kUnit[F[o]];
+  }
+  if ((r = ypass(ctx, false, cs.nin, cs.ain, cs.bin, 0, ctx->nzd, s))) return r;
+  if ((r = zdirect(ctx, cs, 0, ctx->nzd, ctx->tz0, np, s))) return r;
+  return ypass(ctx, true, cs.nout, cs.aout, cs.bout, ctx->tz0, np, s);
+}
+
+// Adjoint from the target planes: slot j of A holds (x-transformed) dJ/dH of
+// component F[j] on the target planes; the W components carry a source. y there,
+// z summed directly onto the design planes, y and x inverse with the chain rule.
+int adjoint_planes(tm_ctx* ctx, const float* rho, float* dJdrho, const int* F, const int* W, int nW,
+                   cudaStream_t s) {
+  int r;
+  const int np = ctx->tz1 - ctx->tz0;
+  ConvSpec ca{};
+  if (!ctx->m0_var) {
+    ca.nin = nW;
+    for (int i = 0; i < nW; i++) {
+      int j = 0;
+      while (F[j] != W[i]) j++;
+      ca.ain[i] = j;
+      ca.bin[i] = j;
+      ca.u[i] = kUnit[W[i]];
+    }
+    ca.nout = 1;
+    ca.bout[0] = ca.bin[0];
+    ca.aout[0] = ca.ain[0];
+    ca.v[0] = ctx->M0c;
+  } else {
+    ca.nin = ca.nout = 3;
+    for (int i = 0; i < 3; i++) {
+      ca.ain[i] = ca.bin[i] = ca.bout[i] = ca.aout[i] = i;
+      ca.u[i] = ca.v[i] = kUnit[i];
+    }
+  }
+  if ((r = ypass(ctx, false, ca.nin, ca.ain, ca.bin, ctx->tz0, np, s))) return r;
+  if ((r = zdirect(ctx, ca, ctx->tz0, np, 0, ctx->nzd, s))) return r;
+  if ((r = ypass(ctx, true, ca.nout, ca.aout, ca.bout, 0, ctx->nzd, s))) return r;
+  return xinv_chain(ctx, rho, dJdrho, ca.nout, ca.aout, s);
+}
+
+StencilArgs stencil_args(tm_ctx* ctx) {
+  StencilArgs a{};
+  a.K = ctx->sK;
+  a.U = ctx->sU;
+  a.rp = ctx->s_rp;
+  a.idx = ctx->s_idx;
+  a.a = ctx->s_a;
+  a.c = ctx->s_c;
+  a.cp = ctx->s_cp;
+  a.cidx = ctx->s_cidx;
+  a.crow = ctx->s_crow;
+  a.ca = ctx->s_ca;
+  a.H = ctx->sH;
+  a.gH = ctx->sgH;
+  a.r = ctx->s_r;
+  a.part = ctx->s_part;
+  a.J = ctx->Jdev;
+  const long long b = (ctx->sK + 255) / 256;
+  a.nblk = (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+  return a;
+}
+
+// J and dJ/drho of the prepared stencil objective
+int evaluate_stencil(tm_ctx* ctx, const float* rho, float* dJdrho, cudaStream_t s) {
+  int r;
+  int W[3], nW = 0;
+  for (int c = 0; c < 3; c++)
+    if (ctx->s_comps & (1 << c)) W[nW++] = c;
+  const int np = ctx->tz1 - ctx->tz0;
+  if (ctx->sK == 0 || nW == 0) {
+    CK(cudaMemsetAsync(ctx->Jdev, 0, sizeof(double), s));
+    CK(cudaMemsetAsync(dJdrho, 0, design_cells(ctx) * sizeof(float), s));
+    return TM_OK;
+  }
+  const StencilArgs sa = stencil_args(ctx);
+  if (np > kDirectPlanesMax) {  // many planes: full field, then the full adjoint
+    if ((r = tm_stray_field(ctx, rho, ctx->sH, s))) return r;
+    {
+      Timed t(ctx, KIND_OTHER, s);
+      CKL(launch_stencil(sa, s));
+    }
+    return tm_stray_field_adjoint(ctx, rho, ctx->sgH, dJdrho, s);
+  }
+  int F[3], nF = 0;
+  for (int c = 0; c < 3; c++)
+    if (ctx->m0_var || (ctx->s_comps & (1 << c))) F[nF++] = c;
+  if ((r = forward_planes(ctx, rho, F, nF, s))) return r;
+  {  // H of the F components on the target planes
+    XInvArgs x{};
+    x.row_base = ctx->tz0 * ctx->ny;
+    x.rows = ctx->tz1 * ctx->ny;
+    x.nx = ctx->nx;
+    x.P = ctx->P;
+    x.sink = SINK_FIELD;
+    x.ncomp = nF;
+    for (int j = 0; j < nF; j++) {
+      x.comp[j] = F[j];
+      x.in_slot[j] = j;
+    }
+    x.in = ctx->A;
+    x.in_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
+    x.H = ctx->sH;
+    x.H_cstride = out_cells(ctx);
+    x.tw = ctx->tw;
+    Timed t(ctx, KIND_XINV, s);
+    CKL(launch_xinv(ctx->L[0], x, s));
+  }
+  {
+    Timed t(ctx, KIND_OTHER, s);
+    CKL(launch_stencil(sa, s));
+  }
+  {  // dJ/dH on the target planes, transformed along x into the same slots
+    const long long plane = (long long)ctx->ny * ctx->nx;
+    XFwdArgs x{};
+    x.rows = np * ctx->ny;
+    x.nx = ctx->nx;
+    x.P = ctx->P;
+    x.src = SRC_VECTOR;
+    x.vec = ctx->sgH + ctx->tz0 * plane;
+    x.vec_cstride = out_cells(ctx);
+    for (int j = 0; j < nF; j++) {
+      x.comp[j] = F[j];
+      x.out_slot[j] = j;
+    }
+    x.out = ctx->A + (long long)ctx->tz0 * ctx->ny * ctx->P;
+    x.out_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
+    x.tw = ctx->tw;
+    Timed t(ctx, KIND_XFWD, s);
+    CKL(launch_xfwd(ctx->L[0], x, nF, s));
+  }
+  return adjoint_planes(ctx, rho, dJdrho, F, W, nW, s);
+}
+
+}  // namespace
+
+int tm_set_stencil_objective(tm_ctx* ctx, long long K, const long long* row_ptr, const int* comp,
+                             const long long* cell, const double* a, const double* c, void* stream) {
+  if (!ctx) return TM_ERR_ARG;
+  if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
+  if (K < 0 || (K > 0 && (!row_ptr || !comp || !cell || !a || !c))) return fail(ctx, TM_ERR_ARG, "null array");
+  if (K > 0x7fffffffLL) return fail(ctx, TM_ERR_SIZE, "too many rows");
+  const long long ocells = out_cells(ctx), plane = (long long)ctx->ny * ctx->nx;
+  const long long E = K > 0 ? row_ptr[K] : 0;
+  if (K > 0 && row_ptr[0] != 0) return fail(ctx, TM_ERR_ARG, "row_ptr[0] must be 0");
+  for (long long k = 0; k < K; k++) {
+    if (row_ptr[k + 1] < row_ptr[k]) return fail(ctx, TM_ERR_ARG, "row_ptr must not decrease");
+    if (!isfinite(c[k])) return fail(ctx, TM_ERR_ARG, "row weights must be finite");
+  }
+  int comps = 0, z0 = ctx->nz, z1 = 0;
+  std::vector<long long> idx(E);
+  for (long long e = 0; e < E; e++) {
+    if (comp[e] < 0 || comp[e] > 2 || cell[e] < 0 || cell[e] >= ocells || !isfinite(a[e]))
+      return fail(ctx, TM_ERR_ARG, "entry %lld: component, cell or coefficient out of range", e);
+    idx[e] = comp[e] * ocells + cell[e];
+    comps |= 1 << comp[e];
+    const int z = (int)(cell[e] / plane);
+    z0 = z < z0 ? z : z0;
+    z1 = z + 1 > z1 ? z + 1 : z1;
+  }
+  // column form: entries ordered by value index, then by row
+  std::vector<long long> rowof(E), ord(E);
+  for (long long k = 0; k < K; k++)
+    for (long long e = row_ptr[k]; e < row_ptr[k + 1]; e++) rowof[e] = k;
+  for (long long e = 0; e < E; e++) ord[e] = e;
+  std::stable_sort(ord.begin(), ord.end(), [&](long long x, long long y) { return idx[x] < idx[y]; });
+  std::vector<long long> cp, cidx;
+  std::vector<int> crow(E);
+  std::vector<double> ca(E);
+  for (long long q = 0; q < E; q++) {
+    const long long e = ord[q];
+    if (q == 0 || idx[e] != idx[ord[q - 1]]) {
+      cp.push_back(q);
+      cidx.push_back(idx[e]);
+    }
+    crow[q] = (int)rowof[e];
+    ca[q] = a[e];
+  }
+  cp.push_back(E);
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = S(stream);
+  free_stencil(ctx);
+  const size_t fb = 3 * (size_t)ocells * sizeof(float);
+  if (!ctx->sH) CK(cudaMalloc(&ctx->sH, fb));
+  if (!ctx->sgH) CK(cudaMalloc(&ctx->sgH, fb));
+  CK(cudaMemsetAsync(ctx->sgH, 0, fb, s));
+  const long long U = (long long)cidx.size();
+  auto up = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(dst, bytes > 0 ? bytes : 8);
+    if (e == cudaSuccess && bytes > 0) e = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, s);
+    return e;
+  };
+  CK(up((void**)&ctx->s_rp, row_ptr, K > 0 ? (K + 1) * sizeof(long long) : 0));
+  CK(up((void**)&ctx->s_idx, idx.data(), E * sizeof(long long)));
+  CK(up((void**)&ctx->s_a, a, E * sizeof(double)));
+  CK(up((void**)&ctx->s_c, c, K * sizeof(double)));
+  CK(up((void**)&ctx->s_cp, cp.data(), cp.size() * sizeof(long long)));
+  CK(up((void**)&ctx->s_cidx, cidx.data(), U * sizeof(long long)));
+  CK(up((void**)&ctx->s_crow, crow.data(), E * sizeof(int)));
+  CK(up((void**)&ctx->s_ca, ca.data(), E * sizeof(double)));
+  CK(cudaMalloc(&ctx->s_r, (K > 0 ? K : 1) * sizeof(double)));
+  CK(cudaMalloc(&ctx->s_part, 1024 * sizeof(double)));
+  CK(cudaStreamSynchronize(s));  // the host arrays above are released on return
+  ctx->sK = K;
+  ctx->sU = U;
+  ctx->s_comps = comps;
+  ctx->tz0 = E > 0 ? z0 : 0;
+  ctx->tz1 = E > 0 ? z1 : 0;
+  ctx->target_kind = 1;
+  ctx->have_target = true;
   return TM_OK;
 }
 
@@ -776,103 +1033,63 @@ int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, vo
   if (r) return r;
   if (!ctx->have_target) return fail(ctx, TM_ERR_STATE, "no target: call tm_set_target first");
   if (!rho || !dJdrho) return fail(ctx, TM_ERR_ARG, "null array");
-  const int np = ctx->tz1 - ctx->tz0;
-  if (np > kDirectPlanesMax)  // many target planes: the FFT z pass is cheaper
-    return tm_objective_and_gradient(ctx, rho, ctx->tmask, ctx->tHt, ctx->tHtc, ctx->tw_, J_host, dJdrho, nullptr,
-                                     stream);
   cudaStream_t s = S(stream);
-  const float* w = ctx->tw_;
-  int W[3], nW = 0;
-  for (int c = 0; c < 3; c++)
-    if (w[c] != 0.0f) W[nW++] = c;
-  if (np == 0 || nW == 0) {
-    CK(cudaMemsetAsync(ctx->Jdev, 0, sizeof(double), s));
-    CK(cudaMemsetAsync(dJdrho, 0, design_cells(ctx) * sizeof(float), s));
+  if (ctx->target_kind == 1) {
+    if ((r = evaluate_stencil(ctx, rho, dJdrho, s))) return r;
   } else {
-    // forward: x, y on the design planes; z summed directly onto the target planes
-    const bool all3 = ctx->m0_var;
-    int F[3], nF = 0;
+    const int np = ctx->tz1 - ctx->tz0;
+    if (np > kDirectPlanesMax)  // many target planes: the FFT z pass is cheaper
+      return tm_objective_and_gradient(ctx, rho, ctx->tmask, ctx->tHt, ctx->tHtc, ctx->tw_, J_host, dJdrho,
+                                       nullptr, stream);
+    const float* w = ctx->tw_;
+    int W[3], nW = 0;
     for (int c = 0; c < 3; c++)
-      if (all3 || w[c] != 0.0f) F[nF++] = c;
-    int nsl;
-    if ((r = xfwd_rho(ctx, rho, s, &nsl))) return r;
-    ConvSpec cs{};
-    cs.nin = nsl;
-    for (int i = 0; i < nsl; i++) {
-      cs.ain[i] = i;
-      cs.bin[i] = i;
-      cs.u[i] = nsl == 1 ? ctx->M0c : kUnit[i];
-    }
-    cs.nout = nF;
-    for (int o = 0; o < nF; o++) {
-      cs.bout[o] = o;
-      cs.aout[o] = o;
-      cs.v[o] = kUnit[F[o]];
-    }
-    if ((r = ypass(ctx, false, cs.nin, cs.ain, cs.bin, 0, ctx->nzd, s))) return r;
-    if ((r = zdirect(ctx, cs, 0, ctx->nzd, ctx->tz0, np, s))) return r;
-    if ((r = ypass(ctx, true, cs.nout, cs.aout, cs.bout, ctx->tz0, np, s))) return r;
-    // objective on the target rows; dJ/dH transformed along x in place
-    XInvArgs x{};
-    x.row_base = ctx->tz0 * ctx->ny;
-    x.rows = ctx->tz1 * ctx->ny;
-    x.nx = ctx->nx;
-    x.P = ctx->P;
-    x.sink = SINK_OBJECTIVE;
-    x.ncomp = nF;
-    for (int j = 0; j < nF; j++) {
-      x.comp[j] = F[j];
-      x.in_slot[j] = j;
-    }
-    x.in = ctx->A;
-    x.in_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
-    x.H_cstride = out_cells(ctx);
-    x.mask = ctx->tmask;
-    x.Ht = ctx->tHt;
-    x.Ht_cstride = out_cells(ctx);
-    for (int c = 0; c < 3; c++) {
-      x.Htc[c] = ctx->tHtc[c];
-      x.w[c] = w[c];
-    }
-    x.adj_out = ctx->A;
-    x.Jpart = ctx->Jpart;
-    x.ny = ctx->ny;
-    x.tw = ctx->tw;
-    {
-      Timed t(ctx, KIND_XINV, s);
-      CKL(launch_xinv(ctx->L[0], x, s));
-    }
-    {
-      Timed t(ctx, KIND_OTHER, s);
-      const int nblk = (np * ctx->ny + xinv_rows_per_block() - 1) / xinv_rows_per_block();
-      CKL(launch_j_finalize(ctx->Jpart, nF * nblk, ctx->Jdev, s));
-    }
-    // adjoint: y on the target planes, z summed directly onto the design planes
-    ConvSpec ca{};
-    if (!ctx->m0_var) {
-      ca.nin = nW;
-      for (int i = 0; i < nW; i++) {
-        int j = 0;
-        while (F[j] != W[i]) j++;
-        ca.ain[i] = j;
-        ca.bin[i] = j;
-        ca.u[i] = kUnit[W[i]];
-      }
-      ca.nout = 1;
-      ca.bout[0] = ca.bin[0];
-      ca.aout[0] = ca.ain[0];
-      ca.v[0] = ctx->M0c;
+      if (w[c] != 0.0f) W[nW++] = c;
+    if (np == 0 || nW == 0) {
+      CK(cudaMemsetAsync(ctx->Jdev, 0, sizeof(double), s));
+      CK(cudaMemsetAsync(dJdrho, 0, design_cells(ctx) * sizeof(float), s));
     } else {
-      ca.nin = ca.nout = 3;
-      for (int i = 0; i < 3; i++) {
-        ca.ain[i] = ca.bin[i] = ca.bout[i] = ca.aout[i] = i;
-        ca.u[i] = ca.v[i] = kUnit[i];
+      int F[3], nF = 0;
+      for (int c = 0; c < 3; c++)
+        if (ctx->m0_var || w[c] != 0.0f) F[nF++] = c;
+      if ((r = forward_planes(ctx, rho, F, nF, s))) return r;
+      // objective on the target rows; dJ/dH transformed along x in place
+      XInvArgs x{};
+      x.row_base = ctx->tz0 * ctx->ny;
+      x.rows = ctx->tz1 * ctx->ny;
+      x.nx = ctx->nx;
+      x.P = ctx->P;
+      x.sink = SINK_OBJECTIVE;
+      x.ncomp = nF;
+      for (int j = 0; j < nF; j++) {
+        x.comp[j] = F[j];
+        x.in_slot[j] = j;
       }
+      x.in = ctx->A;
+      x.in_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
+      x.H_cstride = out_cells(ctx);
+      x.mask = ctx->tmask;
+      x.Ht = ctx->tHt;
+      x.Ht_cstride = out_cells(ctx);
+      for (int c = 0; c < 3; c++) {
+        x.Htc[c] = ctx->tHtc[c];
+        x.w[c] = w[c];
+      }
+      x.adj_out = ctx->A;
+      x.Jpart = ctx->Jpart;
+      x.ny = ctx->ny;
+      x.tw = ctx->tw;
+      {
+        Timed t(ctx, KIND_XINV, s);
+        CKL(launch_xinv(ctx->L[0], x, s));
+      }
+      {
+        Timed t(ctx, KIND_OTHER, s);
+        const int nblk = (np * ctx->ny + xinv_rows_per_block() - 1) / xinv_rows_per_block();
+        CKL(launch_j_finalize(ctx->Jpart, nF * nblk, ctx->Jdev, s));
+      }
+      if ((r = adjoint_planes(ctx, rho, dJdrho, F, W, nW, s))) return r;
     }
-    if ((r = ypass(ctx, false, ca.nin, ca.ain, ca.bin, ctx->tz0, np, s))) return r;
-    if ((r = zdirect(ctx, ca, ctx->tz0, np, 0, ctx->nzd, s))) return r;
-    if ((r = ypass(ctx, true, ca.nout, ca.aout, ca.bout, 0, ctx->nzd, s))) return r;
-    if ((r = xinv_chain(ctx, rho, dJdrho, ca.nout, ca.aout, s))) return r;
   }
   if (J_host) {
     CK(cudaMemcpyAsync(ctx->Jhost, ctx->Jdev, sizeof(double), cudaMemcpyDeviceToHost, s));

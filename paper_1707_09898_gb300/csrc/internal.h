@@ -141,6 +141,22 @@ int launch_mask_extent(const uint8_t* mask, int nz, long long plane, int* ext, c
 int launch_update(float* rho, const float* G, long long n, float alpha, int normalize, const unsigned int* gmax,
                   cudaStream_t s);
 
+// Quadratic stencil objective -- misc.cu
+struct StencilArgs {
+  long long K, U;                                 // rows, distinct referenced values
+  const long long* rp;                            // [K+1] row pointers into idx, a
+  const long long* idx;                           // value index into H / gH ([3][nz][ny][nx] flattened)
+  const double *a, *c;                            // entry coefficients, row weights [K]
+  const long long *cp, *cidx;                     // column form: [U+1] pointers, [U] value indices
+  const int* crow;                                // row of each column entry
+  const double* ca;                               // coefficient of each column entry
+  const float* H;
+  float* gH;
+  double *r, *part, *J;                           // [K] row values, [nblk] partials, J
+  int nblk;
+};
+int launch_stencil(const StencilArgs& a, cudaStream_t s);
+
 // host mirrors of the digit-reversal maps
 int host_pos_of_k(int L, int k);
 int host_k_of_pos(int L, int pos);

@@ -130,7 +130,51 @@ __global__ void k_reduce_slices(float* scratch, int nb) {
 std::mutex g_noalloc_mu;
 float* g_noalloc_ptr[256] = {nullptr};  // device address of g_noalloc_scratch, per device ordinal
 
+
+// Quadratic stencil objective (Sec. "Optimization of field and gradient"): row k of
+// a sparse matrix S picks a linear combination r_k = sum_e a_e H[idx_e] of field
+// values; J = sum_k c_k r_k^2 (float64 block partials), then dJ/dH at every
+// referenced value from the column form of S: sum over its rows of 2 c_k r_k a.
+__global__ void k_stencil_rows(long long K, const long long* rp, const long long* idx, const double* a,
+                               const double* c, const float* H, double* r, double* part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K; k += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (long long e = rp[k]; e < rp[k + 1]; e++) v += a[e] * (double)H[idx[e]];
+    r[k] = v;
+    s += c[k] * v * v;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_stencil_cols(long long U, const long long* cp, const long long* cidx, const int* crow,
+                               const double* ca, const double* c, const double* r, float* gH) {
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < U; u += (long long)gridDim.x * blockDim.x) {
+    double g = 0.0;
+    for (long long e = cp[u]; e < cp[u + 1]; e++) {
+      const int k = crow[e];
+      g += 2.0 * c[k] * r[k] * ca[e];
+    }
+    gH[cidx[u]] = (float)g;
+  }
+}
 }  // namespace
+
+int launch_stencil(const StencilArgs& a, cudaStream_t s) {
+  k_stencil_rows<<<a.nblk, 256, 0, s>>>(a.K, a.rp, a.idx, a.a, a.c, a.H, a.r, a.part);
+  k_j_finalize<<<1, 256, 0, s>>>(a.part, a.nblk, a.J);
+  const long long b = (a.U + 255) / 256;
+  k_stencil_cols<<<(int)(b < 1 ? 1 : (b > 4096 ? 4096 : b)), 256, 0, s>>>(a.U, a.cp, a.cidx, a.crow, a.ca, a.c, a.r,
+                                                                         a.gH);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
 
 int launch_j_finalize(const double* part, int n, double* J, cudaStream_t s) {
   k_j_finalize<<<1, 256, 0, s>>>(part, n, J);

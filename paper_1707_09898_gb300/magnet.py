@@ -136,6 +136,18 @@ class Magnet:
         self._ck(self.L.tm_set_target(self.h, _ptr(mask), _ptr(Ht), _lib.c_float3(*[float(v) for v in Ht_const]),
                                       _lib.c_float3(*[float(v) for v in w]), _stream(self.device)))
 
+    def set_stencil_objective(self, row_ptr, comp, cell, a, c):
+        """Prepare J = sum_k c_k (sum_e a_e H[comp_e][cell_e])^2 for evaluate() (host arrays:
+        row_ptr [K+1], per entry comp, cell = z*ny*nx + y*nx + x, a; per row c)."""
+        import numpy as np
+
+        rp = np.ascontiguousarray(row_ptr, np.int64)
+        arrs = (np.ascontiguousarray(comp, np.int32), np.ascontiguousarray(cell, np.int64),
+                np.ascontiguousarray(a, np.float64), np.ascontiguousarray(c, np.float64))
+        K = len(rp) - 1
+        ptr = [x.ctypes.data_as(ctypes.c_void_p) for x in (rp,) + arrs]
+        self._ck(self.L.tm_set_stencil_objective(self.h, K, *ptr, _stream(self.device)))
+
     def evaluate(self, rho, G=None, sync=True):
         """(J, dJ/drho) for the prepared target. J is a float if sync else None."""
         rho = self._dev(rho, F32, self.design_shape, "rho")

@@ -175,6 +175,24 @@ def paper_problem(box=5):
         ht_const=(0.0, 0.0, 0.0), w=(0.0, 0.0, -0.5))
 
 
+def paper_field_gradient(beta=1e5):
+    """The paper's field-and-gradient problem (Sec. "Optimization of field and gradient"):
+    a 40 x 40 x 20 design of cubic cells of edge 30 (in the length unit of beta) magnetized
+    along +z (M0 = (0, 0, 1), rho = 1 at the start), the target plane two cells above its
+    top face (z = 21 of a 40 x 40 x 22 grid),
+    a centred 20 x 20 field region on it and a one-cell strip along three of its sides
+    (x = 9 and x = 30 with outward normals -x and +x, y = 30 with normal +y).
+    Returns (workload, field mask [ny][nx] bool, strip [(y, x, axis, sign)], beta); axis
+    0 = y, 1 = x."""
+    wl = Workload(
+        name="paper_field_gradient", n_out=(40, 40, 22), nzd=20, cellsize=(30.0, 30.0, 30.0), rho_kind="const",
+        rho_const=1.0, ms=1.0, mask_z=21, mask_xy=(10, 30, 10, 30), ht_const=(0.0, 0.0, 0.0), w=(0.0, 0.0, -0.5))
+    field = wl.mask()[21].astype(bool)
+    strip = ([(y, 9, 1, -1) for y in range(10, 30)] + [(y, 30, 1, 1) for y in range(10, 30)] +
+             [(30, x, 0, 1) for x in range(10, 30)])
+    return wl, field, strip, beta
+
+
 # Warm-start specifications: the target of each optimisation drawn from a seed.
 CONFIG5_TRAIN_SEEDS = range(10000, 12000)
 CONFIG5_HELDOUT_SEEDS = range(20000, 20200)
