@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-oneshot", action="store_true", help="skip timing the one-shot call")
+    ap.add_argument("--separate-yz", action="store_true",
+                    help="prepared path: y and direct z passes as separate kernels (default: fused)")
+    ap.add_argument("--m0", choices=["const", "vmf"], default="const",
+                    help="magnetization: constant (0, 0, Ms), or spatially varying (von Mises-Fisher)")
     return ap.parse_args()
 
 
@@ -159,7 +163,7 @@ def _need(v, u):
     return sum(1 for x in c if x != 0)
 
 
-def alg_bytes(wl, L, direct=True):
+def alg_bytes(wl, L, direct=True, fused=True):
     """Algorithmic bytes per launch of each kernel kind for the objective+gradient step.
 
     Half spectra kx = 0..L/2 only (no padding); components actually carried: with a
@@ -167,6 +171,9 @@ def alg_bytes(wl, L, direct=True):
     the z pass) and the adjoint leaves as one (contracted with M0); the forward carries
     the weighted field components, the adjoint their dJ/dH. Only the np planes that hold
     target cells carry the forward field after the z pass and the adjoint source before it.
+    fused: the prepared path's y transform of the design planes fused with the direct z
+    sum (forward onto one target plane with one output; adjoint always): those kinds read
+    or write the x-transformed design planes, the tensor once, and the target planes.
     """
     nx, ny, nz = wl.n_out
     nzd = wl.nzd
@@ -186,24 +193,35 @@ def alg_bytes(wl, L, direct=True):
         tf = ta = 6
     npl = int(wl.mask().any(axis=(1, 2)).sum())  # planes holding target cells
     s8 = 8
-    if direct:  # z summed in (kx, ky, z) space: the x/y-transformed tensor over nzd offsets
-        Tzc = nzd * (Ly // 2 + 1) * K * 4
-        zf = s8 * K * Ly * (fin * nzd + fout * npl) + tf * Tzc
-        za = s8 * K * Ly * (ain * npl + aout * nzd) + ta * Tzc
-    else:
-        zf = s8 * K * Ly * (fin * nzd + fout * npl) + tf * Tcomp
-        za = s8 * K * Ly * (ain * npl + aout * nzd) + ta * Tcomp
-    yf = (s8 * fin * nzd * K * (ny + Ly) + s8 * ain * npl * K * (ny + Ly)) / 2
-    yi = (s8 * fout * npl * K * (Ly + ny) + s8 * aout * nzd * K * (Ly + ny)) / 2
+    m0 = 0 if const else 12 * nzd * ny * nx  # the varying M0 is read by the first and last pass
+    Tzc = nzd * (Ly // 2 + 1) * K * 4        # x/y-transformed tensor over nzd offsets, one component
     obj = s8 * npl * ny * K * fout * 2 + npl * ny * nx  # spectra in, adjoint spectra out, mask
-    chain = s8 * aout * nzd * ny * K + 8 * nzd * ny * nx
-    return {
-        "x_forward": 4 * nzd * ny * nx + s8 * fin * nzd * ny * K,
-        "y_forward": yf,
-        "z_pass": (zf + za) / 2,
-        "y_inverse": yi,
-        "x_inverse": (obj + chain) / 2,
-    }
+    chain = s8 * aout * nzd * ny * K + 8 * nzd * ny * nx + m0
+    out = {"x_forward": 4 * nzd * ny * nx + m0 + s8 * fin * nzd * ny * K, "x_inverse": (obj + chain) / 2}
+    fuse_f = direct and fused and npl == 1 and fout == 1
+    fuse_a = direct and fused
+    if fuse_f:
+        out["yz_forward"] = s8 * fin * nzd * ny * K + tf * Tzc + s8 * fout * npl * Ly * K
+    if fuse_a:
+        out["zy_adjoint"] = s8 * ain * npl * Ly * K + ta * Tzc + s8 * aout * nzd * ny * K
+    # separate y passes: forward of the design planes (unless fused) and of the adjoint
+    # source planes; inverse of the target planes and of the design planes (unless fused)
+    yf = [s8 * ain * npl * K * (ny + Ly)] + ([] if fuse_f else [s8 * fin * nzd * K * (ny + Ly)])
+    yi = [s8 * fout * npl * K * (Ly + ny)] + ([] if fuse_a else [s8 * aout * nzd * K * (Ly + ny)])
+    out["y_forward"] = sum(yf) / len(yf)
+    out["y_inverse"] = sum(yi) / len(yi)
+    zl = []
+    if not fuse_f:
+        zl.append(s8 * K * Ly * (fin * nzd + fout * npl) + tf * (Tzc if direct else Tcomp))
+    if not fuse_a:
+        zl.append(s8 * K * Ly * (ain * npl + aout * nzd) + ta * (Tzc if direct else Tcomp))
+    if zl:
+        out["z_pass"] = sum(zl) / len(zl)
+    return out
+
+
+def m0_of(wl):
+    return wl.M0_const() if wl.m0_kind == "const" else wl.M0_field()
 
 
 def sha1(path):
@@ -224,7 +242,7 @@ def cpu_baseline(wl, args):
     t_setup = time.time() - t0
     rho = wl.rho()
     t0 = time.perf_counter()
-    J, G, _ = O.objective_and_gradient(op, rho, wl.M0_const(), wl.p, wl.mask(), wl.Ht_const_vec(), wl.w)
+    J, G, _ = O.objective_and_gradient(op, rho, m0_of(wl), wl.p, wl.mask(), wl.Ht_const_vec(), wl.w)
     dt = time.perf_counter() - t0
     return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one full float64 evaluation (objective + adjoint gradient) of the {wl.n_out[0]}^3 workload, "
@@ -238,7 +256,7 @@ def run_reference(args):
         return
     from paper_1707_09898_gb300 import workloads as W
 
-    wl = W.config4(args.n)
+    wl = W.config4(args.n, args.m0)
     from oracle import convolution as C
     from oracle import objective as O
     from oracle import optimizer as P
@@ -250,10 +268,10 @@ def run_reference(args):
     steps = max(1, min(args.steps, 3))
     warm = min(args.warmup, 1)
     for _ in range(warm):
-        J, G, _ = O.objective_and_gradient(op, rho, wl.M0_const(), wl.p, wl.mask(), wl.Ht_const_vec(), wl.w)
+        J, G, _ = O.objective_and_gradient(op, rho, m0_of(wl), wl.p, wl.mask(), wl.Ht_const_vec(), wl.w)
     t0 = time.perf_counter()
     for _ in range(steps):
-        J, G, _ = O.objective_and_gradient(op, rho, wl.M0_const(), wl.p, wl.mask(), wl.Ht_const_vec(), wl.w)
+        J, G, _ = O.objective_and_gradient(op, rho, m0_of(wl), wl.p, wl.mask(), wl.Ht_const_vec(), wl.w)
         rho = P.projected_gradient_step(rho, G, wl.alpha, True)
     dt = time.perf_counter() - t0
     v = steps / dt
@@ -285,12 +303,13 @@ def run_native(args):
     from paper_1707_09898_gb300 import Magnet
     from paper_1707_09898_gb300 import workloads as W
 
-    wl = W.config4(args.n)
+    wl = W.config4(args.n, args.m0)
     if args.impl == "cufft":
         from paper_1707_09898_gb300.cufft_pipeline import CufftMagnet as Impl
     else:
         Impl = Magnet
-    m = Impl(wl.n_out, wl.nzd, wl.cellsize, M0=wl.M0_const(), p=wl.p, device=local)
+    M0 = wl.M0_const() if wl.m0_kind == "const" else torch.from_numpy(wl.M0_field()).to(dev)
+    m = Impl(wl.n_out, wl.nzd, wl.cellsize, M0=M0, p=wl.p, device=local)
     rho0 = torch.from_numpy(wl.rho()).to(dev)
     rho = rho0.clone()
     mask = torch.from_numpy(wl.mask()).to(dev)
@@ -298,6 +317,10 @@ def run_native(args):
     G = torch.empty_like(rho)
 
     prepared = hasattr(m, "set_target")
+    reuse = {"reuse_max": True} if prepared else {}  # max|G| from the chain-rule pass
+    fused = prepared and not args.separate_yz
+    if prepared:
+        m.set_fused(fused)
     if prepared:
         m.set_target(mask, Ht_const=Htc, w=w)
 
@@ -306,7 +329,7 @@ def run_native(args):
             m.evaluate(rho, G=G, sync=False)
         else:
             m.objective_and_gradient(rho, mask, Ht_const=Htc, w=w, G=G, sync=False)
-        m.optimize_step(rho, G, wl.alpha, True)
+        m.optimize_step(rho, G, wl.alpha, True, **reuse)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -362,7 +385,7 @@ def run_native(args):
         e0.record(s)
         for _ in range(args.steps):
             m.objective_and_gradient(rho, mask, Ht_const=Htc, w=w, G=G, sync=False)
-            m.optimize_step(rho, G, wl.alpha, True)
+            m.optimize_step(rho, G, wl.alpha, True, **reuse)
         e1.record(s)
         torch.cuda.synchronize()
         oneshot = {"value": args.steps / (e0.elapsed_time(e1) / 1e3), "unit": UNIT,
@@ -378,7 +401,7 @@ def run_native(args):
     L = m.fft_lengths()
     roof = None
     if prof:
-        ab = alg_bytes(wl, L, direct=prepared)
+        ab = alg_bytes(wl, L, direct=prepared, fused=fused)
         kind = max((k for k in prof if prof[k][1] > 0 and k in ab), key=lambda k: prof[k][0])
         t_launch = prof[kind][0] / prof[kind][1] / 1e3
         achieved = ab[kind] / t_launch / 1e9
@@ -398,6 +421,7 @@ def run_native(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "impl": args.impl,
         "config": {"workload": wl.name, "cells": list(wl.n_out), "fft": list(L), "step": "objective+gradient+update",
+                   "yz": "fused" if fused else "separate",
                    "parallelism": f"replicas{ws}", "l2": "working set (>2 GB) larger than L2; no flush"},
         "clocks": ck, "gpu_launches": (int(round(launches_per_step * args.steps)) if launches_per_step else None),
         "roofline": roof, "e2e": e2e, "J_first": J0, "oneshot": oneshot,

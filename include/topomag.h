@@ -161,6 +161,10 @@ int tm_get_objective(tm_ctx* ctx, double* J_host, void* stream);
  * "Methodology"): rho <- clip(rho - alpha G / max|G|, 0, 1) if normalize != 0
  * (no change when max|G| = 0), else rho <- clip(rho - alpha G, 0, 1).
  * rho [nzd][ny][nx] updated in place; G = dJdrho [nzd][ny][nx].
+ * normalize == 2: as 1, but when dJdrho is the array the last evaluation on this
+ * context wrote (tm_evaluate, tm_objective_and_gradient, tm_stray_field_adjoint),
+ * max|G| is taken from that evaluation instead of being recomputed; the caller
+ * promises not to have changed dJdrho since. Any other array: recomputed.
  */
 int tm_optimize_step(tm_ctx* ctx, float* rho, const float* dJdrho, float alpha, int normalize, void* stream);
 
@@ -189,16 +193,25 @@ int tm_optimize_step_noalloc(float* rho, const float* dJdrho, long long n, float
                              void* stream);
 
 /*
+ * Prepared path (tm_evaluate): 1 (default) fuses the y transform of the design
+ * planes with the direct z sum (forward onto a single target plane, one field
+ * component; adjoint always), so the y spectra of the design planes never reach
+ * memory; 0 runs the y and z passes separately. Same convolution either way.
+ */
+int tm_set_fused(tm_ctx* ctx, int on);
+
+/*
  * Per-kernel timing. tm_profile(ctx, 1) starts recording a CUDA event pair on
  * the launch stream around every kernel the context launches (and resets the
  * record); tm_profile(ctx, 0) stops. tm_profile_read synchronises on the
  * recorded events and returns, per kernel kind, the summed event time in ms and
  * the launch count. Kinds: 0 x forward, 1 y forward, 2 z pass (forward z FFT,
- * tensor product, inverse z FFT), 3 y inverse, 4 x inverse (+ objective or
- * chain rule), 5 other (objective reduction, update).
+ * tensor product, inverse z FFT; or the direct z sum), 3 y inverse, 4 x inverse
+ * (+ objective or chain rule), 5 other (reductions, update), 6 fused y forward +
+ * direct z sum, 7 fused direct z sum + y inverse (tm_set_fused).
  */
 int tm_profile(tm_ctx* ctx, int on);
-int tm_profile_read(tm_ctx* ctx, double ms[6], int launches[6]);
+int tm_profile_read(tm_ctx* ctx, double ms[8], int launches[8]);
 
 /*
  * Inspection (tests): the float64 tensor N at the offsets of the non-negative

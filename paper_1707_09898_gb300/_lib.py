@@ -45,7 +45,8 @@ _SIGS = {
     "tm_optimize_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_float, ctypes.c_int, vp]),
     "tm_optimize_step_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_longlong, ctypes.c_float, ctypes.c_int, vp]),
     "tm_profile": (ctypes.c_int, [vp, ctypes.c_int]),
-    "tm_profile_read": (ctypes.c_int, [vp, ctypes.c_double * 6, ctypes.c_int * 6]),
+    "tm_set_fused": (ctypes.c_int, [vp, ctypes.c_int]),
+    "tm_profile_read": (ctypes.c_int, [vp, ctypes.c_double * 8, ctypes.c_int * 8]),
     "tm_debug_tensor_octant": (ctypes.c_int, [vp, vp, vp]),
     "tm_debug_tensor_spectrum": (ctypes.c_int, [vp, vp, vp]),
     # warm-start network kernels (include/topomag_net.h)

@@ -50,6 +50,12 @@ struct tm_ctx {
   int nJpart = 0;
   double* Jdev = nullptr;
   unsigned int* gmax = nullptr;
+  const float* gmax_of = nullptr;  // the array whose max |.| gmax holds (set by the chain-rule pass)
+  unsigned int* Jcount = nullptr;  // blocks of the objective pass done (re-armed by the last one)
+  bool fuse_yz = true;             // prepared path: y transform fused with the direct z sum
+  float2* yzpart = nullptr;        // [z chunks][Ly][P] partial planes of the fused forward
+  int yzpart_chunks = 0;
+  int nsm = 0;
   int* ext = nullptr;       // [2]: z range of the target planes
   double* Jhost = nullptr;  // pinned
   // per-kernel event timing (tm_profile)
@@ -112,6 +118,9 @@ void free_stencil(tm_ctx* c) {
 
 void free_grid(tm_ctx* c) {
   free_stencil(c);
+  cudaFree(c->yzpart);
+  c->yzpart = nullptr;
+  c->yzpart_chunks = 0;
   cudaFree(c->sH);
   cudaFree(c->sgH);
   c->sH = c->sgH = nullptr;
@@ -140,7 +149,7 @@ void free_grid(tm_ctx* c) {
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-enum { KIND_XFWD = 0, KIND_YFWD, KIND_ZPASS, KIND_YINV, KIND_XINV, KIND_OTHER, KIND_N };
+enum { KIND_XFWD = 0, KIND_YFWD, KIND_ZPASS, KIND_YINV, KIND_XINV, KIND_OTHER, KIND_YZF, KIND_ZYA, KIND_N };
 
 // Records a start/stop event pair around one launch when profiling is on.
 struct Timed {
@@ -354,6 +363,93 @@ int zdirect(tm_ctx* ctx, const ConvSpec& cs, int zi0, int nzi, int zo0, int nzo,
   return TM_OK;
 }
 
+// forward y transform of the design planes fused with the direct z sum onto the
+// single target plane (cs.nout == 1)
+int yz_forward(tm_ctx* ctx, const ConvSpec& cs, int zo, cudaStream_t s) {
+  const int Ly = ctx->L[1];
+  const long long P = ctx->P;
+  const int chunks = (int)(P / TB);
+  int nch = ctx->nsm / chunks;  // one resident block per SM: a single wave
+  nch = nch < 1 ? 1 : (nch > ctx->nzd ? ctx->nzd : nch);
+  const int zchunk = (ctx->nzd + nch - 1) / nch;
+  nch = (ctx->nzd + zchunk - 1) / zchunk;
+  if (nch > ctx->yzpart_chunks) {
+    cudaFree(ctx->yzpart);
+    ctx->yzpart = nullptr;
+    ctx->yzpart_chunks = 0;
+    CK(cudaMalloc(&ctx->yzpart, (size_t)nch * Ly * P * sizeof(float2)));
+    ctx->yzpart_chunks = nch;
+  }
+  YZArgs y{};
+  y.in = ctx->A;
+  y.in_cstride = (long long)ctx->nz * ctx->ny * P;
+  y.in_zstride = (long long)ctx->ny * P;
+  y.out = ctx->B;
+  y.out_cstride = (long long)ctx->nz * Ly * P;
+  y.out_slot = cs.bout[0];
+  y.part = ctx->yzpart;
+  y.P = ctx->P;
+  y.n_in = ctx->ny;
+  y.nin = cs.nin;
+  for (int i = 0; i < cs.nin; i++) {
+    y.in_slot[i] = cs.ain[i];
+    coef6(y.coef[i], cs.v[0], cs.u[i]);
+    y.need[i] = 0;
+    for (int c = 0; c < 6; c++)
+      if (y.coef[i][c] != 0.0f) y.need[i] |= 1 << c;
+  }
+  y.Tz = ctx->Tz;
+  y.Tdz = (long long)(Ly / 2 + 1) * P;
+  y.Tc = (long long)ctx->nz * y.Tdz;
+  y.zin0 = 0;
+  y.nzin = ctx->nzd;
+  y.zchunk = zchunk;
+  y.zout = zo;
+  y.tw = ctx->tw + ctx->L[0];
+  Timed t(ctx, KIND_YZF, s);
+  CKL(launch_yz_fwd(Ly, y, s));
+  return TM_OK;
+}
+
+// direct z sum from the source planes [zi0, zi0 + nzi) fused with the inverse y
+// transform of every design plane
+int zy_adjoint(tm_ctx* ctx, const ConvSpec& cs, int zi0, int nzi, cudaStream_t s) {
+  const int Ly = ctx->L[1];
+  const long long P = ctx->P;
+  ZYArgs z{};
+  z.src = ctx->B;
+  z.src_cstride = (long long)ctx->nz * Ly * P;
+  z.src_zstride = (long long)Ly * P;
+  z.out = ctx->A;
+  z.out_cstride = (long long)ctx->nz * ctx->ny * P;
+  z.out_zstride = (long long)ctx->ny * P;
+  z.P = ctx->P;
+  z.n_out = ctx->ny;
+  z.nin = cs.nin;
+  z.nout = cs.nout;
+  for (int i = 0; i < cs.nin; i++) z.in_slot[i] = cs.bin[i];
+  for (int o = 0; o < cs.nout; o++) {
+    z.out_slot[o] = cs.aout[o];
+    for (int i = 0; i < cs.nin; i++) {
+      coef6(z.coef[o][i], cs.v[o], cs.u[i]);
+      z.need[o][i] = 0;
+      for (int c = 0; c < 6; c++)
+        if (z.coef[o][i][c] != 0.0f) z.need[o][i] |= 1 << c;
+    }
+  }
+  z.Tz = ctx->Tz;
+  z.Tdz = (long long)(Ly / 2 + 1) * P;
+  z.Tc = (long long)ctx->nz * z.Tdz;
+  z.zin0 = zi0;
+  z.nzin = nzi;
+  z.zout0 = 0;
+  z.nzout = ctx->nzd;
+  z.tw = ctx->tw + ctx->L[0];
+  Timed t(ctx, KIND_ZYA, s);
+  CKL(launch_zy_adj(Ly, z, s));
+  return TM_OK;
+}
+
 // forward x pass of the magnetization: rho^p (constant M0, contracted later) -> A slot 0,
 // or rho^p M0_c (varying M0) -> A slots 0, 1, 2. Returns the number of slots written.
 int xfwd_rho(tm_ctx* ctx, const float* rho, cudaStream_t s, int* nslots) {
@@ -404,6 +500,7 @@ int xinv_chain(tm_ctx* ctx, const float* rho, float* G, int ncomp, const int* sl
   x.tw = ctx->tw;
   Timed t(ctx, KIND_XINV, s);
   CKL(launch_xinv(ctx->L[0], x, s));
+  ctx->gmax_of = G;
   return TM_OK;
 }
 
@@ -452,6 +549,9 @@ int tm_create(tm_ctx** out, int device) {
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->Jdev, sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->gmax, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->Jcount, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->Jcount, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->ext, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->Jhost, sizeof(double));
   if (e != cudaSuccess) {
@@ -469,6 +569,7 @@ void tm_destroy(tm_ctx* ctx) {
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   cudaFree(ctx->Jdev);
   cudaFree(ctx->gmax);
+  cudaFree(ctx->Jcount);
   cudaFree(ctx->ext);
   if (ctx->Jhost) cudaFreeHost(ctx->Jhost);
   delete ctx;
@@ -722,6 +823,7 @@ int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask
   int slots[3] = {0, 1, 2};
   if (nW == 0) {
     CK(cudaMemsetAsync(dJdrho, 0, design_cells(ctx) * sizeof(float), s));
+    ctx->gmax_of = nullptr;
   } else if (!ctx->m0_var) {  // inputs: weighted components; output contracted with M0
     cs.nin = nW;
     for (int i = 0; i < nW; i++) {
@@ -817,8 +919,12 @@ int forward_planes(tm_ctx* ctx, const float* rho, const int* F, int nF, cudaStre
     cs.aout[o] = o;
     cs.v[o] = kUnit[F[o]];
   }
-  if ((r = ypass(ctx, false, cs.nin, cs.ain, cs.bin, 0, ctx->nzd, s))) return r;
-  if ((r = zdirect(ctx, cs, 0, ctx->nzd, ctx->tz0, np, s))) return r;
+  if (ctx->fuse_yz && np == 1 && nF == 1) {
+    if ((r = yz_forward(ctx, cs, ctx->tz0, s))) return r;
+  } else {
+    if ((r = ypass(ctx, false, cs.nin, cs.ain, cs.bin, 0, ctx->nzd, s))) return r;
+    if ((r = zdirect(ctx, cs, 0, ctx->nzd, ctx->tz0, np, s))) return r;
+  }
   return ypass(ctx, true, cs.nout, cs.aout, cs.bout, ctx->tz0, np, s);
 }
 
@@ -851,8 +957,12 @@ int adjoint_planes(tm_ctx* ctx, const float* rho, float* dJdrho, const int* F, c
     }
   }
   if ((r = ypass(ctx, false, ca.nin, ca.ain, ca.bin, ctx->tz0, np, s))) return r;
-  if ((r = zdirect(ctx, ca, ctx->tz0, np, 0, ctx->nzd, s))) return r;
-  if ((r = ypass(ctx, true, ca.nout, ca.aout, ca.bout, 0, ctx->nzd, s))) return r;
+  if (ctx->fuse_yz) {
+    if ((r = zy_adjoint(ctx, ca, ctx->tz0, np, s))) return r;
+  } else {
+    if ((r = zdirect(ctx, ca, ctx->tz0, np, 0, ctx->nzd, s))) return r;
+    if ((r = ypass(ctx, true, ca.nout, ca.aout, ca.bout, 0, ctx->nzd, s))) return r;
+  }
   return xinv_chain(ctx, rho, dJdrho, ca.nout, ca.aout, s);
 }
 
@@ -888,6 +998,7 @@ int evaluate_stencil(tm_ctx* ctx, const float* rho, float* dJdrho, cudaStream_t 
   if (ctx->sK == 0 || nW == 0) {
     CK(cudaMemsetAsync(ctx->Jdev, 0, sizeof(double), s));
     CK(cudaMemsetAsync(dJdrho, 0, design_cells(ctx) * sizeof(float), s));
+    ctx->gmax_of = nullptr;
     return TM_OK;
   }
   const StencilArgs sa = stencil_args(ctx);
@@ -1048,6 +1159,7 @@ int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, vo
     if (np == 0 || nW == 0) {
       CK(cudaMemsetAsync(ctx->Jdev, 0, sizeof(double), s));
       CK(cudaMemsetAsync(dJdrho, 0, design_cells(ctx) * sizeof(float), s));
+    ctx->gmax_of = nullptr;
     } else {
       int F[3], nF = 0;
       for (int c = 0; c < 3; c++)
@@ -1077,16 +1189,13 @@ int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, vo
       }
       x.adj_out = ctx->A;
       x.Jpart = ctx->Jpart;
+      x.Jcount = ctx->Jcount;  // J summed by the pass's last block
+      x.Jout = ctx->Jdev;
       x.ny = ctx->ny;
       x.tw = ctx->tw;
       {
         Timed t(ctx, KIND_XINV, s);
         CKL(launch_xinv(ctx->L[0], x, s));
-      }
-      {
-        Timed t(ctx, KIND_OTHER, s);
-        const int nblk = (np * ctx->ny + xinv_rows_per_block() - 1) / xinv_rows_per_block();
-        CKL(launch_j_finalize(ctx->Jpart, nF * nblk, ctx->Jdev, s));
       }
       if ((r = adjoint_planes(ctx, rho, dJdrho, F, W, nW, s))) return r;
     }
@@ -1117,11 +1226,19 @@ int tm_optimize_step(tm_ctx* ctx, float* rho, const float* dJdrho, float alpha, 
   cudaStream_t s = S(stream);
   const long long n = design_cells(ctx);
   Timed t(ctx, KIND_OTHER, s);
-  if (normalize) {
+  // normalize 2: reuse max|G| of the evaluation that wrote dJdrho (the caller has not changed it)
+  if (normalize && !(normalize == 2 && ctx->gmax_of == dJdrho)) {
     CK(cudaMemsetAsync(ctx->gmax, 0, sizeof(unsigned int), s));
     CKL(launch_absmax(dJdrho, n, ctx->gmax, s));
+    ctx->gmax_of = dJdrho;
   }
-  CKL(launch_update(rho, dJdrho, n, alpha, normalize, ctx->gmax, s));
+  CKL(launch_update(rho, dJdrho, n, alpha, normalize != 0, ctx->gmax, s));
+  return TM_OK;
+}
+
+int tm_set_fused(tm_ctx* ctx, int on) {
+  if (!ctx) return TM_ERR_ARG;
+  ctx->fuse_yz = on != 0;
   return TM_OK;
 }
 
@@ -1132,7 +1249,7 @@ int tm_profile(tm_ctx* ctx, int on) {
   return TM_OK;
 }
 
-int tm_profile_read(tm_ctx* ctx, double ms[6], int launches[6]) {
+int tm_profile_read(tm_ctx* ctx, double ms[8], int launches[8]) {
   if (!ctx || !ms || !launches) return fail(ctx, TM_ERR_ARG, "null argument");
   CK(cudaSetDevice(ctx->device));
   for (int k = 0; k < KIND_N; k++) {

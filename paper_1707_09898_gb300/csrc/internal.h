@@ -58,6 +58,8 @@ struct XInvArgs {
   float Htc[3], w[3];
   float2* adj_out;          // [slot][rows][P], aliases in
   double* Jpart;            // [3][gridDim.x]
+  unsigned int* Jcount;     // OBJECTIVE, optional: blocks done; the last one sums Jpart into *Jout
+  double* Jout;
   const float* rho;         // [rows][nx]
   const float* M0v;         // [3][rows][nx] or null (contracted slot)
   long long M0v_cstride;
@@ -120,6 +122,42 @@ struct ZDirArgs {
   int zin0, nzin, zout0, nzout;
 };
 int launch_zdir(const ZDirArgs& a, cudaStream_t s);
+
+// Fused y transform + direct z sum (k_yzfused.cu).
+// Adjoint: from few source planes of B to the real-y rows of every output plane of A.
+struct ZYArgs {
+  const float2* src;                        // B [slot][z][Ly][P]
+  long long src_cstride, src_zstride;
+  float2* out;                              // A [slot][z][ny][P]
+  long long out_cstride, out_zstride;
+  int P, n_out;                             // kx columns (multiple of TB); valid y rows
+  int nin, nout, in_slot[3], out_slot[3];
+  float coef[3][3][6];
+  int need[3][3];
+  const float* Tz;                          // [6][nz][Ly/2+1][P]
+  long long Tc, Tdz;
+  int zin0, nzin, zout0, nzout;
+  const float2* tw;                         // W_Ly
+};
+// Forward: the design planes of A onto one plane and one output of B.
+struct YZArgs {
+  const float2* in;                         // A [slot][z][ny][P]
+  long long in_cstride, in_zstride;
+  float2* out;                              // B [slot][z][Ly][P]
+  long long out_cstride;
+  int out_slot;
+  float2* part;                             // [z chunks][Ly][P]
+  int P, n_in;
+  int nin, in_slot[3];
+  float coef[3][6];                         // s_i = v^T N u_i of the single output
+  int need[3];
+  const float* Tz;
+  long long Tc, Tdz;
+  int zin0, nzin, zchunk, zout;
+  const float2* tw;
+};
+int launch_zy_adj(int L, const ZYArgs& a, cudaStream_t s);
+int launch_yz_fwd(int L, const YZArgs& a, cudaStream_t s);
 
 int launch_xfwd(int L, const XFwdArgs& a, int ncomp, cudaStream_t s);
 int launch_xinv(int L, const XInvArgs& a, cudaStream_t s);

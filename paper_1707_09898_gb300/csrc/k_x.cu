@@ -228,6 +228,35 @@ __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
   }
 }
 
+// Called by every thread of every block after thread 0 wrote the block's J partial:
+// the last block to finish sums the partials in index order (the order of a separate
+// one-block reduction) into *Jout and re-arms the counter.
+__device__ void finish_j(const XInvArgs& a) {
+  __shared__ unsigned int last;
+  __shared__ double r2[kNT];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(a.Jcount, 1u) == gridDim.x * gridDim.y - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int n = gridDim.x * gridDim.y;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += kNT) s += __ldcg(a.Jpart + i);
+  r2[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kNT / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) r2[threadIdx.x] += r2[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *a.Jout = r2[0];
+    *a.Jcount = 0u;
+  }
+}
+
 template <int L, int SINK, int MINB>
 __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
   constexpr int S = plan_stages(L);
@@ -356,6 +385,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
       const long long lo = (long long)a.ext[0] * a.ny, hi = (long long)a.ext[1] * a.ny;
       if (row0 + ROWS <= lo || row0 >= hi) {
         if (threadIdx.x == 0) a.Jpart[jc * gridDim.x + blockIdx.x] = 0.0;
+        if (a.Jcount) finish_j(a);
         return;
       }
     }
@@ -420,6 +450,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
     for (int w = 0; w < kNT / 32; w++) s += red[w];
     a.Jpart[jc * gridDim.x + blockIdx.x] = s;
   }
+  if (a.Jcount) finish_j(a);
   if (!a.adj_out) return;
   cx<float>* adj = reinterpret_cast<cx<float>*>(a.adj_out) + a.in_slot[jc] * a.in_cstride;
   if (!any_mask) {  // the adjoint source vanishes on all rows of this block

@@ -1,0 +1,264 @@
+// The y transform fused with the direct z sum, so that the y spectra of the design
+// planes never travel through memory.
+//
+// After the x transform the convolution of Sec. "Discretization", Eq.
+// (convolution) is, per column (kx, ky), a 1-D convolution along z with the
+// tensor transformed along x and y only (see k_zdir.cu). When the target
+// occupies few planes:
+//   forward:  out(kx, ky, zo) = sum_z s(kx, ky, zo - z) Y(kx, ky, z), where Y is the
+//             y transform of the x-transformed design plane z. k_yz_fwd transforms
+//             each design plane of its chunk of z in shared memory and accumulates
+//             s Y in registers; k_yz_reduce sums the chunks in a fixed order.
+//   adjoint:  Y(kx, ky, z) = sum_p s(kx, ky, z - zp) src(kx, ky, zp) for every design
+//             plane z, followed by the inverse y transform: k_zy_adj computes Y in
+//             the loader of the inverse transform and writes the real-y rows.
+// Same discrete convolution as the unfused passes, without the round trip of the
+// y spectra of all design planes through HBM.
+#include "fft.cuh"
+#include "internal.h"
+
+namespace tmk {
+
+namespace {
+
+// s = a - i b for (o, i) at offset dz of column (kx, ky); t points at Tz + kyf*P + kx
+__device__ __forceinline__ void tensor_s(const float* t, long long Tc, long long Tdz, float sy, int dz,
+                                         const float* coef, int need, float& a, float& b) {
+  const int adz = dz < 0 ? -dz : dz;
+  const float sz = dz < 0 ? -1.0f : 1.0f;
+  const float* p = t + adz * Tdz;
+  a = 0.0f;
+  b = 0.0f;
+  if (need & 1) a += coef[0] * p[0];
+  if (need & 2) a += coef[1] * p[Tc];
+  if (need & 4) a += coef[2] * p[2 * Tc];
+  if (need & 8) a += coef[3] * sy * p[3 * Tc];
+  if (need & 16) b += coef[4] * sz * p[4 * Tc];
+  if (need & 32) b += coef[5] * sy * sz * p[5 * Tc];
+}
+
+// SIMPLE: one input, one source plane, one tensor component c (its sign under y and z
+// reflection folded in), so each element is one source load and one tensor load with no
+// loop: all loads of a thread are in flight together.
+template <int L, bool SIMPLE>
+__global__ void __launch_bounds__(kNT, 2) k_zy_adj(ZYArgs a, int c) {
+  constexpr int S = plan_stages(L);
+  extern __shared__ __align__(16) unsigned char smem[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
+  cx<float>* tile = tw + L;
+  load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
+  const int kx0 = blockIdx.x * TB;
+  const int z = a.zout0 + blockIdx.y;
+  const int o = blockIdx.z;
+  const cx<float>* src = reinterpret_cast<const cx<float>*>(a.src);
+  cx<float>* out = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[o] * a.out_cstride + z * a.out_zstride + kx0;
+  __syncthreads();
+  dit_last_load<float, L, kNT>(tile, [&](int pos, int line) {
+    const int ky = k_of_pos<L>(pos);
+    const bool lo = ky <= L / 2;
+    const int kyf = lo ? ky : L - ky;
+    const float sy = lo ? 1.0f : -1.0f;
+    const int kx = kx0 + line;
+    const float* t = a.Tz + kyf * (long long)a.P + kx;
+    const long long so = (long long)pos * a.P + kx;
+    if constexpr (SIMPLE) {
+      const int dz = z - a.zin0;
+      const int adz = dz < 0 ? -dz : dz;
+      const cx<float> v = src[a.in_slot[0] * a.src_cstride + a.zin0 * a.src_zstride + so];
+      float f = a.coef[o][0][c] * t[c * a.Tc + adz * a.Tdz];
+      if (c == 3 || c == 5) f *= sy;
+      if (c >= 4 && dz < 0) f = -f;
+      return c >= 4 ? mk(f * v.y, -f * v.x) : mk(f * v.x, f * v.y);  // (-i f) v for xz, yz
+    }
+    cx<float> acc = zero<float>();
+    for (int p = 0; p < a.nzin; p++) {
+      const int zp = a.zin0 + p;
+      for (int i = 0; i < a.nin; i++) {
+        const cx<float> v = src[a.in_slot[i] * a.src_cstride + zp * a.src_zstride + so];
+        float sa, sb;
+        tensor_s(t, a.Tc, a.Tdz, sy, z - zp, a.coef[o][i], a.need[o][i], sa, sb);
+        acc = acc + mk(sa * v.x + sb * v.y, sa * v.y - sb * v.x);
+      }
+    }
+    return acc;
+  });
+  __syncthreads();
+  DitRange<float, L, kNT, 1, S - 1>::run(tile, tw);
+  dit_stage0_store<float, L, kNT>(tile, tw, [&](int pos, int line, cx<float> v) {
+    if (pos < a.n_out) out[(long long)pos * a.P + line] = v;
+  });
+}
+
+// Forward: one output plane, one output; block (chunk of kx, chunk of z planes) of
+// NTF threads (twice the FFT kernels' block: half the sums per thread, twice the warps).
+constexpr int NTF = 2 * kNT;
+template <int L, bool SIMPLE>
+__global__ void __launch_bounds__(NTF, 1) k_yz_fwd(YZArgs a, int c) {
+  constexpr int S = plan_stages(L);
+  using SL = StageShape<L, S - 1>;
+  constexpr int R = SL::R, ITER = (SL::NU + NTF - 1) / NTF;
+  extern __shared__ __align__(16) unsigned char smem[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
+  cx<float>* tile = tw + L;
+  load_twiddles<float, NTF>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
+  const int kx0 = blockIdx.x * TB;
+  const int zb0 = a.zin0 + blockIdx.y * a.zchunk;
+  const int zb1 = min(zb0 + a.zchunk, a.zin0 + a.nzin);
+  cx<float> acc[ITER][R];
+#pragma unroll
+  for (int it = 0; it < ITER; it++)
+#pragma unroll
+    for (int q = 0; q < R; q++) acc[it][q] = zero<float>();
+  const cx<float>* in0 = reinterpret_cast<const cx<float>*>(a.in);
+  for (int z = zb0; z < zb1; z++) {
+    for (int i = 0; i < (SIMPLE ? 1 : a.nin); i++) {
+      const cx<float>* in = in0 + a.in_slot[i] * a.in_cstride + z * a.in_zstride + kx0;
+      __syncthreads();
+      dif_stage0_load<float, L, NTF>(tile, tw, [&](int pos, int line) {
+        return pos < a.n_in ? in[(long long)pos * a.P + line] : zero<float>();
+      });
+      __syncthreads();
+      DifRange<float, L, NTF, 1, S - 1>::run(tile, tw);
+      // last stage in registers, then s(zo - z) times the spectrum into the sums
+      const int dz = a.zout - z;
+#pragma unroll
+      for (int it = 0; it < ITER; it++) {
+        const int u = it * NTF + threadIdx.x;
+        if (SL::NU % NTF == 0 || u < SL::NU) {
+          const int line = u % TB, g = u / TB;
+          cx<float> v[R];
+#pragma unroll
+          for (int q = 0; q < R; q++) v[q] = tile[tidx<false>(g * R + q, line)];
+          Dft<float, R, false>::run(v);
+          const int kb = k_of_group<L>(g);
+          const int kx = kx0 + line;
+#pragma unroll
+          for (int q = 0; q < R; q++) {
+            const int ky = kb + q * (L / R);
+            const bool lo = ky <= L / 2;
+            const float* t = a.Tz + (lo ? ky : L - ky) * (long long)a.P + kx;
+            if constexpr (SIMPLE) {
+              const int adz = dz < 0 ? -dz : dz;
+              float f = a.coef[0][c] * t[c * a.Tc + adz * a.Tdz];
+              if ((c == 3 || c == 5) && !lo) f = -f;
+              if (c >= 4 && dz < 0) f = -f;
+              acc[it][q] = acc[it][q] + (c >= 4 ? mk(f * v[q].y, -f * v[q].x) : mk(f * v[q].x, f * v[q].y));
+            } else {
+              float sa, sb;
+              tensor_s(t, a.Tc, a.Tdz, lo ? 1.0f : -1.0f, dz, a.coef[i], a.need[i], sa, sb);
+              acc[it][q] = acc[it][q] + mk(sa * v[q].x + sb * v[q].y, sa * v[q].y - sb * v[q].x);
+            }
+          }
+        }
+      }
+    }
+  }
+  // partial of this z chunk, at the spectrum's positions
+  cx<float>* part = reinterpret_cast<cx<float>*>(a.part) + (long long)blockIdx.y * L * a.P + kx0;
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * NTF + threadIdx.x;
+    if (SL::NU % NTF == 0 || u < SL::NU) {
+      const int line = u % TB, g = u / TB;
+#pragma unroll
+      for (int q = 0; q < R; q++) part[(long long)(g * R + q) * a.P + line] = acc[it][q];
+    }
+  }
+}
+
+// out[pos][kx] = sum over z chunks of the partials, in chunk order
+__global__ void k_yz_reduce(const float2* part, int nchunks, long long plane, float2* out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < plane;
+       e += (long long)gridDim.x * blockDim.x) {
+    float2 s = part[e];
+    for (int c = 1; c < nchunks; c++) {
+      const float2 v = part[(long long)c * plane + e];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    out[e] = s;
+  }
+}
+
+template <int L>
+size_t fused_smem() {
+  return (size_t)(L + L * TB) * sizeof(float2);
+}
+
+// the single tensor component of (o, i) = (0, 0), or -1
+int single_component(const int need) { return (need != 0 && (need & (need - 1)) == 0) ? __builtin_ctz(need) : -1; }
+
+template <int L, bool SIMPLE>
+int launch_adj(const ZYArgs& a, int c, cudaStream_t s) {
+  const size_t sm = fused_smem<L>();
+  static bool init = false;
+  if (!init) {
+    if (cudaFuncSetAttribute(k_zy_adj<L, SIMPLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        cudaSuccess)
+      return -1;
+    init = true;
+  }
+  k_zy_adj<L, SIMPLE><<<dim3(a.P / TB, a.nzout, a.nout), kNT, sm, s>>>(a, c);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int L>
+int run_zy_adj(const ZYArgs& a, cudaStream_t s) {
+  if (a.nzout <= 0 || a.nout <= 0) return 0;
+  const int c = single_component(a.need[0][0]);
+  if (a.nin == 1 && a.nout == 1 && a.nzin == 1 && c >= 0) return launch_adj<L, true>(a, c, s);
+  return launch_adj<L, false>(a, -1, s);
+}
+
+template <int L, bool SIMPLE>
+int launch_fwd(const YZArgs& a, int c, int nch, cudaStream_t s) {
+  const size_t sm = fused_smem<L>();
+  static bool init = false;
+  if (!init) {
+    if (cudaFuncSetAttribute(k_yz_fwd<L, SIMPLE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        cudaSuccess)
+      return -1;
+    init = true;
+  }
+  k_yz_fwd<L, SIMPLE><<<dim3(a.P / TB, nch), NTF, sm, s>>>(a, c);
+  return 0;
+}
+
+template <int L>
+int run_yz_fwd(const YZArgs& a, cudaStream_t s) {
+  const int nch = (a.nzin + a.zchunk - 1) / a.zchunk;
+  const int c = single_component(a.need[0]);
+  if ((a.nin == 1 && c >= 0 ? launch_fwd<L, true>(a, c, nch, s) : launch_fwd<L, false>(a, -1, nch, s)) != 0)
+    return -1;
+  const long long plane = (long long)L * a.P;
+  const long long b = (plane + 255) / 256;
+  k_yz_reduce<<<(int)(b > 2048 ? 2048 : b), 256, 0, s>>>(reinterpret_cast<const float2*>(a.part), nch, plane,
+                                                        a.out + a.out_slot * a.out_cstride + a.zout * plane);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+int launch_zy_adj(int L, const ZYArgs& a, cudaStream_t s) {
+  switch (L) {
+#define TM_CASE(LL) \
+  case LL:          \
+    return run_zy_adj<LL>(a, s);
+    TM_FOR_EACH_L(TM_CASE)
+#undef TM_CASE
+  }
+  return -2;
+}
+
+int launch_yz_fwd(int L, const YZArgs& a, cudaStream_t s) {
+  switch (L) {
+#define TM_CASE(LL) \
+  case LL:          \
+    return run_yz_fwd<LL>(a, s);
+    TM_FOR_EACH_L(TM_CASE)
+#undef TM_CASE
+  }
+  return -2;
+}
+
+}  // namespace tmk

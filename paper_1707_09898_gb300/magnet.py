@@ -136,6 +136,10 @@ class Magnet:
         self._ck(self.L.tm_set_target(self.h, _ptr(mask), _ptr(Ht), _lib.c_float3(*[float(v) for v in Ht_const]),
                                       _lib.c_float3(*[float(v) for v in w]), _stream(self.device)))
 
+    def set_fused(self, on=True):
+        """Prepared path: fuse the y transform with the direct z sum (default) or not."""
+        self._ck(self.L.tm_set_fused(self.h, int(bool(on))))
+
     def set_stencil_objective(self, row_ptr, comp, cell, a, c):
         """Prepare J = sum_k c_k (sum_e a_e H[comp_e][cell_e])^2 for evaluate() (host arrays:
         row_ptr [K+1], per entry comp, cell = z*ny*nx + y*nx + x, a; per row c)."""
@@ -163,21 +167,23 @@ class Magnet:
         self._ck(self.L.tm_get_objective(self.h, ctypes.byref(J), _stream(self.device)))
         return J.value
 
-    def optimize_step(self, rho, G, alpha, normalize=True):
-        self._ck(self.L.tm_optimize_step(self.h, _ptr(rho), _ptr(G), float(alpha), int(bool(normalize)),
-                                         _stream(self.device)))
+    def optimize_step(self, rho, G, alpha, normalize=True, reuse_max=False):
+        """rho <- clip(rho - alpha G / max|G|, 0, 1) (normalize) or clip(rho - alpha G, 0, 1).
+        reuse_max: take max|G| from the evaluation that wrote G (G unchanged since)."""
+        mode = (2 if reuse_max else 1) if normalize else 0
+        self._ck(self.L.tm_optimize_step(self.h, _ptr(rho), _ptr(G), float(alpha), mode, _stream(self.device)))
         return rho
 
     # -- per-kernel event timing ---------------------------------------------
-    KINDS = ("x_forward", "y_forward", "z_pass", "y_inverse", "x_inverse", "other")
+    KINDS = ("x_forward", "y_forward", "z_pass", "y_inverse", "x_inverse", "other", "yz_forward", "zy_adjoint")
 
     def profile(self, on=True):
         self._ck(self.L.tm_profile(self.h, int(bool(on))))
 
     def profile_read(self):
         """{kind: (total ms, launches)} over the launches recorded since profile(True)."""
-        ms = (ctypes.c_double * 6)()
-        n = (ctypes.c_int * 6)()
+        ms = (ctypes.c_double * 8)()
+        n = (ctypes.c_int * 8)()
         self._ck(self.L.tm_profile_read(self.h, ms, n))
         return {k: (ms[i], n[i]) for i, k in enumerate(self.KINDS)}
 

@@ -438,6 +438,51 @@ def inference_ms(net, wl, reps=20):
     return e0.elapsed_time(e1) / reps
 
 
+def conv_profile(net, N=4, reps=10):
+    """CUDA-event time per launch of each layer's forward, backward-data and backward-weight
+    convolution at batch N on the network's grid (activations from one forward pass), with
+    the algorithmic rate 2 * voxels * 27 * Cin * Cout FLOP per launch."""
+    D, H, W = net.size
+    x = torch.zeros((N, D, H, W, C_IN), dtype=BF16, device=net.dev)
+    net.forward(x)
+    net.backward(torch.zeros((N, D, H, W), dtype=F32, device=net.dev))
+    L, s = net.L, _stream(net.dev)
+    dims = {"e1a": 1, "e1b": 1, "e2a": 2, "e2b": 2, "b1": 4, "b2": 4, "d2a": 2, "d2b": 2, "d1a": 1, "d1b": 1}
+    inp = {"e1a": "x", "e1b": "e1a", "e2a": "p1", "e2b": "e2a", "b1": "p2", "b2": "b1", "d2a": "u2", "d2b": "d2a",
+           "d1a": "u1", "d1b": "d1a"}
+    out = []
+    for name, cin, cout in LAYERS:
+        f = dims[name]
+        dd = (N, D // f, H // f, W // f)
+        e = net.P[name]
+        src, dst, g = net.A[inp[name]], net.A[name], net.G.get(name, None)
+        g = torch.zeros(dd + (cout,), dtype=F32, device=net.dev) if g is None or g.shape[-1] != cout else g
+        gin = torch.empty(dd + (cin,), dtype=F32, device=net.dev)
+        calls = {
+            "fwd": lambda: L.tmn_conv3d_forward(_p(src), _p(e["wf"]), _p(e["b"]), _p(dst), *dd, cin, cout, 1, s),
+            "bwd_data": lambda: L.tmn_conv3d_backward_data(_p(g), _p(e["wb"]), _p(gin), *dd, cin, cout, 0, s),
+            "bwd_weight": lambda: L.tmn_conv3d_backward_weight(_p(src), _p(g), _p(e["gw"]), _p(e["gb"]),
+                                                               _p(net.work), net.work.numel(), *dd, cin, cout, s)}
+        flop = 2.0 * np.prod(dd) * 27 * cin * cout
+        row = {"layer": name, "cin": cin, "cout": cout, "voxels": int(np.prod(dd))}
+        for kind, fn in calls.items():
+            if kind == "bwd_data" and name == "e1a":
+                continue
+            for _ in range(2):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row[kind + "_ms"] = ms
+            row[kind + "_tflops"] = flop / (ms * 1e-3) / 1e12
+        out.append(row)
+    return out
+
+
 def save_params(path, params):
     np.savez_compressed(path, **{f"{k}.{j}": v[j] for k, v in params.items() for j in (0, 1)})
 
@@ -462,7 +507,13 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default="warmstart_run")
     ap.add_argument("--weights", default=None, help="evaluate these trained weights (.npz) instead of training")
+    ap.add_argument("--profile-convs", action="store_true", help="only time the convolutions (batch --batch)")
     a = ap.parse_args(argv)
+    if a.profile_convs:
+        rows = conv_profile(WarmStartNet(), N=a.batch)
+        for r in rows:
+            print(json.dumps(r))
+        return
     os.makedirs(a.out, exist_ok=True)
     t0 = time.perf_counter()
 

@@ -140,12 +140,13 @@ def config3():
         ht_kind="normal", ht_seed=5, w=(1.0, 1.0, 1.0))
 
 
-def config4(n):
-    """Throughput workload: n^3 design = output grid, n/4 x n/4 target patch on the top layer."""
+def config4(n, m0="const"):
+    """Throughput workload: n^3 design = output grid, n/4 x n/4 target patch on the top layer.
+    m0 = "vmf": a spatially varying magnetization (von Mises-Fisher about +z, kappa = 10, seed 8)."""
     x0, x1 = _centered(n, n // 4)
     return Workload(
-        name=f"c4_{n}cube", n_out=(n, n, n), nzd=n, rho_seed=7,
-        mask_z=n - 1, mask_xy=(x0, x1, x0, x1), ht_const=(0.0, 0.0, 0.2))
+        name=f"c4_{n}cube" + ("" if m0 == "const" else "_" + m0), n_out=(n, n, n), nzd=n, rho_seed=7,
+        m0_kind=m0, m0_seed=8, mask_z=n - 1, mask_xy=(x0, x1, x0, x1), ht_const=(0.0, 0.0, 0.2))
 
 
 def small(n_out, nzd, cellsize=(1e-3, 1e-3, 1e-3), seed=11, m0_kind="const", w=(0.0, 0.0, 1.0),

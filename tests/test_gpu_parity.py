@@ -258,3 +258,62 @@ def test_cufft_comparison_pipeline_matches_oracle():
     Jr, Gr, _ = O.objective_and_gradient(op, rho, wl.M0_const(), wl.p, mask, wl.Ht_const_vec(), wl.w)
     assert abs(J - Jr) <= 1e-5 * abs(Jr)
     assert rel_l2(G.cpu().numpy(), Gr) <= 1e-4
+
+
+def test_optimize_step_reuses_the_evaluated_max_only_for_that_array():
+    from paper_1707_09898_gb300 import Magnet
+
+    wl = W.config1()
+    m = Magnet(wl.n_out, wl.nzd, wl.cellsize, M0=wl.M0_const(), p=wl.p, device=0)
+    m.set_target(torch.from_numpy(wl.mask()).to(DEV), Ht_const=tuple(float(v) for v in wl.Ht_const_vec()), w=wl.w)
+    rho = torch.from_numpy(wl.rho()).to(DEV)
+    G = torch.empty_like(rho)
+    m.evaluate(rho, G=G)
+    r1 = m.optimize_step(rho.clone(), G, 0.1, True, reuse_max=True)
+    r2 = m.optimize_step(rho.clone(), G, 0.1, True)
+    assert torch.equal(r1, r2)
+    G2 = G * 0.5  # another array: its own max is computed, so the step is the same
+    r3 = m.optimize_step(rho.clone(), G2, 0.1, True, reuse_max=True)
+    assert torch.allclose(r3, r2, atol=1e-6)
+    assert not torch.equal(r2, rho)
+
+
+@pytest.mark.parametrize("case", ["c1", "ragged", "vmf", "three_components", "two_planes"])
+def test_fused_and_separate_yz_passes_agree(case):
+    """The prepared path with the y transform fused into the direct z sum (default) and with
+    separate passes: the same convolution, float32 rounding apart; both against the oracle.
+    c1 / ragged: both directions fused; vmf, three_components: forward separate (three field
+    components), adjoint fused with three spectra; two_planes: forward separate, adjoint
+    fused from two source planes."""
+    from paper_1707_09898_gb300 import Magnet
+
+    if case == "c1":
+        wl = W.config1()
+    elif case == "vmf":
+        wl = W.small((14, 11, 13), 9, seed=61, m0_kind="vmf", w=(1.0, 1.0, 1.0), ht_kind="normal")
+    elif case == "three_components":
+        wl = W.small((18, 10, 12), 8, seed=62, w=(0.5, 1.0, 2.0), ht_kind="normal")
+    else:
+        wl = W.small((20, 12, 15), 9, seed=63)
+    mask = wl.mask()
+    if case == "two_planes":
+        mask[-2] = mask[-1]
+    M0 = wl.M0_field() if wl.m0_kind != "const" else wl.M0_const()
+    m = Magnet(wl.n_out, wl.nzd, wl.cellsize, M0=torch.from_numpy(M0).to(DEV) if wl.m0_kind != "const" else M0,
+               p=wl.p, device=0)
+    Ht = wl.Ht_field()
+    m.set_target(torch.from_numpy(mask).to(DEV), Ht=torch.from_numpy(Ht).to(DEV), w=wl.w)
+    rho = torch.from_numpy(wl.rho()).to(DEV)
+    out = {}
+    for fused in (True, False):
+        m.set_fused(fused)
+        J, G = m.evaluate(rho)
+        out[fused] = (J, G.cpu().numpy())
+    (Jf, Gf), (Js, Gs) = out[True], out[False]
+    assert abs(Jf - Js) <= 1e-6 * abs(Js)
+    assert np.linalg.norm(Gf - Gs) <= 1e-5 * np.linalg.norm(Gs)
+    op = C.FFTOperator(C.Geometry(wl.n_out, wl.nzd, wl.cellsize))
+    Jr, Gr, _ = O.objective_and_gradient(op, wl.rho(), M0, wl.p, mask, Ht, wl.w)
+    for J, G in out.values():
+        assert abs(J - Jr) <= 1e-5 * abs(Jr)
+        assert np.linalg.norm(G - Gr) <= 1e-4 * np.linalg.norm(Gr)
