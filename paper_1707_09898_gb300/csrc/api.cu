@@ -622,7 +622,7 @@ int tm_set_grid(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[
   }
   CK(cudaMalloc(&ctx->zcol, zc.size() * sizeof(int2)));
   CK(cudaMemcpy(ctx->zcol, zc.data(), zc.size() * sizeof(int2), cudaMemcpyHostToDevice));
-  const int rpb = xinv_rows_per_block();
+  const int rpb = xobj_rows_per_block() < xinv_rows_per_block() ? xobj_rows_per_block() : xinv_rows_per_block();
   ctx->nJpart = 3 * ((ctx->nz * ctx->ny + rpb - 1) / rpb);
   CK(cudaMalloc(&ctx->Jpart, ctx->nJpart * sizeof(double)));
   ctx->have_grid = true;
@@ -1193,9 +1193,9 @@ int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, vo
       x.Jout = ctx->Jdev;
       x.ny = ctx->ny;
       x.tw = ctx->tw;
-      {
+      {  // few target rows: the latency-bound compact kernel (one warp per row pair)
         Timed t(ctx, KIND_XINV, s);
-        CKL(launch_xinv(ctx->L[0], x, s));
+        CKL(launch_xobj(ctx->L[0], x, s));
       }
       if ((r = adjoint_planes(ctx, rho, dJdrho, F, W, nW, s))) return r;
     }

@@ -165,6 +165,10 @@ int launch_yfwd(int L, const YArgs& a, int ncomp, cudaStream_t s);
 int launch_yinv(int L, const YArgs& a, int ncomp, cudaStream_t s);
 int launch_zpass(int L, const ZArgs& a, cudaStream_t s);
 int xinv_rows_per_block();
+// Objective on few target rows, compact warp-per-row-pair transforms (k_xobj.cu);
+// needs a.Jcount / a.Jout (J summed by the last block) and a.adj_out.
+int launch_xobj(int L, const XInvArgs& a, cudaStream_t s);
+int xobj_rows_per_block();
 size_t zpass_smem(int L);
 
 // Tensor setup (float64) -- tensor.cu
