@@ -4,10 +4,10 @@
 //   half spectra of two real rows -> inverse x transform -> H, J, g -> forward x
 //   transform of g -> half spectra of the adjoint source.
 // The target rows are few (one or a few planes), so this kernel is bound by latency,
-// not bandwidth: one warp per pair of rows runs an iterative mixed-radix Stockham
-// transform (radix 4, 2, 3 stages in natural order, loops rather than unrolled
-// stages) in its own shared-memory buffers, synchronising only the warp. The code is
-// a few hundred instructions for every length.
+// not bandwidth: a group of four warps per pair of rows runs an iterative mixed-radix
+// Stockham transform (radix 4, 2, 3 stages in natural order, loops rather than
+// unrolled stages) in its own shared-memory buffers, synchronising only the group
+// (named barrier). The code is a few hundred instructions for every length.
 #include "fft.cuh"
 #include "internal.h"
 
@@ -15,28 +15,34 @@ namespace tmk {
 
 namespace {
 
-constexpr int OW = 8;  // warps (row pairs) per block
-constexpr int KI = 10;  // ceil((576 / 2 + 1) / 32): half-spectrum values per lane
-constexpr int XI = 18;  // 576 / 32: real values per lane
+constexpr int OW = 8;   // warps per block
+constexpr int GW = 4;   // warps per row pair (one transform group)
+constexpr int GT = GW * 32;
+constexpr int NG = OW / GW;  // row pairs per block
+constexpr int KI = 3;   // ceil((576 / 2 + 1) / GT): half-spectrum values per thread
+constexpr int XI = 5;   // ceil(576 / GT): real values per thread
 
 __device__ __forceinline__ cx<float> cmul(cx<float> a, cx<float> b) {
   return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ cx<float> conjf(cx<float> a) { return mk(a.x, -a.y); }
 
-// One warp: length-L transform of src into dst (natural order both), sign -1 forward,
+// barrier of the GT threads of transform group g (ids 1.. ; 0 is the block barrier)
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(GT) : "memory"); }
+
+// One group: length-L transform of src into dst (natural order both), sign -1 forward,
 // +1 inverse (unnormalised). Stockham stages: for j < L/R, the R inputs src[j + r L/R]
 // times W^(r (j mod Ns) L/(Ns R)) go through a radix-R DFT to dst[(j/Ns) Ns R + j mod
 // Ns + r Ns], Ns the product of the radices before. Returns the buffer holding the result.
-__device__ cx<float>* warp_fft(cx<float>* src, cx<float>* dst, int L, const cx<float>* tw, bool inverse) {
-  const int lane = threadIdx.x & 31;
+__device__ cx<float>* group_fft(cx<float>* src, cx<float>* dst, int L, const cx<float>* tw, bool inverse, int gt,
+                                int g) {
   int rem = L, Ns = 1;
   while (rem > 1) {
     const int R = rem % 4 == 0 ? 4 : (rem % 2 == 0 ? 2 : 3);
     const int M = L / R;
     const int step = L / (Ns * R);
 #pragma unroll 1
-    for (int j = lane; j < M; j += 32) {
+    for (int j = gt; j < M; j += GT) {
       const int k = j % Ns;
       cx<float> v[4];
 #pragma unroll
@@ -44,7 +50,7 @@ __device__ cx<float>* warp_fft(cx<float>* src, cx<float>* dst, int L, const cx<f
         if (r < R) {
           v[r] = src[j + r * M];
           if (r > 0 && k > 0) {
-            cx<float> w = tw[(r * k * step) % L];
+            cx<float> w = tw[r * k * step];
             if (inverse) w = conjf(w);
             v[r] = cmul(v[r], w);
           }
@@ -75,7 +81,7 @@ __device__ cx<float>* warp_fft(cx<float>* src, cx<float>* dst, int L, const cx<f
       for (int r = 0; r < 4; r++)
         if (r < R) dst[base + r * Ns] = y[r];
     }
-    __syncwarp();
+    group_sync(g);
     cx<float>* t = src;
     src = dst;
     dst = t;
@@ -87,48 +93,50 @@ __device__ cx<float>* warp_fft(cx<float>* src, cx<float>* dst, int L, const cx<f
 
 __global__ void __launch_bounds__(OW * 32) k_xobj(XInvArgs a, int L) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int any_mask[NG];
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  cx<float>* b0 = tw + L + warp * 2 * L;
+  const int g = warp / GW, gt = threadIdx.x - g * GT;
+  cx<float>* b0 = tw + L + g * 2 * L;
   cx<float>* b1 = b0 + L;
   for (int i = threadIdx.x; i < L; i += OW * 32) tw[i] = reinterpret_cast<const cx<float>*>(a.tw)[i];
+  if (gt == 0) any_mask[g] = 0;
   __syncthreads();
   const int jc = blockIdx.y, c = a.comp[jc];
   const float wc = a.w[c];
   const int K = L / 2 + 1;
-  const int ra = a.row_base + (blockIdx.x * OW + warp) * 2, rb = ra + 1;
+  const int ra = a.row_base + (blockIdx.x * NG + g) * 2, rb = ra + 1;
   const cx<float>* in = reinterpret_cast<const cx<float>*>(a.in) + a.in_slot[jc] * a.in_cstride;
   double jacc = 0.0;
-  if (ra < a.rows) {
+  if (ra < a.rows) {  // uniform over the group
     const bool hb = rb < a.rows;
     // Z(k) = A(k) + i B(k) over the full length, A and B extended by Hermitian symmetry;
-    // every load of the lane is issued before the first store
+    // every load of the thread is issued before the first store
     cx<float> Av[KI], Bv[KI];
 #pragma unroll
     for (int it = 0; it < KI; it++) {
-      const int k = lane + 32 * it;
+      const int k = gt + GT * it;
       Av[it] = k < K ? in[(long long)ra * a.P + k] : zero<float>();
       Bv[it] = (k < K && hb) ? in[(long long)rb * a.P + k] : zero<float>();
     }
 #pragma unroll
     for (int it = 0; it < KI; it++) {
-      const int k = lane + 32 * it;
+      const int k = gt + GT * it;
       if (k < K) {
         const cx<float> A = Av[it], B = Bv[it];
         b0[k] = mk(A.x - B.y, A.y + B.x);
         if (k > 0 && k < L - k) b0[L - k] = mk(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
       }
     }
-    __syncwarp();
-    cx<float>* z = warp_fft(b0, b1, L, tw, true);
+    group_sync(g);
+    cx<float>* z = group_fft(b0, b1, L, tw, true, gt, g);
     cx<float>* o = z == b0 ? b1 : b0;
-    int mine = 0;
-    // mask and target values of the lane's cells, all loads first
+    // mask and target values of the thread's cells, all loads first
     unsigned char mk2[XI][2];
     float ht[XI][2];
 #pragma unroll
     for (int it = 0; it < XI; it++) {
-      const int x = lane + 32 * it;
+      const int x = gt + GT * it;
 #pragma unroll
       for (int h = 0; h < 2; h++) {
         const int row = h ? rb : ra;
@@ -138,11 +146,12 @@ __global__ void __launch_bounds__(OW * 32) k_xobj(XInvArgs a, int L) {
         ht[it][h] = (ok && a.Ht) ? a.Ht[c * a.Ht_cstride + e] : a.Htc[c];
       }
     }
+    int mine = 0;
 #pragma unroll
     for (int it = 0; it < XI; it++) {
-      const int x = lane + 32 * it;
+      const int x = gt + GT * it;
       if (x < L) {
-        float g[2] = {0.0f, 0.0f};
+        float gv[2] = {0.0f, 0.0f};
         if (x < a.nx) {
           const cx<float> hv = z[x];
 #pragma unroll
@@ -151,24 +160,24 @@ __global__ void __launch_bounds__(OW * 32) k_xobj(XInvArgs a, int L) {
               mine = 1;
               const float r = (h ? hv.y : hv.x) - ht[it][h];
               jacc += (double)wc * (double)r * (double)r;
-              g[h] = 2.0f * wc * r;
+              gv[h] = 2.0f * wc * r;
             }
           }
         }
-        o[x] = mk(g[0], g[1]);
+        o[x] = mk(gv[0], gv[1]);
       }
     }
-    mine = __any_sync(0xffffffffu, mine);
+    if (mine) any_mask[g] = 1;
+    group_sync(g);
     cx<float>* adj = reinterpret_cast<cx<float>*>(a.adj_out) + a.in_slot[jc] * a.in_cstride;
-    if (!mine) {  // no target cell on these rows: the adjoint source vanishes
-      for (int k = lane; k < a.P; k += 32) {
+    if (!any_mask[g]) {  // no target cell on these rows: the adjoint source vanishes
+      for (int k = gt; k < a.P; k += GT) {
         adj[(long long)ra * a.P + k] = zero<float>();
         if (hb) adj[(long long)rb * a.P + k] = zero<float>();
       }
     } else {
-      __syncwarp();
-      cx<float>* Zg = warp_fft(o, z, L, tw, false);
-      for (int k = lane; k < a.P; k += 32) {
+      cx<float>* Zg = group_fft(o, z, L, tw, false, gt, g);
+      for (int k = gt; k < a.P; k += GT) {
         cx<float> A = zero<float>(), B = zero<float>();
         if (k < K) {
           const cx<float> Z = Zg[k], Zm = Zg[(L - k) % L];
@@ -217,7 +226,7 @@ __global__ void __launch_bounds__(OW * 32) k_xobj(XInvArgs a, int L) {
 
 }  // namespace
 
-size_t xobj_smem(int L) { return (size_t)(L + OW * 2 * L) * sizeof(float2); }
+size_t xobj_smem(int L) { return (size_t)(L + NG * 2 * L) * sizeof(float2); }
 
 int launch_xobj(int L, const XInvArgs& a, cudaStream_t s) {
   const size_t sm = xobj_smem(L);
@@ -229,12 +238,12 @@ int launch_xobj(int L, const XInvArgs& a, cudaStream_t s) {
     init = true;
   }
   const int rows = a.rows - a.row_base;
-  const int blocks = (rows + 2 * OW - 1) / (2 * OW);
+  const int blocks = (rows + 2 * NG - 1) / (2 * NG);
   if (blocks <= 0 || a.ncomp == 0 || !a.Jcount || !a.adj_out) return blocks <= 0 || a.ncomp == 0 ? 0 : -1;
   k_xobj<<<dim3(blocks, a.ncomp), OW * 32, sm, s>>>(a, L);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
-int xobj_rows_per_block() { return 2 * OW; }
+int xobj_rows_per_block() { return 2 * NG; }
 
 }  // namespace tmk

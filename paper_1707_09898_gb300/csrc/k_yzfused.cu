@@ -166,6 +166,109 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd(YZArgs a, int c) {
   }
 }
 
+
+// The single-component forward with the next design plane's input rows and tensor
+// slice copied into shared memory (cp.async, two buffers) while the current plane is
+// transformed, so the loads overlap the transform instead of following it.
+__device__ __forceinline__ void cp16(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int L>
+__global__ void __launch_bounds__(NTF, 1) k_yz_fwd_staged(YZArgs a, int c) {
+  constexpr int S = plan_stages(L);
+  using SL = StageShape<L, S - 1>;
+  constexpr int R = SL::R, ITER = (SL::NU + NTF - 1) / NTF;
+  constexpr int KY = L / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
+  cx<float>* tile = tw + L;
+  cx<float>* sin0 = tile + L * TB;                               // [2][L/2][TB] input rows
+  float* st0 = reinterpret_cast<float*>(sin0 + 2 * (L / 2) * TB);  // [2][KY][TB] tensor slice
+  load_twiddles<float, NTF>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
+  const int kx0 = blockIdx.x * TB;
+  const int zb0 = a.zin0 + blockIdx.y * a.zchunk;
+  const int zb1 = min(zb0 + a.zchunk, a.zin0 + a.nzin);
+  const cx<float>* in0 = reinterpret_cast<const cx<float>*>(a.in) + a.in_slot[0] * a.in_cstride + kx0;
+  const float* tc = a.Tz + c * a.Tc + kx0;
+  auto issue = [&](int z, int buf) {  // 16-byte copies: 8 per input row, 4 per tensor row
+    const cx<float>* src = in0 + z * a.in_zstride;
+    cx<float>* sin = sin0 + buf * (L / 2) * TB;
+    for (int q = threadIdx.x; q < a.n_in * 8; q += NTF) {
+      const int row = q >> 3, part = q & 7;
+      cp16(sin + row * TB + part * 2, src + (long long)row * a.P + part * 2);
+    }
+    const int dz = a.zout - z, adz = dz < 0 ? -dz : dz;
+    const float* t = tc + adz * a.Tdz;
+    float* stt = st0 + buf * KY * TB;
+    for (int q = threadIdx.x; q < KY * 4; q += NTF) {
+      const int row = q >> 2, part = q & 3;
+      cp16(stt + row * TB + part * 4, t + (long long)row * a.P + part * 4);
+    }
+    cp_commit();
+  };
+  cx<float> acc[ITER][R];
+#pragma unroll
+  for (int it = 0; it < ITER; it++)
+#pragma unroll
+    for (int q = 0; q < R; q++) acc[it][q] = zero<float>();
+  if (zb0 < zb1) issue(zb0, 0);
+  for (int z = zb0; z < zb1; z++) {
+    const int buf = (z - zb0) & 1;
+    __syncthreads();  // every thread is done with the other buffer and with the tile
+    if (z + 1 < zb1) {
+      issue(z + 1, buf ^ 1);
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
+    }
+    __syncthreads();  // plane z's copies of every thread have landed
+    const cx<float>* sin = sin0 + buf * (L / 2) * TB;
+    const float* stt = st0 + buf * KY * TB;
+    dif_stage0_load<float, L, NTF>(tile, tw, [&](int pos, int line) {
+      return pos < a.n_in ? sin[pos * TB + line] : zero<float>();
+    });
+    __syncthreads();
+    DifRange<float, L, NTF, 1, S - 1>::run(tile, tw);
+    const int dz = a.zout - z;
+    const float cz = (c >= 4 && dz < 0) ? -a.coef[0][c] : a.coef[0][c];
+#pragma unroll
+    for (int it = 0; it < ITER; it++) {
+      const int u = it * NTF + threadIdx.x;
+      if (SL::NU % NTF == 0 || u < SL::NU) {
+        const int line = u % TB, g = u / TB;
+        cx<float> v[R];
+#pragma unroll
+        for (int q = 0; q < R; q++) v[q] = tile[tidx<false>(g * R + q, line)];
+        Dft<float, R, false>::run(v);
+        const int kb = k_of_group<L>(g);
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+          const int ky = kb + q * (L / R);
+          const bool lo = ky <= L / 2;
+          float f = cz * stt[(lo ? ky : L - ky) * TB + line];
+          if ((c == 3 || c == 5) && !lo) f = -f;
+          acc[it][q] = acc[it][q] + (c >= 4 ? mk(f * v[q].y, -f * v[q].x) : mk(f * v[q].x, f * v[q].y));
+        }
+      }
+    }
+  }
+  cx<float>* part = reinterpret_cast<cx<float>*>(a.part) + (long long)blockIdx.y * L * a.P + kx0;
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int u = it * NTF + threadIdx.x;
+    if (SL::NU % NTF == 0 || u < SL::NU) {
+      const int line = u % TB, g = u / TB;
+#pragma unroll
+      for (int q = 0; q < R; q++) part[(long long)(g * R + q) * a.P + line] = acc[it][q];
+    }
+  }
+}
+
 // out[pos][kx] = sum over z chunks of the partials, in chunk order
 __global__ void k_yz_reduce(const float2* part, int nchunks, long long plane, float2* out) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < plane;
@@ -210,6 +313,25 @@ int run_zy_adj(const ZYArgs& a, cudaStream_t s) {
   return launch_adj<L, false>(a, -1, s);
 }
 
+template <int L>
+size_t staged_smem() {
+  return (size_t)(L + L * TB + 2 * (L / 2) * TB) * sizeof(float2) + (size_t)2 * (L / 2 + 1) * TB * sizeof(float);
+}
+
+template <int L>
+int launch_fwd_staged(const YZArgs& a, int c, int nch, cudaStream_t s) {
+  const size_t sm = staged_smem<L>();
+  static bool init = false;
+  if (!init) {
+    if (cudaFuncSetAttribute(k_yz_fwd_staged<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        cudaSuccess)
+      return -1;
+    init = true;
+  }
+  k_yz_fwd_staged<L><<<dim3(a.P / TB, nch), NTF, sm, s>>>(a, c);
+  return 0;
+}
+
 template <int L, bool SIMPLE>
 int launch_fwd(const YZArgs& a, int c, int nch, cudaStream_t s) {
   const size_t sm = fused_smem<L>();
@@ -228,7 +350,7 @@ template <int L>
 int run_yz_fwd(const YZArgs& a, cudaStream_t s) {
   const int nch = (a.nzin + a.zchunk - 1) / a.zchunk;
   const int c = single_component(a.need[0]);
-  if ((a.nin == 1 && c >= 0 ? launch_fwd<L, true>(a, c, nch, s) : launch_fwd<L, false>(a, -1, nch, s)) != 0)
+  if ((a.nin == 1 && c >= 0 ? launch_fwd_staged<L>(a, c, nch, s) : launch_fwd<L, false>(a, -1, nch, s)) != 0)
     return -1;
   const long long plane = (long long)L * a.P;
   const long long b = (plane + 255) / 256;
