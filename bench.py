@@ -197,7 +197,12 @@ def alg_bytes(wl, L, direct=True, fused=True):
     Tzc = nzd * (Ly // 2 + 1) * K * 4        # x/y-transformed tensor over nzd offsets, one component
     obj = s8 * npl * ny * K * fout * 2 + npl * ny * nx  # spectra in, adjoint spectra out, mask
     chain = s8 * aout * nzd * ny * K + 8 * nzd * ny * nx + m0
-    out = {"x_forward": 4 * nzd * ny * nx + m0 + s8 * fin * nzd * ny * K, "x_inverse": (obj + chain) / 2}
+    out = {"x_forward": 4 * nzd * ny * nx + m0 + s8 * fin * nzd * ny * K}
+    if direct:  # prepared path: the objective on the target rows is its own kind
+        out["objective"] = obj
+        out["x_inverse"] = chain
+    else:
+        out["x_inverse"] = (obj + chain) / 2
     fuse_f = direct and fused and npl == 1 and fout == 1
     fuse_a = direct and fused
     if fuse_f:

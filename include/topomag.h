@@ -208,10 +208,11 @@ int tm_set_fused(tm_ctx* ctx, int on);
  * the launch count. Kinds: 0 x forward, 1 y forward, 2 z pass (forward z FFT,
  * tensor product, inverse z FFT; or the direct z sum), 3 y inverse, 4 x inverse
  * (+ objective or chain rule), 5 other (reductions, update), 6 fused y forward +
- * direct z sum, 7 fused direct z sum + y inverse (tm_set_fused).
+ * direct z sum, 7 fused direct z sum + y inverse (tm_set_fused), 8 the objective
+ * on the target rows of the prepared path (x inverse, J, dJ/dH, x forward).
  */
 int tm_profile(tm_ctx* ctx, int on);
-int tm_profile_read(tm_ctx* ctx, double ms[8], int launches[8]);
+int tm_profile_read(tm_ctx* ctx, double ms[9], int launches[9]);
 
 /*
  * Inspection (tests): the float64 tensor N at the offsets of the non-negative

@@ -46,7 +46,7 @@ _SIGS = {
     "tm_optimize_step_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_longlong, ctypes.c_float, ctypes.c_int, vp]),
     "tm_profile": (ctypes.c_int, [vp, ctypes.c_int]),
     "tm_set_fused": (ctypes.c_int, [vp, ctypes.c_int]),
-    "tm_profile_read": (ctypes.c_int, [vp, ctypes.c_double * 8, ctypes.c_int * 8]),
+    "tm_profile_read": (ctypes.c_int, [vp, ctypes.c_double * 9, ctypes.c_int * 9]),
     "tm_debug_tensor_octant": (ctypes.c_int, [vp, vp, vp]),
     "tm_debug_tensor_spectrum": (ctypes.c_int, [vp, vp, vp]),
     # warm-start network kernels (include/topomag_net.h)

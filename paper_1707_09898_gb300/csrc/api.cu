@@ -149,7 +149,7 @@ void free_grid(tm_ctx* c) {
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
-enum { KIND_XFWD = 0, KIND_YFWD, KIND_ZPASS, KIND_YINV, KIND_XINV, KIND_OTHER, KIND_YZF, KIND_ZYA, KIND_N };
+enum { KIND_XFWD = 0, KIND_YFWD, KIND_ZPASS, KIND_YINV, KIND_XINV, KIND_OTHER, KIND_YZF, KIND_ZYA, KIND_OBJ, KIND_N };
 
 // Records a start/stop event pair around one launch when profiling is on.
 struct Timed {
@@ -1193,8 +1193,8 @@ int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, vo
       x.Jout = ctx->Jdev;
       x.ny = ctx->ny;
       x.tw = ctx->tw;
-      {  // few target rows: the latency-bound compact kernel (one warp per row pair)
-        Timed t(ctx, KIND_XINV, s);
+      {  // few target rows: the latency-bound compact kernel (one warp group per row pair)
+        Timed t(ctx, KIND_OBJ, s);
         CKL(launch_xobj(ctx->L[0], x, s));
       }
       if ((r = adjoint_planes(ctx, rho, dJdrho, F, W, nW, s))) return r;
@@ -1249,7 +1249,7 @@ int tm_profile(tm_ctx* ctx, int on) {
   return TM_OK;
 }
 
-int tm_profile_read(tm_ctx* ctx, double ms[8], int launches[8]) {
+int tm_profile_read(tm_ctx* ctx, double ms[9], int launches[9]) {
   if (!ctx || !ms || !launches) return fail(ctx, TM_ERR_ARG, "null argument");
   CK(cudaSetDevice(ctx->device));
   for (int k = 0; k < KIND_N; k++) {

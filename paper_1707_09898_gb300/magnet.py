@@ -175,15 +175,16 @@ class Magnet:
         return rho
 
     # -- per-kernel event timing ---------------------------------------------
-    KINDS = ("x_forward", "y_forward", "z_pass", "y_inverse", "x_inverse", "other", "yz_forward", "zy_adjoint")
+    KINDS = ("x_forward", "y_forward", "z_pass", "y_inverse", "x_inverse", "other", "yz_forward", "zy_adjoint",
+             "objective")
 
     def profile(self, on=True):
         self._ck(self.L.tm_profile(self.h, int(bool(on))))
 
     def profile_read(self):
         """{kind: (total ms, launches)} over the launches recorded since profile(True)."""
-        ms = (ctypes.c_double * 8)()
-        n = (ctypes.c_int * 8)()
+        ms = (ctypes.c_double * 9)()
+        n = (ctypes.c_int * 9)()
         self._ck(self.L.tm_profile_read(self.h, ms, n))
         return {k: (ms[i], n[i]) for i, k in enumerate(self.KINDS)}
 
