@@ -203,8 +203,9 @@ def alg_bytes(wl, L, direct=True, fused=True):
         out["x_inverse"] = chain
     else:
         out["x_inverse"] = (obj + chain) / 2
+    single = const and len(W) == 1 and tf == 1  # one spectrum, one tensor component
     fuse_f = direct and fused and npl == 1 and fout == 1
-    fuse_a = direct and fused
+    fuse_a = direct and fused and npl == 1 and single
     if fuse_f:
         out["yz_forward"] = s8 * fin * nzd * ny * K + tf * Tzc + s8 * fout * npl * Ly * K
     if fuse_a:

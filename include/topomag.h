@@ -194,9 +194,10 @@ int tm_optimize_step_noalloc(float* rho, const float* dJdrho, long long n, float
 
 /*
  * Prepared path (tm_evaluate): 1 (default) fuses the y transform of the design
- * planes with the direct z sum (forward onto a single target plane, one field
- * component; adjoint always), so the y spectra of the design planes never reach
- * memory; 0 runs the y and z passes separately. Same convolution either way.
+ * planes with the direct z sum when one spectrum meets one target plane (constant
+ * M0, one weighted field component): forward onto the plane, adjoint from it, so
+ * the y spectra of the design planes never reach memory; 0, or any other case,
+ * runs the y and z passes separately. Same convolution either way.
  */
 int tm_set_fused(tm_ctx* ctx, int on);
 

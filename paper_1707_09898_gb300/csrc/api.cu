@@ -957,7 +957,17 @@ int adjoint_planes(tm_ctx* ctx, const float* rho, float* dJdrho, const int* F, c
     }
   }
   if ((r = ypass(ctx, false, ca.nin, ca.ain, ca.bin, ctx->tz0, np, s))) return r;
-  if (ctx->fuse_yz) {
+  // fused only in its single-spectrum, single-component form; with several spectra or
+  // tensor components the separate passes measured faster
+  bool simple = ca.nin == 1 && ca.nout == 1 && np == 1;
+  if (simple) {
+    float c6[6];
+    coef6(c6, ca.v[0], ca.u[0]);
+    int nc = 0;
+    for (int c = 0; c < 6; c++) nc += c6[c] != 0.0f;
+    simple = nc == 1;
+  }
+  if (ctx->fuse_yz && simple) {
     if ((r = zy_adjoint(ctx, ca, ctx->tz0, np, s))) return r;
   } else {
     if ((r = zdirect(ctx, ca, ctx->tz0, np, 0, ctx->nzd, s))) return r;
