@@ -33,11 +33,20 @@ sys.path.insert(0, ROOT)
 METRIC = "adjoint-gradient evals/s at 256^3 cells, FP32 vs FP64 oracle; % of HBM peak"
 UNIT = "evals/s"
 
-# DRAM bytes (read + write) per launch of the dominant kernel kind at 256^3 from one ncu
-# capture (profiles/zdir_c4_256cube_ncu.md: the direct z sum, forward and adjoint launch
-# averaged); valid only while its source file is unchanged.
-ZPASS_TRAFFIC = {"bytes": 330.5e6, "source": "paper_1707_09898_gb300/csrc/k_zdir.cu",
-                 "source_sha1": "1e01034aaa7e24a5aeb9221956bd20b7f6d468eb"}
+# DRAM bytes (read + write) per launch of the main kernel kinds of the prepared 256^3 step,
+# each from one ncu capture (profiles/fused_yz_c4_256cube_ncu.md; the direct z sum of the
+# separate path: profiles/zdir_c4_256cube_ncu.md, forward and adjoint launch averaged);
+# valid only while the kernel's source file is unchanged.
+MEASURED_TRAFFIC = {
+    "yz_forward": {"bytes": 218.7e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
+                   "source_sha1": "72ccd07cf8a97e3f86d82e02d941f6bbccb08ec6"},
+    "zy_adjoint": {"bytes": 160.8e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
+                   "source_sha1": "72ccd07cf8a97e3f86d82e02d941f6bbccb08ec6"},
+    "x_inverse": {"bytes": 254.5e6, "source": "paper_1707_09898_gb300/csrc/k_x.cu",
+                  "source_sha1": "0286acf2119db756a84d9c4567749aa70feb8d32"},
+    "z_pass": {"bytes": 330.5e6, "source": "paper_1707_09898_gb300/csrc/k_zdir.cu",
+               "source_sha1": "1e01034aaa7e24a5aeb9221956bd20b7f6d468eb"},
+}
 
 
 def parse():
@@ -412,9 +421,10 @@ def run_native(args):
         t_launch = prof[kind][0] / prof[kind][1] / 1e3
         achieved = ab[kind] / t_launch / 1e9
         traffic = None
-        src = os.path.join(ROOT, ZPASS_TRAFFIC["source"])
-        if prepared and kind == "z_pass" and ZPASS_TRAFFIC["source_sha1"] == sha1(src):
-            traffic = ZPASS_TRAFFIC["bytes"]
+        mt = MEASURED_TRAFFIC.get(kind)
+        if prepared and args.n == 256 and args.m0 == "const" and mt and \
+                mt["source_sha1"] == sha1(os.path.join(ROOT, mt["source"])):
+            traffic = mt["bytes"]
         roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
                 "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                 "alg_bytes_per_launch": ab[kind], "ms_per_launch": t_launch * 1e3,
