@@ -31,8 +31,10 @@ int tmn_conv3d_forward(const void* in, const void* Wf, const float* bias, void* 
 int tmn_conv3d_backward_data(const float* dout, const void* Wb, float* din, int N, int D, int H, int W, int Cin,
                              int Cout, int accumulate, void* stream);
 
-/* dW[27][Cin][Cout] and db[Cout] (overwritten) from in (bfloat16) and dout (float32);
- * work: float32 scratch of work_floats >= 27*Cin*Cout elements (more allows more blocks). */
+/* dW[27][Cin][Cout] and db[Cout] (overwritten) from in (bfloat16) and dout (float32; rounded
+ * to bfloat16 for dW, as for the data gradient, float32 for db); tensor cores, float32
+ * sums in a fixed order. Cin % 16 == 0, Cout in {16, 32, 64}. work: float32 scratch of
+ * work_floats >= 27*Cin*Cout elements (more allows more blocks). */
 int tmn_conv3d_backward_weight(const void* in, const float* dout, float* dW, float* db, float* work,
                                long long work_floats, int N, int D, int H, int W, int Cin, int Cout, void* stream);
 

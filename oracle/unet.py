@@ -39,10 +39,10 @@ def conv(x, W, b):
 
 def conv_backward(x, W, g, q=None):
     """(dx, dW, db) of conv(x, W, b) for the output gradient g; q, if given, is applied to g
-    before the data gradient only (a storage precision)."""
-    dW = np.stack([np.einsum("nzyxi,nzyxo->io", _shift(x, dz, dy, dx), g) for (dz, dy, dx) in TAPS])
-    db = g.sum(axis=(0, 1, 2, 3))
+    before the data and the weight gradient (a storage precision), not before db."""
     gq = q(g) if q is not None else g
+    dW = np.stack([np.einsum("nzyxi,nzyxo->io", _shift(x, dz, dy, dx), gq) for (dz, dy, dx) in TAPS])
+    db = g.sum(axis=(0, 1, 2, 3))
     dx_ = np.zeros_like(x)
     for t, (dz, dy, dx) in enumerate(TAPS):
         dx_ += _shift(gq @ W[t].T, -dz, -dy, -dx)
@@ -102,7 +102,7 @@ def forward(params, x, q=None):
 
 def loss_and_grads(params, x, target, q=None):
     """(loss, grads) of mean (rho0 - target)^2; q as in forward(), also applied to each output
-    gradient before it enters a data-gradient product."""
+    gradient before it enters a data- or weight-gradient product."""
     rho, c = forward(params, x, q)
     n = rho.size
     loss = float(np.mean((rho - target) ** 2))

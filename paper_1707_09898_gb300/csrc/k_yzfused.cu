@@ -53,35 +53,68 @@ __global__ void __launch_bounds__(kNT, 2) k_zy_adj(ZYArgs a, int c) {
   const cx<float>* src = reinterpret_cast<const cx<float>*>(a.src);
   cx<float>* out = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[o] * a.out_cstride + z * a.out_zstride + kx0;
   __syncthreads();
-  dit_last_load<float, L, kNT>(tile, [&](int pos, int line) {
-    const int ky = k_of_pos<L>(pos);
-    const bool lo = ky <= L / 2;
-    const int kyf = lo ? ky : L - ky;
-    const float sy = lo ? 1.0f : -1.0f;
-    const int kx = kx0 + line;
-    const float* t = a.Tz + kyf * (long long)a.P + kx;
-    const long long so = (long long)pos * a.P + kx;
-    if constexpr (SIMPLE) {
-      const int dz = z - a.zin0;
-      const int adz = dz < 0 ? -dz : dz;
-      const cx<float> v = src[a.in_slot[0] * a.src_cstride + a.zin0 * a.src_zstride + so];
-      float f = a.coef[o][0][c] * t[c * a.Tc + adz * a.Tdz];
-      if (c == 3 || c == 5) f *= sy;
-      if (c >= 4 && dz < 0) f = -f;
-      return c >= 4 ? mk(f * v.y, -f * v.x) : mk(f * v.x, f * v.y);  // (-i f) v for xz, yz
-    }
-    cx<float> acc = zero<float>();
-    for (int p = 0; p < a.nzin; p++) {
-      const int zp = a.zin0 + p;
-      for (int i = 0; i < a.nin; i++) {
-        const cx<float> v = src[a.in_slot[i] * a.src_cstride + zp * a.src_zstride + so];
-        float sa, sb;
-        tensor_s(t, a.Tc, a.Tdz, sy, z - zp, a.coef[o][i], a.need[o][i], sa, sb);
-        acc = acc + mk(sa * v.x + sb * v.y, sa * v.y - sb * v.x);
+  if constexpr (SIMPLE) {
+    // first inverse stage (radix R, M = 1) with the direct z sum in its loads: the
+    // positions g R + q of a group hold ky = k(g R) + q L/R, so no per-element
+    // digit reversal; sign of the folded tensor and of odd dz precomputed
+    constexpr int s = S - 1;
+    using SS = StageShape<L, s>;
+    constexpr int R = SS::R, ITER = (SS::NU + kNT - 1) / kNT;
+    const int dz = z - a.zin0;
+    const int adz = dz < 0 ? -dz : dz;
+    const float cz = (c >= 4 && dz < 0) ? -a.coef[o][0][c] : a.coef[o][0][c];
+    const float* tcol = a.Tz + c * a.Tc + adz * a.Tdz + kx0;
+    const cx<float>* srow = src + a.in_slot[0] * a.src_cstride + a.zin0 * a.src_zstride + kx0;
+    cx<float> v[ITER][R];
+#pragma unroll
+    for (int it = 0; it < ITER; it++) {
+      const int u = it * kNT + threadIdx.x;
+      if (SS::NU % kNT == 0 || u < SS::NU) {
+        const int line = u % TB, g = u / TB;
+        const int kb = k_of_group<L>(g);
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+          const int ky = kb + q * (L / R);
+          const bool lo = ky <= L / 2;
+          const cx<float> vv = srow[(g * R + q) * a.P + line];
+          float f = cz * tcol[(lo ? ky : L - ky) * a.P + line];
+          if ((c == 3 || c == 5) && !lo) f = -f;
+          v[it][q] = c >= 4 ? mk(f * vv.y, -f * vv.x) : mk(f * vv.x, f * vv.y);  // (-i f) v for xz, yz
+        }
       }
     }
-    return acc;
-  });
+#pragma unroll
+    for (int it = 0; it < ITER; it++) {
+      const int u = it * kNT + threadIdx.x;
+      if (SS::NU % kNT == 0 || u < SS::NU) {
+        const int line = u % TB, g = u / TB;
+        Dft<float, R, true>::run(v[it]);
+#pragma unroll
+        for (int q = 0; q < R; q++) tile[tidx<false>(g * R + q, line)] = v[it][q];
+      }
+    }
+  } else {
+    dit_last_load<float, L, kNT>(tile, [&](int pos, int line) {
+      const int ky = k_of_pos<L>(pos);
+      const bool lo = ky <= L / 2;
+      const int kyf = lo ? ky : L - ky;
+      const float sy = lo ? 1.0f : -1.0f;
+      const int kx = kx0 + line;
+      const float* t = a.Tz + kyf * (long long)a.P + kx;
+      const long long so = (long long)pos * a.P + kx;
+      cx<float> acc = zero<float>();
+      for (int p = 0; p < a.nzin; p++) {
+        const int zp = a.zin0 + p;
+        for (int i = 0; i < a.nin; i++) {
+          const cx<float> v = src[a.in_slot[i] * a.src_cstride + zp * a.src_zstride + so];
+          float sa, sb;
+          tensor_s(t, a.Tc, a.Tdz, sy, z - zp, a.coef[o][i], a.need[o][i], sa, sb);
+          acc = acc + mk(sa * v.x + sb * v.y, sa * v.y - sb * v.x);
+        }
+      }
+      return acc;
+    });
+  }
   __syncthreads();
   DitRange<float, L, kNT, 1, S - 1>::run(tile, tw);
   dit_stage0_store<float, L, kNT>(tile, tw, [&](int pos, int line, cx<float> v) {

@@ -9,7 +9,8 @@
 // bfloat16 copies Wf [27][Cout][Cin] (forward) and Wb [27][Cin][Cout] (backward).
 // 3x3x3 convolutions (stride 1, zero padding 1) forward and backward-data are
 // implicit GEMMs on the tensor cores (mma m16n8k16, bfloat16 in, float32
-// accumulate); weight gradients are float32 reductions over voxels.
+// accumulate); so are the weight gradients (a GEMM over voxels per tap, the output
+// gradient rounded to bfloat16 as in the data gradient).
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -160,58 +161,90 @@ __global__ void __launch_bounds__(WARPS * 32) k_conv_mma(const void* src, const 
     }
 }
 
-// dW[tap][ci][co] partial over a voxel range: each thread owns up to 16 (ci, co) pairs
-// of one tap; inputs staged in shared memory as float32.
-constexpr int WV = 128;  // voxels per staging step
-__global__ void __launch_bounds__(256) k_conv_dw(const bf16* in, const float* dout, float* part, int N, int D, int H,
-                                                 int W, int Cin, int Cout, int chunks_per_block) {
-  extern __shared__ float sh[];
-  float* sin = sh;               // [WV][Cin]
-  float* sdo = sh + WV * Cin;    // [WV][Cout]
-  const int tap = blockIdx.y;
+// dW[tap][ci][co] partial over a voxel range on the tensor cores: for one tap and one
+// 16-channel tile of ci, dW_tile = sum_v in[v + off][ci] dout[v][co] is a 16 x Cout x
+// (voxels) GEMM. Each step stages 64 voxels (shifted input rows, bfloat16; dout rows
+// rounded to bfloat16) in shared memory; warp w takes voxels 16w..16w+15 as the k
+// dimension of one m16n8k16 per 8 columns of co. The four warps' float32 sums are added
+// in a fixed order into one partial per block.
+constexpr int WVD = 64;  // voxels per staging step
+template <int NT>
+__global__ void __launch_bounds__(128) k_conv_dw_mma(const bf16* in, const float* dout, float* part, int N, int D,
+                                                     int H, int W, int Cin, int Cout, int chunks_per_block) {
+  constexpr int CO = NT * 8;
+  __shared__ __align__(16) bf16 sa[WVD][16 + 8];
+  __shared__ __align__(16) bf16 sb[WVD][CO + 8];
+  __shared__ long long srow[WVD];
+  __shared__ float red[4][16][CO];
+  const int tap = blockIdx.y, mt = blockIdx.z;
   const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
   const long long nvox = (long long)N * D * H * W;
-  const int npair = Cin * Cout;
-  float acc[16];
+  float acc[NT][4];
 #pragma unroll
-  for (int i = 0; i < 16; i++) acc[i] = 0.0f;
-  const long long vstart = (long long)blockIdx.x * chunks_per_block * WV;
-  for (int c = 0; c < chunks_per_block; c++) {
-    const long long vb = vstart + (long long)c * WV;
+  for (int j = 0; j < NT; j++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) acc[j][q] = 0.0f;
+  const long long vstart = (long long)blockIdx.x * chunks_per_block * WVD;
+  for (int cidx = 0; cidx < chunks_per_block; cidx++) {
+    const long long vb = vstart + (long long)cidx * WVD;
     if (vb >= nvox) break;
     __syncthreads();
-    for (int i = threadIdx.x; i < WV * Cin; i += blockDim.x) {
-      const int r = i / Cin, ci = i - r * Cin;
-      const long long v = vb + r;
-      float val = 0.0f;
+    if (threadIdx.x < WVD) {  // source row of each staged voxel (-1: outside the grid)
+      const long long v = vb + threadIdx.x;
+      long long src = -1;
       if (v < nvox) {
         const Vox q = vox_of(v, D, H, W);
         const int z = q.z + dz, y = q.y + dy, x = q.x + dx;
-        if (z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W)
-          val = __bfloat162float(in[((((long long)q.n * D + z) * H + y) * W + x) * Cin + ci]);
+        if (z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W) src = (((long long)q.n * D + z) * H + y) * W + x;
       }
-      sin[i] = val;
-    }
-    for (int i = threadIdx.x; i < WV * Cout; i += blockDim.x) {
-      const long long v = vb + i / Cout;
-      sdo[i] = v < nvox ? dout[vb * Cout + i] : 0.0f;
+      srow[threadIdx.x] = src;
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < WVD * 16; i += 128) {
+      const int r = i >> 4, ci = i & 15;
+      const long long src = srow[r];
+      sa[r][ci] = src >= 0 ? in[src * Cin + mt * 16 + ci] : __float2bfloat16(0.0f);
+    }
+    for (int i = threadIdx.x; i < WVD * CO; i += 128) {
+      const int r = i / CO, co = i - r * CO;
+      const long long v = vb + r;
+      sb[r][co] = __float2bfloat16(v < nvox ? dout[v * Cout + co] : 0.0f);
+    }
+    __syncthreads();
+    const int k0 = warp * 16;
+    uint32_t af[4];
+    af[0] = (uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t][g]) | ((uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t + 1][g]) << 16);
+    af[1] = (uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t][g + 8]) |
+            ((uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t + 1][g + 8]) << 16);
+    af[2] = (uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t + 8][g]) |
+            ((uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t + 9][g]) << 16);
+    af[3] = (uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t + 8][g + 8]) |
+            ((uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t + 9][g + 8]) << 16);
 #pragma unroll
-    for (int u = 0; u < 16; u++) {
-      const int p = threadIdx.x + u * 256;
-      if (p >= npair) break;
-      const int ci = p / Cout, co = p - ci * Cout;
-      float s = 0.0f;
-      for (int r = 0; r < WV; r++) s += sin[r * Cin + ci] * sdo[r * Cout + co];
-      acc[u] += s;
+    for (int j = 0; j < NT; j++) {
+      const int n = j * 8 + g;
+      uint32_t bfr[2];
+      bfr[0] = (uint32_t)__bfloat16_as_ushort(sb[k0 + 2 * t][n]) | ((uint32_t)__bfloat16_as_ushort(sb[k0 + 2 * t + 1][n]) << 16);
+      bfr[1] = (uint32_t)__bfloat16_as_ushort(sb[k0 + 2 * t + 8][n]) |
+               ((uint32_t)__bfloat16_as_ushort(sb[k0 + 2 * t + 9][n]) << 16);
+      mma16816(acc[j], af, bfr);
     }
   }
+  // rows g (c0, c1) and g + 8 (c2, c3) of the tile, columns j*8 + 2t, +1
 #pragma unroll
-  for (int u = 0; u < 16; u++) {
-    const int p = threadIdx.x + u * 256;
-    if (p >= npair) break;
-    part[((long long)blockIdx.x * 27 + tap) * npair + p] = acc[u];
+  for (int j = 0; j < NT; j++) {
+    red[warp][g][j * 8 + 2 * t] = acc[j][0];
+    red[warp][g][j * 8 + 2 * t + 1] = acc[j][1];
+    red[warp][g + 8][j * 8 + 2 * t] = acc[j][2];
+    red[warp][g + 8][j * 8 + 2 * t + 1] = acc[j][3];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 16 * CO; i += 128) {
+    const int r = i / CO, co = i - r * CO;
+    const float v = ((red[0][r][co] + red[1][r][co]) + red[2][r][co]) + red[3][r][co];
+    part[((long long)blockIdx.x * 27 + tap) * Cin * Cout + (long long)(mt * 16 + r) * Cout + co] = v;
   }
 }
 
@@ -439,9 +472,10 @@ int tmn_conv3d_backward_data(const float* dout, const void* Wb, float* din, int 
 
 int tmn_conv3d_backward_weight(const void* in, const float* dout, float* dW, float* db, float* work,
                                long long work_floats, int N, int D, int H, int W, int Cin, int Cout, void* stream) {
-  if (!in || !dout || !dW || !db || !work || Cin * Cout > 16 * 256) return -1;
+  if (!in || !dout || !dW || !db || !work || Cin % 16 || Cin < 16 || (Cout != 16 && Cout != 32 && Cout != 64))
+    return -1;
   const long long nvox = (long long)N * D * H * W;
-  const long long chunks = (nvox + WV - 1) / WV;
+  const long long chunks = (nvox + WVD - 1) / WVD;
   const long long per_blk = 27LL * Cin * Cout;
   int nblk = (int)(work_floats / per_blk);
   if (nblk > 64) nblk = 64;
@@ -449,13 +483,11 @@ int tmn_conv3d_backward_weight(const void* in, const float* dout, float* dW, flo
   const int cpb = (int)((chunks + nblk - 1) / nblk);
   nblk = (int)((chunks + cpb - 1) / cpb);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const size_t sm = (size_t)WV * (Cin + Cout) * sizeof(float);
-  static bool init = false;
-  if (!init) {
-    cudaFuncSetAttribute(k_conv_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    init = true;
-  }
-  k_conv_dw<<<dim3(nblk, 27), 256, sm, s>>>(reinterpret_cast<const bf16*>(in), dout, work, N, D, H, W, Cin, Cout, cpb);
+  const dim3 grid(nblk, 27, Cin / 16);
+  const bf16* x = reinterpret_cast<const bf16*>(in);
+  if (Cout == 16) k_conv_dw_mma<2><<<grid, 128, 0, s>>>(x, dout, work, N, D, H, W, Cin, Cout, cpb);
+  if (Cout == 32) k_conv_dw_mma<4><<<grid, 128, 0, s>>>(x, dout, work, N, D, H, W, Cin, Cout, cpb);
+  if (Cout == 64) k_conv_dw_mma<8><<<grid, 128, 0, s>>>(x, dout, work, N, D, H, W, Cin, Cout, cpb);
   k_dw_reduce<<<grid_of(per_blk), 256, 0, s>>>(work, nblk, per_blk, dW);
   k_db<<<Cout, 256, 0, s>>>(dout, nvox, Cout, db);
   return ok();

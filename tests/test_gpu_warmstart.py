@@ -9,7 +9,7 @@ output rounding remain:
   here by 1e-5 sum|terms| for the K <= 27 * 96 * 2 of these sizes.
 The whole network is compared on an 8^3 grid (batch 2) against the oracle with
 the same storage roundings (bfloat16 activations after each conv and pool, a
-bfloat16 gradient entering each data-gradient product), so only float32
+bfloat16 gradient entering each data- and weight-gradient product), so only float32
 summation order differs; and, loosely, against the all-float64 oracle (a
 weight gradient sums ~1e3 voxel terms of either sign, so bfloat16 storage
 errors, relative to sum|terms|, reach sqrt(1e3) * 2^-9 ~ 6e-2 of the sum).
@@ -107,8 +107,9 @@ def test_conv_backward_data_and_weight(L, cin, cout):
     assert np.all(np.abs(din.cpu().numpy() - dx_ref) <= 1e-5 * bound + 1e-30)
     assert L.tmn_conv3d_backward_data(p(gd), p(Wb), p(din), *DIMS, cin, cout, 1, S()) == 0  # accumulate
     assert np.all(np.abs(din.cpu().numpy() - 2 * dx_ref) <= 2e-5 * bound + 1e-30)
-    # weight gradient: float32 reductions of bfloat16 inputs times float32 gradients
-    g32 = rng.normal(size=DIMS + (cout,)).astype(np.float32).astype(np.float64)
+    # weight gradient: float32 sums of bfloat16 products (dout rounded to bfloat16, as the
+    # kernel does; the bias gradient sums the float32 values)
+    g32 = bf16_round(rng.normal(size=DIMS + (cout,)))
     _, dW_ref, db_ref = U.conv_backward(x, W, g32)
     _, dWb, dbb = U.conv_backward(np.abs(x), W, np.abs(g32))
     dW = torch.empty(27, cin, cout, device=DEV)
