@@ -142,7 +142,8 @@ __global__ void k_projgr(const double* x, const double* g, long long n, double l
 __global__ void k_bp(const double* __restrict__ x, const double* __restrict__ g, long long n, double lo, double hi,
                      const double* __restrict__ S, const double* __restrict__ Y, Cols c, double theta,
                      double* __restrict__ d, double* __restrict__ t, int8_t* __restrict__ st, double* part,
-                     int* cnt) {
+                     int* cnt, VI* tmin) {
+  VI tm{INFINITY, -1};
   double v[2 * MAXM + 1];
 #pragma unroll
   for (int k = 0; k < 2 * MAXM + 1; k++) v[k] = 0.0;
@@ -166,6 +167,7 @@ __global__ void k_bp(const double* __restrict__ x, const double* __restrict__ g,
     if (s == 0) {
       di = ng;
       ti = ng < 0.0 ? tl / (-ng) : tu / ng;
+      tm = vimin(tm, VI{ti, i});
       count++;
 #pragma unroll
       for (int a = 0; a < 2 * MAXM; a++)
@@ -179,6 +181,7 @@ __global__ void k_bp(const double* __restrict__ x, const double* __restrict__ g,
   // d.d goes to slot col2 of the partial
   v[col2] = v[2 * MAXM];
   block_sums<2 * MAXM + 1>(v, col2 + 1, part);
+  block_min(tm, tmin);
   for (int o = 16; o; o >>= 1) count += __shfl_down_sync(0xffffffffu, count, o);
   __shared__ int shc[WPB];
   if ((threadIdx.x & 31) == 0) shc[threadIdx.x >> 5] = count;
@@ -424,6 +427,19 @@ __global__ void k_gcp_search(const unsigned long long* key, const int* val, int 
       return;
     }
   }
+}
+
+// the winning warp's candidate {j, dtm, t_j, P_j, c_j} into out (one thread)
+__global__ void k_pick_cand(const int* jstar, int chunk, const double* cand, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int js = *jstar;
+  constexpr int cl = 3 + 2 * 2 * MAXM;
+  if (js < 1 || js == 0x7fffffff) {
+    out[0] = -1.0;
+    return;
+  }
+  const double* c = cand + (long long)((js - 1) / chunk) * cl;
+  for (int i = 0; i < cl; i++) out[i] = c[i];
 }
 
 // xcp = x + tsum d; free = moving or zero-gradient; then the first jst sorted
@@ -879,6 +895,17 @@ int fetch_sums(tm_lbfgsb* o, int nblk, int nv, cudaStream_t s) {
   LCK(cudaStreamSynchronize(s));
   return TM_OK;
 }
+// sums (nblk_s partials of nv) to hbuf[0..nv) and the min of nblk_m partials to *out, one sync
+int fetch_both(tm_lbfgsb* o, int nblk_s, int nv, int nblk_m, VI* out, cudaStream_t s) {
+  k_finish<<<1, 256, 0, s>>>(o->part, nblk_s, nv, o->red);
+  LCKL();
+  k_finish_min<<<1, 32, 0, s>>>(o->mpart, nblk_m, o->mred);
+  LCKL();
+  LCK(cudaMemcpyAsync(o->hbuf, o->red, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+  LCK(cudaMemcpyAsync(out, o->mred, sizeof(VI), cudaMemcpyDeviceToHost, s));
+  LCK(cudaStreamSynchronize(s));
+  return TM_OK;
+}
 int fetch_min(tm_lbfgsb* o, int nblk, VI* out, cudaStream_t s) {
   k_finish_min<<<1, 32, 0, s>>>(o->mpart, nblk, o->mred);
   LCKL();
@@ -912,16 +939,18 @@ int direction(tm_lbfgsb* o, cudaStream_t s) {
   const double theta = o->theta;
   const int ntile = (int)((n + TILE - 1) / TILE);
   // breakpoints, p0 = W^T d, d.d
-  k_bp<<<ntile, NT, 0, s>>>(o->x, o->g, n, o->lo, o->hi, o->S, o->Y, c, theta, o->d, o->t, o->st, o->part, o->cnt);
+  k_bp<<<ntile, NT, 0, s>>>(o->x, o->g, n, o->lo, o->hi, o->S, o->Y, c, theta, o->d, o->t, o->st, o->part, o->cnt,
+                            o->mpart);
   LCKL();
-  if (int e = fetch_sums(o, ntile, col2 + 1, s)) return e;
-  std::vector<double> p0(o->hbuf, o->hbuf + col2);
-  const double D2 = o->hbuf[col2];
   k_scan_ex<<<1, 1024, 0, s>>>(o->cnt, ntile);
   LCKL();
-  int K = 0;
-  LCK(cudaMemcpyAsync(&K, o->cnt + ntile, sizeof(int), cudaMemcpyDeviceToHost, s));
-  LCK(cudaStreamSynchronize(s));
+  int* Kh = reinterpret_cast<int*>(o->hbuf + 1000);  // pinned slot for the count
+  LCK(cudaMemcpyAsync(Kh, o->cnt + ntile, sizeof(int), cudaMemcpyDeviceToHost, s));
+  VI tmin;
+  if (int e = fetch_both(o, ntile, col2 + 1, ntile, &tmin, s)) return e;
+  std::vector<double> p0(o->hbuf, o->hbuf + col2);
+  const double D2 = o->hbuf[col2];
+  const int K = *Kh;
   o->nbreak = K;
   std::vector<double> Minv, M;
   if (o->col > 0) {
@@ -942,8 +971,10 @@ int direction(tm_lbfgsb* o, cudaStream_t s) {
       for (int b = 0; b < col2; b++) pmp += p0[a] * M[a * col2 + b] * p0[b];
     const double f1 = -D2, f2org = theta * D2, f2 = f2org - pmp;
     const double dtm0 = -f1 / f2;
-    double t1 = INFINITY;
-    if (K > 0) {
+    // the smallest breakpoint decides whether the minimiser lies before it; only then
+    // is the sort (and the breakpoint scan) needed
+    const double t1 = K > 0 ? tmin.v : INFINITY;
+    if (K > 0 && !(dtm0 < t1)) {
       k_bp_compact<<<ntile, NT, 0, s>>>(o->t, o->st, n, o->cnt, o->key, o->val);
       LCKL();
       // sort by t (stable, so equal t keep index order)
@@ -960,10 +991,6 @@ int direction(tm_lbfgsb* o, cudaStream_t s) {
         std::swap(k1, k2);
         std::swap(v1, v2);
       }
-      unsigned long long kb = 0;
-      LCK(cudaMemcpyAsync(&kb, o->key, sizeof(kb), cudaMemcpyDeviceToHost, s));
-      LCK(cudaStreamSynchronize(s));
-      std::memcpy(&t1, &kb, sizeof(double));
     }
     if (K == 0 || dtm0 < t1) {
       jst = 0;
@@ -990,14 +1017,13 @@ int direction(tm_lbfgsb* o, cudaStream_t s) {
       k_gcp_search<<<blocks, NT, 0, s>>>(o->key, o->val, chunk, o->d, o->S, o->Y, n, c, q, o->part, o->small,
                                         o->small + col2, o->jstar, o->cand);
       LCKL();
-      int js = 0;
-      LCK(cudaMemcpyAsync(&js, o->jstar, sizeof(int), cudaMemcpyDeviceToHost, s));
-      LCK(cudaStreamSynchronize(s));
-      if (js < 1 || js > K) return fail(o, TM_ERR_STATE, "Cauchy point search found no segment");
-      const int w = (js - 1) / chunk;
       const int cl = 3 + 2 * 2 * MAXM;
-      LCK(cudaMemcpyAsync(o->hbuf, o->cand + (long long)w * cl, cl * sizeof(double), cudaMemcpyDeviceToHost, s));
+      k_pick_cand<<<1, 32, 0, s>>>(o->jstar, chunk, o->cand, o->red);
+      LCKL();
+      LCK(cudaMemcpyAsync(o->hbuf, o->red, cl * sizeof(double), cudaMemcpyDeviceToHost, s));
       LCK(cudaStreamSynchronize(s));
+      const int js = (int)o->hbuf[0];
+      if (js < 1 || js > K) return fail(o, TM_ERR_STATE, "Cauchy point search found no segment");
       jst = js;
       const double dtm = std::max(o->hbuf[1], 0.0);
       tsum = o->hbuf[2] + dtm;
@@ -1070,11 +1096,10 @@ int begin_search(tm_lbfgsb* o, float* e32, double* e64, cudaStream_t s, bool& as
   const int gb = grid_for(n, o->nsm);
   k_dir<<<gb, NT, 0, s>>>(o->x, o->g, o->xbar, n, o->lo, o->hi, o->d, o->part, o->mpart);
   LCKL();
-  if (int e = fetch_sums(o, gb, 2, s)) return e;
+  VI m;
+  if (int e = fetch_both(o, gb, 2, gb, &m, s)) return e;
   o->gd = o->hbuf[0];
   o->dtd = o->hbuf[1];
-  VI m;
-  if (int e = fetch_min(o, gb, &m, s)) return e;
   o->stpmx = o->iter == 0 ? 1.0 : std::min(BIG, m.v);
   ascent = !(o->gd < 0.0);
   if (ascent) return TM_OK;
@@ -1166,7 +1191,7 @@ int tm_lbfgsb_create(tm_lbfgsb** out, int device, long long n, int m, double low
   A((void**)&o->red, 1024 * sizeof(double));
   A((void**)&o->small, (2 * MAXM + 4 * MAXM * MAXM) * sizeof(double));
   A((void**)&o->cand, nwmax * (3 + 4 * MAXM) * sizeof(double));
-  A((void**)&o->mpart, 8 * o->nsm * sizeof(VI));
+  A((void**)&o->mpart, std::max(8LL * o->nsm, ntile) * sizeof(VI));  // also one per k_bp tile
   A((void**)&o->mred, sizeof(VI));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&o->hbuf, 1024 * sizeof(double));
   if (e != cudaSuccess) {
@@ -1282,14 +1307,13 @@ int tm_lbfgsb_iterate(tm_lbfgsb* o, double f, const float* g32, const double* g6
   k_accept<<<gb, NT, 0, s>>>(o->x, o->g, o->xt, o->gt, o->d, n, o->stp, store ? 1 : 0, o->S + (long long)slot * n,
                              o->Y + (long long)slot * n, o->S, o->Y, c, o->part);
   LCKL();
-  if (int e = fetch_sums(o, gb, 1 + 2 * c.col, s)) return e;
+  k_projgr<<<gb, NT, 0, s>>>(o->x, o->g, n, o->lo, o->hi, o->mpart);  // after the accepted x, g
+  LCKL();
+  VI m;
+  if (int e = fetch_both(o, gb, 1 + 2 * c.col, gb, &m, s)) return e;
   std::vector<double> h(o->hbuf, o->hbuf + 1 + 2 * c.col);
   o->fold = o->f;
   o->f = f;
-  k_projgr<<<gb, NT, 0, s>>>(o->x, o->g, n, o->lo, o->hi, o->mpart);
-  LCKL();
-  VI m;
-  if (int e = fetch_min(o, gb, &m, s)) return e;
   o->sbgnrm = -m.v;
   if (store) {
     if (o->col == o->m) {  // shift the retained pairs' products up-left
