@@ -116,6 +116,94 @@ __global__ void __launch_bounds__(256) k_zdir_simple(ZDirArgs a, int c) {
   }
 }
 
+
+// Three inputs, three outputs with coefficients v_o = e_o, u_i = e_i (a spatially
+// varying M0: the magnetization enters and the field leaves component by component):
+// s_oi is the tensor component (o, i) itself, so per streamed column value the six
+// components are loaded once and out_o = sum_i N_oi in_i, with N_xz = -i b4 and
+// N_yz = -i b5 (odd in z; xy and yz odd in y). Same 4-way z split as k_zdir_simple.
+__device__ __forceinline__ void apply_n(const cx<float> in[3], const float t[6], cx<float> out[3]) {
+  // (-i b) v = (b v.y, -b v.x)
+  out[0] = mk(t[0] * in[0].x + t[3] * in[1].x + t[4] * in[2].y, t[0] * in[0].y + t[3] * in[1].y - t[4] * in[2].x);
+  out[1] = mk(t[3] * in[0].x + t[1] * in[1].x + t[5] * in[2].y, t[3] * in[0].y + t[1] * in[1].y - t[5] * in[2].x);
+  out[2] = mk(t[4] * in[0].y + t[5] * in[1].y + t[2] * in[2].x, -t[4] * in[0].x - t[5] * in[1].x + t[2] * in[2].y);
+}
+
+__global__ void __launch_bounds__(256) k_zdir_id(ZDirArgs a) {
+  constexpr int ZS = 4;
+  const int kx = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int part = (threadIdx.x >> 5) & (ZS - 1);
+  const int zc = blockIdx.y * 2 + (threadIdx.x >> 7);
+  __shared__ cx<float> red[2][ZS][3][32];
+  const bool valid = kx < a.P && zc < a.Ly;
+  const int2 col = valid ? a.zcol[zc] : make_int2(0, 0);
+  const bool lo = col.y <= a.Ly / 2;
+  const int kyf = lo ? col.y : a.Ly - col.y;
+  const float sy = lo ? 1.0f : -1.0f;
+  const float* t0 = a.Tz + kyf * (long long)a.P + kx;
+  const long long colo = (long long)col.x * a.P + kx;
+  const cx<float>* buf = reinterpret_cast<const cx<float>*>(a.buf);
+  cx<float>* obuf = reinterpret_cast<cx<float>*>(a.buf);
+  auto tensor = [&](int dz, float t[6]) {
+    const int adz = dz < 0 ? -dz : dz;
+    const float sz = dz < 0 ? -1.0f : 1.0f;
+    const float* p = t0 + adz * a.Tdz;
+#pragma unroll
+    for (int c = 0; c < 6; c++) t[c] = p[c * a.Tc];
+    t[3] *= sy;
+    t[4] *= sz;
+    t[5] *= sy * sz;
+  };
+  if (a.nzout == 1) {  // stream the inputs onto one output plane; quarters summed in order
+    const int zo = a.zout0;
+    const int per = (a.nzin + ZS - 1) / ZS;
+    const int z0 = a.zin0 + part * per, z1 = min(z0 + per, a.zin0 + a.nzin);
+    cx<float> acc[3] = {zero<float>(), zero<float>(), zero<float>()};
+    if (valid) {
+#pragma unroll 4
+      for (int z = z0; z < z1; z++) {
+        cx<float> in[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) in[i] = buf[a.in_slot[i] * a.cstride + z * a.zstride + colo];
+        float t[6];
+        tensor(zo - z, t);
+        cx<float> o[3];
+        apply_n(in, t, o);
+#pragma unroll
+        for (int k = 0; k < 3; k++) acc[k] = acc[k] + o[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) red[threadIdx.x >> 7][part][k][threadIdx.x & 31] = acc[k];
+    __syncthreads();
+    if (part == 0 && valid) {
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        cx<float> sum = red[threadIdx.x >> 7][0][k][threadIdx.x & 31];
+        for (int q = 1; q < ZS; q++) sum = sum + red[threadIdx.x >> 7][q][k][threadIdx.x & 31];
+        obuf[a.out_slot[k] * a.cstride + zo * a.zstride + colo] = sum;
+      }
+    }
+  } else {  // one input plane onto every output plane; quarters of the planes
+    if (!valid) return;
+    const int zi = a.zin0;
+    cx<float> in[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) in[i] = buf[a.in_slot[i] * a.cstride + zi * a.zstride + colo];
+    const int per = (a.nzout + ZS - 1) / ZS;
+    const int z0 = a.zout0 + part * per, z1 = min(z0 + per, a.zout0 + a.nzout);
+#pragma unroll 4
+    for (int z = z0; z < z1; z++) {
+      float t[6];
+      tensor(z - zi, t);
+      cx<float> o[3];
+      apply_n(in, t, o);
+#pragma unroll
+      for (int k = 0; k < 3; k++) obuf[a.out_slot[k] * a.cstride + z * a.zstride + colo] = o[k];
+    }
+  }
+}
+
 template <int NP>
 __global__ void __launch_bounds__(256) k_zdir(ZDirArgs a) {
   const int kx = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -205,6 +293,18 @@ int launch_zdir(const ZDirArgs& a, cudaStream_t s) {
   if (small < 0 || small > kDirectPlanesMax) return -2;
   if (small == 0) return 0;
   dim3 grid((a.P + 31) / 32, (a.Ly + 7) / 8);
+  if (a.nin == 3 && a.nout == 3 && small == 1) {  // coefficients e_o^T N e_i: each the component (o, i)
+    bool id = true;
+    for (int o = 0; o < 3; o++)
+      for (int i = 0; i < 3; i++) {
+        const int c = o == i ? o : (o + i == 1 ? 3 : (o + i == 2 ? 4 : 5));
+        id = id && a.need[o][i] == (1 << c) && a.coef[o][i][c] == 1.0f;
+      }
+    if (id) {
+      k_zdir_id<<<dim3((a.P + 31) / 32, (a.Ly + 1) / 2), 256, 0, s>>>(a);
+      return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+    }
+  }
   if (a.nin == 1 && a.nout == 1 && small == 1) {
     const int need = a.need[0][0];
     if (need != 0 && (need & (need - 1)) == 0) {
