@@ -38,12 +38,14 @@ UNIT = "evals/s"
 # separate path: profiles/zdir_c4_256cube_ncu.md, forward and adjoint launch averaged);
 # valid only while the kernel's source file is unchanged.
 MEASURED_TRAFFIC = {
-    "yz_forward": {"bytes": 218.7e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
-                   "source_sha1": "72ccd07cf8a97e3f86d82e02d941f6bbccb08ec6"},
-    "zy_adjoint": {"bytes": 160.8e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
-                   "source_sha1": "72ccd07cf8a97e3f86d82e02d941f6bbccb08ec6"},
-    "x_inverse": {"bytes": 254.5e6, "source": "paper_1707_09898_gb300/csrc/k_x.cu",
-                  "source_sha1": "0286acf2119db756a84d9c4567749aa70feb8d32"},
+    "x_forward": {"bytes": 163.2e6, "source": "paper_1707_09898_gb300/csrc/k_xfwd.cu",
+                  "source_sha1": "fc77e31fd202a150829d691547493cbc4c10fa21"},
+    "yz_forward": {"bytes": 224.6e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
+                   "source_sha1": "1e20cd21523fcecd89829489074bc9f18a341e2d"},
+    "zy_adjoint": {"bytes": 163.3e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
+                   "source_sha1": "1e20cd21523fcecd89829489074bc9f18a341e2d"},
+    "x_inverse": {"bytes": 254.5e6, "source": "paper_1707_09898_gb300/csrc/k_xinv.cu",
+                  "source_sha1": "cd8d1b264cefcf85f6e2b7cf4c0376b661a56014"},
     "z_pass": {"bytes": 330.5e6, "source": "paper_1707_09898_gb300/csrc/k_zdir.cu",
                "source_sha1": "1e01034aaa7e24a5aeb9221956bd20b7f6d468eb"},
 }

@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
-PRODUCT_UNITS = ["api.cu", "k_x.cu", "k_yz.cu", "k_zdir.cu", "tensor.cu", "misc.cu", "unet.cu", "lbfgsb.cu", "k_yzfused.cu", "k_xobj.cu"]
+PRODUCT_UNITS = ["api.cu", "k_xfwd.cu", "k_xinv.cu", "k_yz.cu", "k_zdir.cu", "tensor.cu", "misc.cu", "unet.cu", "lbfgsb.cu", "k_yzfused.cu", "k_xobj.cu"]
 CUFFT_UNITS = ["cufft_pipeline.cu"]
 
 LIB = os.path.join(HERE, "libtopomag.so")

@@ -55,6 +55,8 @@ struct tm_ctx {
   bool fuse_yz = true;             // prepared path: y transform fused with the direct z sum
   float2* yzpart = nullptr;        // [z chunks][Ly][P] partial planes of the fused forward
   int yzpart_chunks = 0;
+  float2* yzseg = nullptr;         // [2 * SMs][Ly][TB] segment partials of the flattened fused forward
+  unsigned* yzcnt = nullptr;       // [P / TB] item counters of the flattened fused forward
   int nsm = 0;
   int* ext = nullptr;       // [2]: z range of the target planes
   double* Jhost = nullptr;  // pinned
@@ -121,6 +123,10 @@ void free_grid(tm_ctx* c) {
   cudaFree(c->yzpart);
   c->yzpart = nullptr;
   c->yzpart_chunks = 0;
+  cudaFree(c->yzseg);
+  c->yzseg = nullptr;
+  cudaFree(c->yzcnt);
+  c->yzcnt = nullptr;
   cudaFree(c->sH);
   cudaFree(c->sgH);
   c->sH = c->sgH = nullptr;
@@ -364,8 +370,9 @@ int zdirect(tm_ctx* ctx, const ConvSpec& cs, int zi0, int nzi, int zo0, int nzo,
 }
 
 // forward y transform of the design planes fused with the direct z sum onto the
-// single target plane (cs.nout == 1)
-int yz_forward(tm_ctx* ctx, const ConvSpec& cs, int zo, cudaStream_t s) {
+// single target plane (cs.nout == 1); *yinv_done: the kernel also wrote the target
+// plane's inverse y transform into A
+int yz_forward(tm_ctx* ctx, const ConvSpec& cs, int zo, cudaStream_t s, bool* yinv_done) {
   const int Ly = ctx->L[1];
   const long long P = ctx->P;
   const int chunks = (int)(P / TB);
@@ -406,8 +413,18 @@ int yz_forward(tm_ctx* ctx, const ConvSpec& cs, int zo, cudaStream_t s) {
   y.zchunk = zchunk;
   y.zout = zo;
   y.tw = ctx->tw + ctx->L[0];
+  if (!ctx->yzseg) {
+    CK(cudaMalloc(&ctx->yzseg, (size_t)2 * ctx->nsm * Ly * TB * sizeof(float2)));
+    CK(cudaMalloc(&ctx->yzcnt, (size_t)chunks * sizeof(unsigned)));
+    CK(cudaMemsetAsync(ctx->yzcnt, 0, (size_t)chunks * sizeof(unsigned), s));
+  }
+  y.seg = ctx->yzseg;
+  y.cnt = ctx->yzcnt;
+  y.yrows = ctx->A + cs.aout[0] * ((long long)ctx->nz * ctx->ny * P) + (long long)zo * ctx->ny * P;
   Timed t(ctx, KIND_YZF, s);
-  CKL(launch_yz_fwd(Ly, y, s));
+  const int r = launch_yz_fwd(Ly, y, s);
+  if (r < 0) CKL(r);
+  *yinv_done = r == 1;
   return TM_OK;
 }
 
@@ -920,7 +937,9 @@ int forward_planes(tm_ctx* ctx, const float* rho, const int* F, int nF, cudaStre
     cs.v[o] = kUnit[F[o]];
   }
   if (ctx->fuse_yz && np == 1 && nF == 1) {
-    if ((r = yz_forward(ctx, cs, ctx->tz0, s))) return r;
+    bool done = false;
+    if ((r = yz_forward(ctx, cs, ctx->tz0, s, &done))) return r;
+    if (done) return TM_OK;
   } else {
     if ((r = ypass(ctx, false, cs.nin, cs.ain, cs.bin, 0, ctx->nzd, s))) return r;
     if ((r = zdirect(ctx, cs, 0, ctx->nzd, ctx->tz0, np, s))) return r;

@@ -231,6 +231,15 @@ __device__ __forceinline__ void apply_twiddles(cx<T>* v, int j, const cx<T>* tw)
   }
 }
 
+// Tile index of position base + q M of a stage unit. For a radix-16 unit with M = 1 in
+// the swizzled layout the positions are g 16 + q, whose swizzle is q ^ (g mod 16): one
+// XOR per element instead of the general shift-and-mask.
+template <int R, int M, bool SW>
+__device__ __forceinline__ int unit_idx(int g, int base, int q, int line) {
+  if constexpr (SW && R == TB && M == 1) return g * (TB * TB) + q * TB + ((line ^ (g & 15)) ^ q);
+  else return tidx<SW>(base + q * M, line);
+}
+
 // One forward DIF stage in place on the tile.
 template <typename T, int L, int s, int NT, bool SW = false>
 __device__ __forceinline__ void dif_stage(cx<T>* tile, const cx<T>* tw) {
@@ -244,11 +253,11 @@ __device__ __forceinline__ void dif_stage(cx<T>* tile, const cx<T>* tw) {
       const int base = g * S::G + j;
       cx<T> v[S::R];
 #pragma unroll
-      for (int q = 0; q < S::R; q++) v[q] = tile[tidx<SW>(base + q * S::M, line)];
+      for (int q = 0; q < S::R; q++) v[q] = tile[unit_idx<S::R, S::M, SW>(g, base, q, line)];
       Dft<T, S::R, false>::run(v);
       apply_twiddles<T, L, s, false>(v, j, tw);
 #pragma unroll
-      for (int q = 0; q < S::R; q++) tile[tidx<SW>(base + q * S::M, line)] = v[q];
+      for (int q = 0; q < S::R; q++) tile[unit_idx<S::R, S::M, SW>(g, base, q, line)] = v[q];
     }
   }
 }
@@ -266,11 +275,11 @@ __device__ __forceinline__ void dit_stage(cx<T>* tile, const cx<T>* tw) {
       const int base = g * S::G + j;
       cx<T> v[S::R];
 #pragma unroll
-      for (int q = 0; q < S::R; q++) v[q] = tile[tidx<SW>(base + q * S::M, line)];
+      for (int q = 0; q < S::R; q++) v[q] = tile[unit_idx<S::R, S::M, SW>(g, base, q, line)];
       apply_twiddles<T, L, s, true>(v, j, tw);
       Dft<T, S::R, true>::run(v);
 #pragma unroll
-      for (int q = 0; q < S::R; q++) tile[tidx<SW>(base + q * S::M, line)] = v[q];
+      for (int q = 0; q < S::R; q++) tile[unit_idx<S::R, S::M, SW>(g, base, q, line)] = v[q];
     }
   }
 }

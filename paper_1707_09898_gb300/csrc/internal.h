@@ -155,6 +155,13 @@ struct YZArgs {
   long long Tc, Tdz;
   int zin0, nzin, zchunk, zout;
   const float2* tw;
+  // single-component path on two-stage plans (when set): per-block segment partials
+  // [2 * blocks][Ly][TB], per-column-block item counters (zero between launches), and the
+  // target plane's rows in A [ny][P]; launch_yz_fwd then also writes the inverse y
+  // transform of the target plane there and returns 1
+  float2* seg;
+  unsigned* cnt;
+  float2* yrows;
 };
 int launch_zy_adj(int L, const ZYArgs& a, cudaStream_t s);
 int launch_yz_fwd(int L, const YZArgs& a, cudaStream_t s);

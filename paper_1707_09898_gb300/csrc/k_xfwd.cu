@@ -1,0 +1,153 @@
+// Forward x pass of the stray-field convolution (Sec. "Discretization", Eq. (convolution)).
+//
+// Real rows (rho^p, rho^p M0_c of Sec. "Methodology" Eq. 2, or a given vector
+// component) are zero padded from nx to L (the first DIF stage reads only x < nx) and
+// transformed two rows at a time (row a + i row b), then separated into the half
+// spectra kx = 0..L/2. The first stage maps consecutive threads to consecutive x of
+// one row pair, so global rows are read in 64-byte runs straight into registers; the
+// half-spectrum rows are written with consecutive threads on consecutive kx.
+#include "xpass.cuh"
+
+namespace tmk {
+
+namespace {
+
+// Persistent: a block loops over 32-row tiles; the raw inputs of the next tile are
+// loaded into registers while the current tile is separated and stored, so global
+// latency overlaps the shared-memory work. P3: p = 3 fixed at compile time.
+template <int L, int SRC, bool P3>
+__global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
+  constexpr int S = plan_stages(L);
+  using S0 = StageShape<L, 0>;
+  constexpr bool withM0 = SRC == SRC_RHO_M0;
+  constexpr int RM = withM0 ? 1 : 0;
+  constexpr int R = S0::R, M = S0::M, NU = M * TB, ITER = (NU + kNT - 1) / kNT;
+  // nx <= L/2, so the stage-0 inputs x = j + q M with q >= R/2 are always padding
+  constexpr int RH = R / 2 > 0 ? R / 2 : 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
+  cx<float>* tw0 = tw + L;
+  cx<float>* tile = tw0 + L;
+  load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
+  load_twiddles0<L>(tw0, reinterpret_cast<const cx<float>*>(a.tw));
+  const int c = a.comp[blockIdx.y];
+  cx<float>* out = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[blockIdx.y] * a.out_cstride;
+  const int ntiles = (a.rows + ROWS - 1) / ROWS;
+  const float* src = SRC == SRC_VECTOR ? a.vec + c * a.vec_cstride : a.rho;
+  const float* m0 = withM0 ? a.M0v + c * a.M0v_cstride : nullptr;
+  float ra[ITER][RH], rb[ITER][RH], ma[ITER][RM ? RH : 1], mb[ITER][RM ? RH : 1];
+  auto fetch = [&](int t) {
+    const int row0 = t * ROWS;
+#pragma unroll
+    for (int it = 0; it < ITER; it++) {
+      const int u = it * kNT + threadIdx.x;
+      const int j = u % M, line = u / M;
+      const int r = row0 + 2 * line;
+      const bool ok = NU % kNT == 0 || u < NU;
+      const bool va = ok && r < a.rows, vb = ok && r + 1 < a.rows;
+      const long long o = (long long)r * a.nx + j;  // x = j of row a; row b follows
+      const int xn = a.nx - j;                       // x < nx  <=>  q M < xn
+#pragma unroll
+      for (int q = 0; q < RH; q++) {
+        const bool in_x = q * M < xn;
+        ra[it][q] = (in_x && va) ? src[o + q * M] : 0.0f;
+        rb[it][q] = (in_x && vb) ? src[o + a.nx + q * M] : 0.0f;
+        if constexpr (withM0) {
+          ma[it][q] = (in_x && va) ? m0[o + q * M] : 0.0f;
+          mb[it][q] = (in_x && vb) ? m0[o + a.nx + q * M] : 0.0f;
+        }
+      }
+    }
+  };
+  int t = blockIdx.x;
+  if (t < ntiles) fetch(t);
+  __syncthreads();
+  for (; t < ntiles; t += gridDim.x) {
+    const int row0 = t * ROWS;
+#pragma unroll
+    for (int it = 0; it < ITER; it++) {
+      const int u = it * kNT + threadIdx.x;
+      if (NU % kNT == 0 || u < NU) {
+        const int j = u % M, line = u / M;
+        cx<float> v[R];
+#pragma unroll
+        for (int q = RH; q < R; q++) v[q] = zero<float>();
+#pragma unroll
+        for (int q = 0; q < RH; q++) {
+          float va = ra[it][q], vb = rb[it][q];
+          if constexpr (SRC != SRC_VECTOR) {
+            va = ipow_t<P3>(va, a.p);
+            vb = ipow_t<P3>(vb, a.p);
+            if constexpr (withM0) {
+              va *= ma[it][q];
+              vb *= mb[it][q];
+            }
+          }
+          v[q] = mk(va, vb);
+        }
+        Dft<float, R, false>::run(v);
+        twiddle0<L, false>(v, j, tw0);
+#pragma unroll
+        for (int q = 0; q < R; q++) tile[tix0<M>(j, q, line)] = v[q];
+      }
+    }
+    __syncthreads();
+    DifRange<float, L, kNT, 1, S, true>::run(tile, tw);
+    if (t + (int)gridDim.x < ntiles) fetch(t + gridDim.x);
+    xseparate<L>(tile, out, row0, a.rows, a.P);
+    __syncthreads();
+  }
+}
+
+template <int L, int SRC, bool P3>
+int run_xfwd_src(const XFwdArgs& a, int ncomp, cudaStream_t s) {
+  const size_t sm = xsmem<L>();
+  static bool init = false;
+  if (!init) {
+    if (cudaFuncSetAttribute(k_xfwd<L, SRC, P3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        cudaSuccess)
+      return -1;
+    init = true;
+  }
+  const int tiles = (a.rows + ROWS - 1) / ROWS;
+  if (tiles == 0 || ncomp == 0) return 0;
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+  }
+  const int per_comp = (2 * nsm + ncomp - 1) / ncomp;  // two resident blocks per SM in total
+  const int blocks = tiles < per_comp ? tiles : per_comp;
+  k_xfwd<L, SRC, P3><<<dim3(blocks, ncomp), kNT, sm, s>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+template <int L, int SRC>
+int run_xfwd_pow(const XFwdArgs& a, int ncomp, cudaStream_t s) {
+  if constexpr (k_per_thread<L>()) {
+    if (a.p == 3.0f) return run_xfwd_src<L, SRC, true>(a, ncomp, s);
+  }
+  return run_xfwd_src<L, SRC, false>(a, ncomp, s);
+}
+template <int L>
+int run_xfwd(const XFwdArgs& a, int ncomp, cudaStream_t s) {
+  if (a.src == SRC_RHO_POW) return run_xfwd_pow<L, SRC_RHO_POW>(a, ncomp, s);
+  if (a.src == SRC_RHO_M0) return run_xfwd_pow<L, SRC_RHO_M0>(a, ncomp, s);
+  return run_xfwd_src<L, SRC_VECTOR, false>(a, ncomp, s);
+}
+
+}  // namespace
+
+int launch_xfwd(int L, const XFwdArgs& a, int ncomp, cudaStream_t s) {
+  switch (L) {
+#define TM_CASE(LL) \
+  case LL:          \
+    return run_xfwd<LL>(a, ncomp, s);
+    TM_FOR_EACH_L(TM_CASE)
+#undef TM_CASE
+  }
+  return -2;
+}
+
+}  // namespace tmk

@@ -1,0 +1,302 @@
+// Inverse x pass of the stray-field convolution (Sec. "Discretization", Eq. (convolution)).
+//
+// Half spectra are extended by Hermitian symmetry, two rows are recovered from one
+// complex inverse transform, cropped to nx, and handed to a sink: write H; the
+// least-squares objective and dJ/dH, whose zero-padded forward x transform (the
+// adjoint source) starts in the same registers; or the chain rule
+// dJ/drho = p rho^(p-1) M0 . (D g) (Sec. "Methodology", Eqs. (adjoint1)-(adjoint2)).
+// The last inverse stage maps consecutive threads to consecutive x of one row pair,
+// so global rows are written in 64-byte runs straight from registers.
+#include "xpass.cuh"
+
+namespace tmk {
+
+namespace {
+
+// Called by every thread of every block after thread 0 wrote the block's J partial:
+// the last block to finish sums the partials in index order (the order of a separate
+// one-block reduction) into *Jout and re-arms the counter.
+__device__ void finish_j(const XInvArgs& a) {
+  __shared__ unsigned int last;
+  __shared__ double r2[kNT];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(a.Jcount, 1u) == gridDim.x * gridDim.y - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int n = gridDim.x * gridDim.y;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += kNT) s += __ldcg(a.Jpart + i);
+  r2[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kNT / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) r2[threadIdx.x] += r2[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *a.Jout = r2[0];
+    *a.Jcount = 0u;
+  }
+}
+
+// P3: p = 3 fixed at compile time (chain sink with one contracted slot only).
+template <int L, int SINK, int MINB, bool P3>
+__global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
+  constexpr int S = plan_stages(L);
+  using S0 = StageShape<L, 0>;
+  constexpr int R = S0::R, M = S0::M, NU = M * TB, ITER = (NU + kNT - 1) / kNT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
+  cx<float>* tw0 = tw + L;
+  cx<float>* tile = tw0 + L;
+  __shared__ double red[kNT / 32];
+  load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
+  load_twiddles0<L>(tw0, reinterpret_cast<const cx<float>*>(a.tw));
+  const int row0 = a.row_base + blockIdx.x * ROWS;
+  const cx<float>* in0 = reinterpret_cast<const cx<float>*>(a.in);
+
+  if constexpr (SINK == SINK_CHAIN && MINB == 2) {
+    // one slot, already contracted with the constant M0: G = p rho^(p-1) D
+    constexpr int RH = R / 2 > 0 ? R / 2 : 1;  // x = j + q M < nx <= L/2 needs q < R/2
+    __shared__ float wmax[kNT / 32];
+    __syncthreads();
+    xhermitian<L>(tile, in0 + a.in_slot[0] * a.in_cstride, row0, a.rows, a.P);
+    // p rho^(p-1) of this tile, fetched while the inverse stages run
+    float pa[ITER][RH], pb[ITER][RH];
+#pragma unroll
+    for (int it = 0; it < ITER; it++) {
+      const int u = it * kNT + threadIdx.x;
+      const int j = u % M, line = u / M;
+      const int r = row0 + 2 * line;
+      const bool ok = NU % kNT == 0 || u < NU;
+      const bool va = ok && r < a.rows, vb = ok && r + 1 < a.rows;
+      const long long o = (long long)r * a.nx + j;
+      const int xn = a.nx - j;
+#pragma unroll
+      for (int q = 0; q < RH; q++) {
+        const bool in_x = q * M < xn;
+        pa[it][q] = (in_x && va) ? a.rho[o + q * M] : 0.0f;
+        pb[it][q] = (in_x && vb) ? a.rho[o + a.nx + q * M] : 0.0f;
+      }
+    }
+    __syncthreads();
+    DitRange<float, L, kNT, 1, S, true>::run(tile, tw);
+    float gm = 0.0f;
+    xdit0<L>(tile, tw0, [&](int it, int j, int line, cx<float>* v) {
+      const int r = row0 + 2 * line;
+      const bool va = r < a.rows, vb = r + 1 < a.rows;
+      float* g = a.G + (long long)r * a.nx + j;
+      const int xn = a.nx - j;
+#pragma unroll
+      for (int q = 0; q < RH; q++) {
+        if (q * M >= xn) continue;
+        if (va) {
+          const float G = dpow_t<P3>(pa[it][q], a.p) * v[q].x;
+          g[q * M] = G;
+          gm = fmaxf(gm, fabsf(G));
+        }
+        if (vb) {
+          const float G = dpow_t<P3>(pb[it][q], a.p) * v[q].y;
+          g[a.nx + q * M] = G;
+          gm = fmaxf(gm, fabsf(G));
+        }
+      }
+      return false;
+    });
+    for (int off = 16; off > 0; off >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, off));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = gm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kNT / 32; w++) gm = fmaxf(gm, wmax[w]);
+      if (gm > 0.0f) atomicMax(a.gmax, __float_as_uint(gm));
+    }
+    return;
+  } else if constexpr (SINK == SINK_CHAIN) {
+    float acc[ITER][R][2];
+#pragma unroll
+    for (int it = 0; it < ITER; it++)
+#pragma unroll
+      for (int q = 0; q < R; q++) acc[it][q][0] = acc[it][q][1] = 0.0f;
+    for (int jc = 0; jc < a.ncomp; jc++) {
+      __syncthreads();
+      xhermitian<L>(tile, in0 + a.in_slot[jc] * a.in_cstride, row0, a.rows, a.P);
+      __syncthreads();
+      DitRange<float, L, kNT, 1, S, true>::run(tile, tw);
+      const int c = a.comp[jc];
+      xdit0<L>(tile, tw0, [&](int it, int j, int line, cx<float>* v) {
+        const int ra = row0 + 2 * line, rb = ra + 1;
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+          const int x = j + q * M;
+          float ma = 1.0f, mb = 1.0f;  // contracted slot: coefficient 1
+          if (a.M0v && x < a.nx) {
+            if (ra < a.rows) ma = a.M0v[c * a.M0v_cstride + (long long)ra * a.nx + x];
+            if (rb < a.rows) mb = a.M0v[c * a.M0v_cstride + (long long)rb * a.nx + x];
+          }
+          acc[it][q][0] += ma * v[q].x;
+          acc[it][q][1] += mb * v[q].y;
+        }
+        return false;
+      });
+    }
+    float gm = 0.0f;
+#pragma unroll
+    for (int it = 0; it < ITER; it++) {
+      const int u = it * kNT + threadIdx.x;
+      if (NU % kNT == 0 || u < NU) {
+        const int j = u % M, line = u / M;
+        const int ra = row0 + 2 * line;
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+          const int x = j + q * M;
+          if (x >= a.nx) continue;
+#pragma unroll
+          for (int h = 0; h < 2; h++) {
+            const int row = ra + h;
+            if (row >= a.rows) continue;
+            const long long o = (long long)row * a.nx + x;
+            const float G = dpow(a.rho[o], a.p) * acc[it][q][h];
+            a.G[o] = G;
+            gm = fmaxf(gm, fabsf(G));
+          }
+        }
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, off));
+    if ((threadIdx.x & 31) == 0 && gm > 0.0f) atomicMax(a.gmax, __float_as_uint(gm));
+    return;
+  } else {
+    const int jc = blockIdx.y, c = a.comp[jc];
+    const cx<float>* in = in0 + a.in_slot[jc] * a.in_cstride;
+    if constexpr (SINK == SINK_OBJECTIVE) {
+      if (a.ext) {  // only the rows of the target planes carry H (and the adjoint source)
+        const long long lo = (long long)a.ext[0] * a.ny, hi = (long long)a.ext[1] * a.ny;
+        if (row0 + ROWS <= lo || row0 >= hi) {
+          if (threadIdx.x == 0) a.Jpart[jc * gridDim.x + blockIdx.x] = 0.0;
+          if (a.Jcount) finish_j(a);
+          return;
+        }
+      }
+    }
+    __syncthreads();
+    xhermitian<L>(tile, in, row0, a.rows, a.P);
+    __syncthreads();
+    DitRange<float, L, kNT, 1, S, true>::run(tile, tw);
+
+    if constexpr (SINK == SINK_FIELD) {
+      xdit0<L>(tile, tw0, [&](int, int j, int line, cx<float>* v) {
+        const int ra = row0 + 2 * line, rb = ra + 1;
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+          const int x = j + q * M;
+          if (x >= a.nx) continue;
+          if (ra < a.rows) a.H[c * a.H_cstride + (long long)ra * a.nx + x] = v[q].x;
+          if (rb < a.rows) a.H[c * a.H_cstride + (long long)rb * a.nx + x] = v[q].y;
+        }
+        return false;
+      });
+      return;
+    } else {
+      // SINK_OBJECTIVE: J partial; g_c = 2 w_c (H_c - Ht_c) on the mask, zero elsewhere and
+      // for x >= nx (the padding); the forward stage 0 of the adjoint source runs on g
+      const float wc = a.w[c];
+      double jacc = 0.0;
+      int mine = 0;
+      xdit0<L>(tile, tw0, [&](int, int j, int line, cx<float>* v) {
+        const int ra = row0 + 2 * line;
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+          const int x = j + q * M;
+          float g[2] = {0.0f, 0.0f};
+          if (x < a.nx) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+              const int row = ra + h;
+              if (row >= a.rows) continue;
+              const long long o = (long long)row * a.nx + x;
+              const float hv = h ? v[q].y : v[q].x;
+              if (a.H) a.H[c * a.H_cstride + o] = hv;
+              if (wc != 0.0f && a.mask[o]) {
+                mine = 1;
+                const float r = hv - (a.Ht ? a.Ht[c * a.Ht_cstride + o] : a.Htc[c]);
+                jacc += (double)wc * (double)r * (double)r;
+                g[h] = 2.0f * wc * r;
+              }
+            }
+          }
+          v[q] = mk(g[0], g[1]);
+        }
+        return true;
+      });
+      for (int off = 16; off > 0; off >>= 1) jacc += __shfl_xor_sync(0xffffffffu, jacc, off);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = jacc;
+      const int any_mask = __syncthreads_or(mine);
+      if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kNT / 32; w++) s += red[w];
+        a.Jpart[jc * gridDim.x + blockIdx.x] = s;
+      }
+      if (a.Jcount) finish_j(a);
+      if (!a.adj_out) return;
+      cx<float>* adj = reinterpret_cast<cx<float>*>(a.adj_out) + a.in_slot[jc] * a.in_cstride;
+      if (!any_mask) {  // the adjoint source vanishes on all rows of this block
+        for (int i = threadIdx.x; i < ROWS * a.P; i += kNT) {
+          const int rr = i / a.P, k = i - rr * a.P, row = row0 + rr;
+          if (row < a.rows) adj[(long long)row * a.P + k] = zero<float>();
+        }
+        return;
+      }
+      DifRange<float, L, kNT, 1, S, true>::run(tile, tw);
+      xseparate<L>(tile, adj, row0, a.rows, a.P);
+    }
+  }
+}
+
+template <int L, int SINK, int MINB, bool P3>
+int run_xinv_sink(const XInvArgs& a, cudaStream_t s) {
+  const size_t sm = xsmem<L>();
+  static bool init = false;
+  if (!init) {
+    if (cudaFuncSetAttribute(k_xinv<L, SINK, MINB, P3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        cudaSuccess)
+      return -1;
+    init = true;
+  }
+  const int blocks = (a.rows - a.row_base + ROWS - 1) / ROWS;
+  if (blocks <= 0 || a.ncomp == 0) return 0;
+  const int gy = SINK == SINK_CHAIN ? 1 : a.ncomp;
+  k_xinv<L, SINK, MINB, P3><<<dim3(blocks, gy), kNT, sm, s>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+template <int L>
+int run_xinv(const XInvArgs& a, cudaStream_t s) {
+  if (a.sink == SINK_FIELD) return run_xinv_sink<L, SINK_FIELD, 2, false>(a, s);
+  if (a.sink == SINK_OBJECTIVE) return run_xinv_sink<L, SINK_OBJECTIVE, 2, false>(a, s);
+  if (a.ncomp == 1 && a.M0v == nullptr) {  // contracted slot
+    if constexpr (k_per_thread<L>()) {
+      if (a.p == 3.0f) return run_xinv_sink<L, SINK_CHAIN, 2, true>(a, s);
+    }
+    return run_xinv_sink<L, SINK_CHAIN, 2, false>(a, s);
+  }
+  return run_xinv_sink<L, SINK_CHAIN, 1, false>(a, s);
+}
+
+}  // namespace
+
+int xinv_rows_per_block() { return ROWS; }
+
+int launch_xinv(int L, const XInvArgs& a, cudaStream_t s) {
+  switch (L) {
+#define TM_CASE(LL) \
+  case LL:          \
+    return run_xinv<LL>(a, s);
+    TM_FOR_EACH_L(TM_CASE)
+#undef TM_CASE
+  }
+  return -2;
+}
+
+}  // namespace tmk

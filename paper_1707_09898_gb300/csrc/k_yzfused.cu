@@ -302,6 +302,370 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_staged(YZArgs a, int c) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialized versions of the two single-component kernels for two-stage plans
+// whose first stage has kNT units and whose last stage has 2 kNT (L = 512): a block of
+// 512 threads runs two groups of eight warps on one plane each, a plane apart, with a
+// tile per group and one block barrier per plane:
+//   forward: the "transform" warps read the staged input rows of plane z + 1 and run
+//            the first DIF stage into one tile while the "accumulate" warps finish
+//            plane z from the other tile (the last stage in registers) and add
+//            s(zo - z) times it into their sums;
+//   adjoint: the "load" warps form s(z - zp) times the source spectrum for plane z + 1
+//            and run the first inverse stage into one tile while the "store" warps
+//            finish plane z from the other tile and write its rows.
+// The tensor slices (and, forward, the next plane's input rows) are copied into shared
+// memory with cp.async a round ahead. C is the tensor component, so the sign rules of
+// the folded tensor are resolved at compile time; the positions of the last stage are
+// g R1 + q with frequency ky = g + q L/R1, so the tensor row of every element is a
+// compile-time offset from one of two per-thread bases.
+template <int L>
+__host__ __device__ constexpr bool yz_ws_plan() {
+  return plan_stages(L) == 2 && StageShape<L, 0>::NU == kNT && StageShape<L, 1>::NU == 2 * kNT;
+}
+
+__device__ __forceinline__ void bar_named(int id, int n) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+constexpr int kBarAll = 1, kBarGroup = 2;  // named barriers (0 is __syncthreads)
+
+// tensor factor of last-stage element q of group g, C's sign rules applied;
+// tlo = slice + g TB + line (rows g + q L/R1), thi = slice + (L - g) TB + line
+template <int L, int C>
+__device__ __forceinline__ float ws_tensor(const float* tlo, const float* thi, int g, int q, float cz) {
+  constexpr int R1 = StageShape<L, 1>::R, QS = L / R1;
+  float f = cz * (q < R1 / 2 ? tlo[q * QS * TB] : thi[-q * QS * TB]);
+  // ky = g + q QS lies above L/2 for q > R1/2, and for q = R1/2 unless g = 0
+  if constexpr (C == 3 || C == 5) {
+    if (q > R1 / 2 || (q == R1 / 2 && g > 0)) f = -f;
+  }
+  return f;
+}
+template <int C>
+__device__ __forceinline__ cx<float> ws_apply(float f, cx<float> v) {  // (-i f) v for xz, yz
+  return C >= 4 ? mk(f * v.y, -f * v.x) : mk(f * v.x, f * v.y);
+}
+template <int L, int C>
+__device__ __forceinline__ cx<float> ws_tensor_apply(const float* tlo, const float* thi, int g, int q, float cz,
+                                                     cx<float> v) {
+  return ws_apply<C>(ws_tensor<L, C>(tlo, thi, g, q, cz), v);
+}
+
+template <int L>
+constexpr size_t fwd_ws_smem() {
+  return (size_t)(L + 2 * L * TB + (L / 2) * TB) * sizeof(float2) + (size_t)2 * (L / 2 + 1) * TB * sizeof(float);
+}
+
+// Forward, flattened: block b transforms the (column block, design plane) items
+// [T b / B, T (b + 1) / B), T = (P / TB) nzin, z fastest, so that every SM holds one block
+// with the same share of the work. The sums of a column block are flushed as a segment
+// partial after the block's last item of it (at most two segments per block, as long as
+// B >= P / TB); each segment adds its item count to the column block's counter, and the
+// block whose segment completes the nzin items sums that column block's segments in
+// block order, writes the target plane's spectrum into B and runs the inverse y
+// transform of the target plane on it (rows y < ny into A), then re-arms the counter.
+template <int L, int C>
+__global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a) {
+  using S0 = StageShape<L, 0>;
+  using S1 = StageShape<L, 1>;
+  constexpr int R0 = S0::R, M0 = S0::M, R1 = S1::R, KY = L / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int fin[2];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
+  cx<float>* tiles = tw + L;                                      // [2][L][TB]
+  cx<float>* sin = tiles + 2 * L * TB;                            // [L/2][TB] input rows
+  float* stt0 = reinterpret_cast<float*>(sin + (L / 2) * TB);     // [2][KY][TB] tensor slices
+  load_twiddles<float, NTF>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
+  if (threadIdx.x < 2) fin[threadIdx.x] = -1;
+  const long long T = (long long)(a.P / TB) * a.nzin;
+  const int i0 = (int)(T * blockIdx.x / gridDim.x), i1 = (int)(T * (blockIdx.x + 1) / gridDim.x);
+  const int n = i1 - i0;
+  const int cb0 = i0 / a.nzin;  // column block of segment 0
+  __syncthreads();
+  if (threadIdx.x < kNT) {
+    // transform warps: stage 0 of item i0 + r in round r; copies a round ahead
+    const int t = threadIdx.x;
+    const cx<float>* in0 = reinterpret_cast<const cx<float>*>(a.in) + a.in_slot[0] * a.in_cstride;
+    const float* tc = a.Tz + C * a.Tc;
+    auto issue_rows = [&](int cb, int z) {  // 16-byte copies: 8 per input row
+      const cx<float>* src = in0 + z * a.in_zstride + cb * TB;
+      for (int q = t; q < a.n_in * 8; q += kNT) {
+        const int row = q >> 3, part = q & 7;
+        cp16(sin + row * TB + part * 2, src + (long long)row * a.P + part * 2);
+      }
+    };
+    auto issue_slice = [&](int cb, int z, int buf) {  // 4 per tensor row
+      const int dz = a.zout - z, adz = dz < 0 ? -dz : dz;
+      const float* tsrc = tc + adz * a.Tdz + cb * TB;
+      float* stt = stt0 + buf * KY * TB;
+      for (int q = t; q < KY * 4; q += kNT) {
+        const int row = q >> 2, part = q & 3;
+        cp16(stt + row * TB + part * 4, tsrc + (long long)row * a.P + part * 4);
+      }
+    };
+    // (column block, plane) of the current item and of the next one
+    int cb = cb0, z = a.zin0 + (i0 - cb0 * a.nzin);
+    int cbn = z + 1 == a.zin0 + a.nzin ? cb + 1 : cb, zn = z + 1 == a.zin0 + a.nzin ? a.zin0 : z + 1;
+    if (n > 0) issue_rows(cb, z);
+    cp_commit();
+    const int line = t % TB, j = t / TB;
+    for (int r = 0; r <= n; r++) {
+      if (r < n) {
+        cp_wait<0>();
+        bar_named(kBarGroup, kNT);  // the item's rows are in shared memory for every transform thread
+        cx<float> v[R0];
+#pragma unroll
+        for (int q = 0; q < R0; q++) {
+          const int pos = j + q * M0;
+          v[q] = (q < R0 / 2 && pos < a.n_in) ? sin[pos * TB + line] : zero<float>();  // n_in <= L/2
+        }
+        bar_named(kBarGroup, kNT);  // every transform thread is done with the rows
+        issue_slice(cb, z, r & 1);
+        cp_commit();
+        if (r + 1 < n) issue_rows(cbn, zn);
+        cp_commit();
+        cb = cbn;
+        z = zn;
+        cbn = z + 1 == a.zin0 + a.nzin ? cb + 1 : cb;
+        zn = z + 1 == a.zin0 + a.nzin ? a.zin0 : z + 1;
+        Dft<float, R0, false>::run(v);
+        apply_twiddles<float, L, 0, false>(v, j, tw);
+        cx<float>* tile = tiles + (r & 1) * L * TB;
+#pragma unroll
+        for (int q = 0; q < R0; q++) tile[(j + q * M0) * TB + line] = v[q];
+        cp_wait<1>();  // this thread's copies of the slice have landed (the next rows may not)
+      }
+      bar_named(kBarAll, NTF);
+    }
+  } else {
+    // accumulate warps: last stage of item i0 + r - 1 in round r, times s, into the sums
+    const int t = threadIdx.x - kNT;
+    const float coef = a.coef[0][C];
+    cx<float> acc[2][R1];
+#pragma unroll
+    for (int it = 0; it < 2; it++)
+#pragma unroll
+      for (int q = 0; q < R1; q++) acc[it][q] = zero<float>();
+    int cb = cb0, z = a.zin0 + (i0 - cb0 * a.nzin);  // the item of the next round
+    for (int r = 0; r <= n; r++) {
+      if (r >= 1) {
+        const int i = i0 + r - 1;
+        const int dz = a.zout - z;
+        const float cz = (C >= 4 && dz < 0) ? -coef : coef;
+        const cx<float>* tile = tiles + ((r - 1) & 1) * L * TB;
+        const float* stt = stt0 + ((r - 1) & 1) * KY * TB;
+#pragma unroll
+        for (int it = 0; it < 2; it++) {
+          const int u = it * kNT + t, line = u % TB, g = u / TB;
+          cx<float> v[R1];
+#pragma unroll
+          for (int q = 0; q < R1; q++) v[q] = tile[(g * R1 + q) * TB + line];
+          Dft<float, R1, false>::run(v);
+          const float* tlo = stt + g * TB + line;
+          const float* thi = stt + (L - g) * TB + line;
+#pragma unroll
+          for (int q = 0; q < R1; q++) acc[it][q] = acc[it][q] + ws_tensor_apply<L, C>(tlo, thi, g, q, cz, v[q]);
+        }
+        const bool last = z + 1 == a.zin0 + a.nzin;  // the last plane of column block cb
+        if (i + 1 == i1 || last) {  // the block's last item of column block cb
+          const int sg = cb == cb0 ? 0 : 1;
+          cx<float>* seg = reinterpret_cast<cx<float>*>(a.seg) + (long long)(blockIdx.x * 2 + sg) * L * TB;
+#pragma unroll
+          for (int it = 0; it < 2; it++) {
+            const int u = it * kNT + t, line = u % TB, g = u / TB;
+#pragma unroll
+            for (int q = 0; q < R1; q++) {
+              seg[(g * R1 + q) * TB + line] = acc[it][q];
+              acc[it][q] = zero<float>();
+            }
+          }
+          __threadfence();
+          bar_named(kBarGroup + 1, kNT);  // every accumulate thread's partial is written and fenced
+          if (t == 0) {
+            const int cnt = i + 1 - max(i0, cb * a.nzin);
+            if ((int)atomicAdd(a.cnt + cb, (unsigned)cnt) + cnt == a.nzin) fin[sg] = cb;
+          }
+        }
+        if (last) {
+          cb++;
+          z = a.zin0;
+        } else {
+          z++;
+        }
+      }
+      bar_named(kBarAll, NTF);
+    }
+  }
+  __syncthreads();
+  for (int sg = 0; sg < 2; sg++) {
+    const int cb = fin[sg];
+    if (cb < 0) continue;
+    // this block completed column block cb: sum its segments in block order
+    __threadfence();
+    const int B = gridDim.x;
+    const long long x0 = (long long)cb * a.nzin, x1 = x0 + a.nzin - 1;  // first and last item of cb
+    const int b_lo = (int)(((x0 + 1) * B - 1) / T), b_hi = (int)(((x1 + 1) * B - 1) / T);
+    const cx<float>* segs = reinterpret_cast<const cx<float>*>(a.seg);
+    cx<float>* tile = tiles;
+    cx<float>* bplane =
+        reinterpret_cast<cx<float>*>(a.out) + a.out_slot * a.out_cstride + (long long)a.zout * L * a.P + cb * TB;
+    static_assert((L * TB) % NTF == 0, "elements per thread");
+    constexpr int NE = L * TB / NTF;
+    cx<float> acc[NE];
+#pragma unroll
+    for (int k = 0; k < NE; k++) acc[k] = zero<float>();
+    for (int b = b_lo; b <= b_hi; b++) {  // a segment's loads are all in flight together
+      const int sgb = (int)(T * b / B) / a.nzin == cb ? 0 : 1;
+      const float2* sp = reinterpret_cast<const float2*>(segs + (long long)(b * 2 + sgb) * L * TB) + threadIdx.x;
+      float2 v[NE];
+#pragma unroll
+      for (int k = 0; k < NE; k++) v[k] = __ldcg(sp + k * NTF);
+#pragma unroll
+      for (int k = 0; k < NE; k++) acc[k] = acc[k] + mk(v[k].x, v[k].y);
+    }
+#pragma unroll
+    for (int k = 0; k < NE; k++) {
+      const int e = threadIdx.x + k * NTF;
+      tile[e] = acc[k];
+      bplane[(long long)(e / TB) * a.P + (e % TB)] = acc[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) a.cnt[cb] = 0u;
+    {  // first inverse stage (last plan stage, positions g R1 + q), 2 kNT units
+      const int u = threadIdx.x, line = u % TB, g = u / TB;
+      cx<float> v[R1];
+#pragma unroll
+      for (int q = 0; q < R1; q++) v[q] = tile[(g * R1 + q) * TB + line];
+      Dft<float, R1, true>::run(v);
+#pragma unroll
+      for (int q = 0; q < R1; q++) tile[(g * R1 + q) * TB + line] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < kNT) {  // last inverse stage (plan stage 0), rows y < ny out
+      const int line = threadIdx.x % TB, j = threadIdx.x / TB;
+      cx<float> v[R0];
+#pragma unroll
+      for (int q = 0; q < R0; q++) v[q] = tile[(j + q * M0) * TB + line];
+      apply_twiddles<float, L, 0, true>(v, j, tw);
+      Dft<float, R0, true>::run(v);
+      cx<float>* o = reinterpret_cast<cx<float>*>(a.yrows) + cb * TB + line;
+#pragma unroll
+      for (int q = 0; q < R0; q++) {
+        const int y = j + q * M0;
+        if (y < a.n_in) o[(long long)y * a.P] = v[q];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int L>
+constexpr size_t adj_ws_smem() {
+  return (size_t)(L + 2 * L * TB) * sizeof(float2) + (size_t)2 * (L / 2 + 1) * TB * sizeof(float);
+}
+
+// Adjoint: the (column block, design plane) items [T b / B, T (b + 1) / B) of block b,
+// T = (P / TB) nzout; one item per round and group.
+template <int L, int C>
+__global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a) {
+  using S0 = StageShape<L, 0>;
+  using S1 = StageShape<L, 1>;
+  constexpr int R0 = S0::R, M0 = S0::M, R1 = S1::R, KY = L / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
+  cx<float>* tiles = tw + L;                                      // [2][L][TB]
+  float* stt0 = reinterpret_cast<float*>(tiles + 2 * L * TB);     // [2][KY][TB] tensor slices
+  load_twiddles<float, NTF>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
+  const long long T = (long long)(a.P / TB) * a.nzout;
+  const int i0 = (int)(T * blockIdx.x / gridDim.x), i1 = (int)(T * (blockIdx.x + 1) / gridDim.x);
+  const int n = i1 - i0;
+  auto item = [&](int i, int& kx0, int& z) {
+    const int cb = i / a.nzout;
+    kx0 = cb * TB;
+    z = a.zout0 + (i - cb * a.nzout);
+  };
+  const float* tc = a.Tz + C * a.Tc;
+  auto issue_slice = [&](int i, int buf, int t) {  // 16-byte copies, 4 per tensor row
+    int kx0, z;
+    item(i, kx0, z);
+    const int dz = z - a.zin0, adz = dz < 0 ? -dz : dz;
+    const float* tsrc = tc + adz * a.Tdz + kx0;
+    float* stt = stt0 + buf * KY * TB;
+    for (int q = t; q < KY * 4; q += kNT) {
+      const int row = q >> 2, part = q & 3;
+      cp16(stt + row * TB + part * 4, tsrc + (long long)row * a.P + part * 4);
+    }
+  };
+  if (threadIdx.x >= kNT && n > 0) issue_slice(i0, 0, threadIdx.x - kNT);
+  cp_commit();
+  cp_wait<0>();
+  __syncthreads();
+  if (threadIdx.x < kNT) {
+    // load warps: s times the source, first inverse stage, into tile r % 2 in round r
+    const int t = threadIdx.x;
+    const float coef = a.coef[0][0][C];
+    const cx<float>* src = reinterpret_cast<const cx<float>*>(a.src) + a.in_slot[0] * a.src_cstride +
+                           a.zin0 * a.src_zstride;
+    for (int r = 0; r <= n; r++) {
+      if (r < n) {
+        int kx0, z;
+        item(i0 + r, kx0, z);
+        const int dz = z - a.zin0;
+        const float cz = (C >= 4 && dz < 0) ? -coef : coef;
+        const float* stt = stt0 + (r & 1) * KY * TB;
+        cx<float>* tile = tiles + (r & 1) * L * TB;
+        cx<float> v[2][R1];
+#pragma unroll
+        for (int it = 0; it < 2; it++) {
+          const int u = it * kNT + t, line = u % TB, g = u / TB;
+          const cx<float>* s = src + (long long)(g * R1) * a.P + kx0 + line;  // positions g R1 + q
+#pragma unroll
+          for (int q = 0; q < R1; q++) v[it][q] = s[q * a.P];
+        }
+#pragma unroll
+        for (int it = 0; it < 2; it++) {
+          const int u = it * kNT + t, line = u % TB, g = u / TB;
+          const float* tlo = stt + g * TB + line;
+          const float* thi = stt + (L - g) * TB + line;
+#pragma unroll
+          for (int q = 0; q < R1; q++) v[it][q] = ws_apply<C>(ws_tensor<L, C>(tlo, thi, g, q, cz), v[it][q]);
+          Dft<float, R1, true>::run(v[it]);
+#pragma unroll
+          for (int q = 0; q < R1; q++) tile[(g * R1 + q) * TB + line] = v[it][q];
+        }
+      }
+      bar_named(kBarAll, NTF);
+    }
+  } else {
+    // store warps: last inverse stage of the item of round r - 1, rows y < n_out out
+    const int t = threadIdx.x - kNT;
+    const int line = t % TB, j = t / TB;
+    cx<float>* out0 = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[0] * a.out_cstride;
+    for (int r = 0; r <= n; r++) {
+      if (r + 1 < n) issue_slice(i0 + r + 1, (r + 1) & 1, t);
+      cp_commit();
+      if (r >= 1) {
+        int kx0, z;
+        item(i0 + r - 1, kx0, z);
+        const cx<float>* tile = tiles + ((r - 1) & 1) * L * TB;
+        cx<float> v[R0];
+#pragma unroll
+        for (int q = 0; q < R0; q++) v[q] = tile[(j + q * M0) * TB + line];
+        apply_twiddles<float, L, 0, true>(v, j, tw);
+        Dft<float, R0, true>::run(v);
+        cx<float>* o = out0 + z * a.out_zstride + kx0 + line;
+#pragma unroll
+        for (int q = 0; q < R0; q++) {
+          const int y = j + q * M0;
+          if (y < a.n_out) o[(long long)y * a.P] = v[q];
+        }
+      }
+      cp_wait<0>();  // the next item's slice has landed
+      bar_named(kBarAll, NTF);
+    }
+  }
+}
+
 // out[pos][kx] = sum over z chunks of the partials, in chunk order
 __global__ void k_yz_reduce(const float2* part, int nchunks, long long plane, float2* out) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < plane;
@@ -338,11 +702,50 @@ int launch_adj(const ZYArgs& a, int c, cudaStream_t s) {
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
+int sm_count() {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+  }
+  return nsm;
+}
+
+template <int L, int C>
+int launch_adj_ws(const ZYArgs& a, cudaStream_t s) {
+  constexpr size_t sm = adj_ws_smem<L>();
+  static bool init = false;
+  if (!init) {
+    if (cudaFuncSetAttribute(k_zy_adj_ws<L, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        cudaSuccess)
+      return -1;
+    init = true;
+  }
+  const long long items = (long long)(a.P / TB) * a.nzout;
+  const int blocks = (int)(items < sm_count() ? items : sm_count());  // one resident block per SM
+  k_zy_adj_ws<L, C><<<blocks, NTF, sm, s>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
 template <int L>
 int run_zy_adj(const ZYArgs& a, cudaStream_t s) {
   if (a.nzout <= 0 || a.nout <= 0) return 0;
   const int c = single_component(a.need[0][0]);
-  if (a.nin == 1 && a.nout == 1 && a.nzin == 1 && c >= 0) return launch_adj<L, true>(a, c, s);
+  if (a.nin == 1 && a.nout == 1 && a.nzin == 1 && c >= 0) {
+    if constexpr (yz_ws_plan<L>()) {
+      switch (c) {
+        case 0: return launch_adj_ws<L, 0>(a, s);
+        case 1: return launch_adj_ws<L, 1>(a, s);
+        case 2: return launch_adj_ws<L, 2>(a, s);
+        case 3: return launch_adj_ws<L, 3>(a, s);
+        case 4: return launch_adj_ws<L, 4>(a, s);
+        default: return launch_adj_ws<L, 5>(a, s);
+      }
+    }
+    return launch_adj<L, true>(a, c, s);
+  }
   return launch_adj<L, false>(a, -1, s);
 }
 
@@ -379,12 +782,46 @@ int launch_fwd(const YZArgs& a, int c, int nch, cudaStream_t s) {
   return 0;
 }
 
+template <int L, int C>
+int launch_fwd_ws(const YZArgs& a, int nch, cudaStream_t s) {
+  constexpr size_t sm = fwd_ws_smem<L>();
+  static bool init = false;
+  if (!init) {
+    if (cudaFuncSetAttribute(k_yz_fwd_ws<L, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+        cudaSuccess)
+      return -1;
+    init = true;
+  }
+  const long long items = (long long)(a.P / TB) * a.nzin;
+  const int blocks = (int)(items < sm_count() ? items : sm_count());  // one resident block per SM
+  k_yz_fwd_ws<L, C><<<blocks, NTF, sm, s>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;  // 1: the target plane's y inverse is done
+}
+
+template <int L>
+int launch_fwd_single(const YZArgs& a, int c, int nch, cudaStream_t s) {
+  if constexpr (yz_ws_plan<L>()) {
+    // needs the segment buffers, and at most two column blocks per block (blocks >= P / TB)
+    if (a.n_in <= L / 2 && a.seg && a.cnt && a.yrows && a.P / TB <= sm_count()) {
+      switch (c) {
+        case 0: return launch_fwd_ws<L, 0>(a, nch, s);
+        case 1: return launch_fwd_ws<L, 1>(a, nch, s);
+        case 2: return launch_fwd_ws<L, 2>(a, nch, s);
+        case 3: return launch_fwd_ws<L, 3>(a, nch, s);
+        case 4: return launch_fwd_ws<L, 4>(a, nch, s);
+        default: return launch_fwd_ws<L, 5>(a, nch, s);
+      }
+    }
+  }
+  return launch_fwd_staged<L>(a, c, nch, s);
+}
+
 template <int L>
 int run_yz_fwd(const YZArgs& a, cudaStream_t s) {
   const int nch = (a.nzin + a.zchunk - 1) / a.zchunk;
   const int c = single_component(a.need[0]);
-  if ((a.nin == 1 && c >= 0 ? launch_fwd_staged<L>(a, c, nch, s) : launch_fwd<L, false>(a, -1, nch, s)) != 0)
-    return -1;
+  const int r = a.nin == 1 && c >= 0 ? launch_fwd_single<L>(a, c, nch, s) : launch_fwd<L, false>(a, -1, nch, s);
+  if (r != 0) return r;
   const long long plane = (long long)L * a.P;
   const long long b = (plane + 255) / 256;
   k_yz_reduce<<<(int)(b > 2048 ? 2048 : b), 256, 0, s>>>(reinterpret_cast<const float2*>(a.part), nch, plane,
