@@ -4,10 +4,12 @@
 Workload: 256^3 cells of 1 mm, design box = output grid, M0 = (0, 0, Ms),
 p = 3, rho ~ U[0,1] (seed 7), objective J = sum over a centred 64 x 64 patch of
 the top layer of (H_z - 0.2 Ms)^2; padded FFT grid 512^3. One step = one
-stray-field + adjoint-gradient evaluation (tm_objective_and_gradient: forward
-x/y/z/y/x passes with the fused objective, adjoint passes with the fused chain
-rule) followed by one projected-gradient update (tm_optimize_step). The
-tensor setup is excluded, as in the paper's timings.
+projected-gradient update and one stray-field + adjoint-gradient evaluation
+(forward x/y/z/y/x passes with the fused objective, adjoint passes with the fused
+chain rule). The prepared path makes it one call, tm_evaluate_step: the update on
+the previous gradient runs inside the first pass of the evaluation at the new rho
+(--two-call-step: tm_evaluate + tm_optimize_step). The tensor setup is excluded, as
+in the paper's timings.
 
 Arms:
   native (default)  the CUDA library through its C ABI
@@ -61,6 +63,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-oneshot", action="store_true", help="skip timing the one-shot call")
+    ap.add_argument("--two-call-step", action="store_true",
+                    help="prepared path: tm_evaluate + tm_optimize_step per step instead of tm_evaluate_step")
     ap.add_argument("--separate-yz", action="store_true",
                     help="prepared path: y and direct z passes as separate kernels (default: fused)")
     ap.add_argument("--m0", choices=["const", "vmf"], default="const",
@@ -174,7 +178,7 @@ def _need(v, u):
     return sum(1 for x in c if x != 0)
 
 
-def alg_bytes(wl, L, direct=True, fused=True):
+def alg_bytes(wl, L, direct=True, fused=True, step_fused=False):
     """Algorithmic bytes per launch of each kernel kind for the objective+gradient step.
 
     Half spectra kx = 0..L/2 only (no padding); components actually carried: with a
@@ -185,6 +189,8 @@ def alg_bytes(wl, L, direct=True, fused=True):
     fused: the prepared path's y transform of the design planes fused with the direct z
     sum (forward onto one target plane with one output; adjoint always): those kinds read
     or write the x-transformed design planes, the tensor once, and the target planes.
+    step_fused: the x forward pass also applies the projected-gradient step (reads G,
+    writes the new rho).
     """
     nx, ny, nz = wl.n_out
     nzd = wl.nzd
@@ -208,7 +214,7 @@ def alg_bytes(wl, L, direct=True, fused=True):
     Tzc = nzd * (Ly // 2 + 1) * K * 4        # x/y-transformed tensor over nzd offsets, one component
     obj = s8 * npl * ny * K * fout * 2 + npl * ny * nx  # spectra in, adjoint spectra out, mask
     chain = s8 * aout * nzd * ny * K + 8 * nzd * ny * nx + m0
-    out = {"x_forward": 4 * nzd * ny * nx + m0 + s8 * fin * nzd * ny * K}
+    out = {"x_forward": (12 if step_fused else 4) * nzd * ny * nx + m0 + s8 * fin * nzd * ny * K}
     if direct:  # prepared path: the objective on the target rows is its own kind
         out["objective"] = obj
         out["x_inverse"] = chain
@@ -341,14 +347,21 @@ def run_native(args):
     if prepared:
         m.set_target(mask, Ht_const=Htc, w=w)
 
+    one_call = prepared and not args.two_call_step
+
     def step(r=None):
         r = rho if r is None else r
+        if one_call:  # the update on the previous gradient, then the evaluation at the new rho
+            m.evaluate_step(r, G, wl.alpha, True, reuse_max=True, sync=False)
+            return
         if prepared:
             m.evaluate(r, G=G, sync=False)
         else:
             m.objective_and_gradient(r, mask, Ht_const=Htc, w=w, G=G, sync=False)
         m.optimize_step(r, G, wl.alpha, True, **reuse)
 
+    if one_call:
+        m.evaluate(rho, G=G, sync=False)  # the gradient the first step moves along
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -434,7 +447,8 @@ def run_native(args):
     L = m.fft_lengths()
     roof = None
     if prof:
-        ab = alg_bytes(wl, L, direct=prepared, fused=fused)
+        step_fused = one_call and L[0] == 512 and wl.m0_kind == "const"
+        ab = alg_bytes(wl, L, direct=prepared, fused=fused, step_fused=step_fused)
         kind = max((k for k in prof if prof[k][1] > 0 and k in ab), key=lambda k: prof[k][0])
         t_launch = prof[kind][0] / prof[kind][1] / 1e3
         achieved = ab[kind] / t_launch / 1e9
@@ -454,12 +468,14 @@ def run_native(args):
         "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "impl": args.impl,
-        "config": {"workload": wl.name, "cells": list(wl.n_out), "fft": list(L), "step": "objective+gradient+update",
+        "config": {"workload": wl.name, "cells": list(wl.n_out), "fft": list(L), "step": "update+objective+gradient",
                    "yz": "fused" if fused else "separate",
                    "parallelism": f"replicas{ws}", "l2": "working set (>2 GB) larger than L2; no flush"},
         "clocks": ck, "gpu_launches": (int(round(launches_per_step * args.steps)) if launches_per_step else None),
         "roofline": roof, "e2e": e2e, "J_first": J0, "oneshot": oneshot,
-        "call": "tm_set_target once; per step tm_evaluate + tm_optimize_step" if prepared else None,
+        "call": (("tm_set_target once; per step tm_evaluate_step (update on the previous gradient, "
+                  "then the evaluation)") if one_call else
+                 "tm_set_target once; per step tm_evaluate + tm_optimize_step") if prepared else None,
     }
     if ws == 1 and not args.no_cpu_baseline and args.impl == "native":
         try:

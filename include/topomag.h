@@ -169,6 +169,24 @@ int tm_get_objective(tm_ctx* ctx, double* J_host, void* stream);
 int tm_optimize_step(tm_ctx* ctx, float* rho, const float* dJdrho, float alpha, int normalize, void* stream);
 
 /*
+ * One iteration of the projected-gradient loop (Sec. "Methodology") in a single call:
+ * the step of tm_optimize_step on the gradient dJdrho holds (normally the one the
+ * previous evaluation wrote), then tm_evaluate at the new rho, which overwrites
+ * dJdrho with the new gradient. Same results, bit for bit, as
+ *   tm_optimize_step(ctx, rho, dJdrho, alpha, normalize, stream);
+ *   tm_evaluate(ctx, rho, J_host, dJdrho, stream);
+ * A loop starts with one tm_evaluate and then calls this once per iteration.
+ * rho [nzd][ny][nx] updated in place; normalize as for tm_optimize_step (2 reuses
+ * max|dJdrho| from the evaluation that wrote it). Where the prepared path transforms
+ * rho as one spectrum along x with L = 512 (constant M0, target on at most 8 planes),
+ * the step is applied inside that first pass, which then writes the new rho; in every
+ * other case it runs as its own pass first. Requires tm_set_target. Errors as
+ * tm_evaluate; TM_ERR_ARG for null arrays or a non-finite alpha.
+ */
+int tm_evaluate_step(tm_ctx* ctx, float* rho, float alpha, int normalize, double* J_host, float* dJdrho,
+                     void* stream);
+
+/*
  * Allocation-free projected-gradient step (no context needed). For callers that
  * must not allocate device memory when they call in: code running under a
  * framework whose caching allocator has reserved the device memory (a fresh

@@ -43,6 +43,7 @@ _SIGS = {
     "tm_evaluate": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp]),
     "tm_set_stencil_objective": (ctypes.c_int, [vp, ctypes.c_longlong, vp, vp, vp, vp, vp, vp]),
     "tm_optimize_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_float, ctypes.c_int, vp]),
+    "tm_evaluate_step": (ctypes.c_int, [vp, vp, ctypes.c_float, ctypes.c_int, vp, vp, vp]),
     "tm_optimize_step_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_longlong, ctypes.c_float, ctypes.c_int, vp]),
     "tm_profile": (ctypes.c_int, [vp, ctypes.c_int]),
     "tm_set_fused": (ctypes.c_int, [vp, ctypes.c_int]),

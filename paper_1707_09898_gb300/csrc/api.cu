@@ -51,6 +51,11 @@ struct tm_ctx {
   double* Jdev = nullptr;
   unsigned int* gmax = nullptr;
   const float* gmax_of = nullptr;  // the array whose max |.| gmax holds (set by the chain-rule pass)
+  // projected-gradient step that tm_evaluate_step hands to the x forward pass of rho
+  float* pend_rho = nullptr;
+  const float* pend_G = nullptr;
+  float pend_alpha = 0.0f;
+  int pend_normalize = 0;
   unsigned int* Jcount = nullptr;  // blocks of the objective pass done (re-armed by the last one)
   bool fuse_yz = true;             // prepared path: y transform fused with the direct z sum
   float2* yzpart = nullptr;        // [z chunks][Ly][P] partial planes of the fused forward
@@ -487,6 +492,14 @@ int xfwd_rho(tm_ctx* ctx, const float* rho, cudaStream_t s, int* nslots) {
   x.out_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
   x.tw = ctx->tw;
   *nslots = ctx->m0_var ? 3 : 1;
+  if (ctx->pend_rho && ctx->pend_rho == rho && xfwd_fuses_step(ctx->L[0], x.src, *nslots)) {
+    x.upd_rho = ctx->pend_rho;
+    x.upd_G = ctx->pend_G;
+    x.upd_alpha = ctx->pend_alpha;
+    x.upd_normalize = ctx->pend_normalize;
+    x.upd_gmax = ctx->gmax;
+    ctx->pend_rho = nullptr;  // consumed
+  }
   Timed t(ctx, KIND_XFWD, s);
   CKL(launch_xfwd(ctx->L[0], x, *nslots, s));
   return TM_OK;
@@ -1263,6 +1276,46 @@ int tm_optimize_step(tm_ctx* ctx, float* rho, const float* dJdrho, float alpha, 
   }
   CKL(launch_update(rho, dJdrho, n, alpha, normalize != 0, ctx->gmax, s));
   return TM_OK;
+}
+
+int tm_evaluate_step(tm_ctx* ctx, float* rho, float alpha, int normalize, double* J_host, float* dJdrho,
+                     void* stream) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!ctx->have_target) return fail(ctx, TM_ERR_STATE, "no target: call tm_set_target first");
+  if (!rho || !dJdrho) return fail(ctx, TM_ERR_ARG, "null array");
+  if (!isfinite(alpha)) return fail(ctx, TM_ERR_ARG, "alpha not finite");
+  cudaStream_t s = S(stream);
+  const long long n = design_cells(ctx);
+  if (normalize && !(normalize == 2 && ctx->gmax_of == dJdrho)) {
+    Timed t(ctx, KIND_OTHER, s);
+    CK(cudaMemsetAsync(ctx->gmax, 0, sizeof(unsigned int), s));
+    CKL(launch_absmax(dJdrho, n, ctx->gmax, s));
+    ctx->gmax_of = dJdrho;
+  }
+  // the step runs inside the x forward pass of rho when the prepared path reaches it with
+  // one spectrum; otherwise as its own pass first
+  const int np = ctx->tz1 - ctx->tz0;
+  int nW = 0;
+  for (int c = 0; c < 3; c++) nW += ctx->tw_[c] != 0.0f;
+  const bool fused = ctx->target_kind == 0 && np >= 1 && np <= kDirectPlanesMax && nW > 0 &&
+                     (reinterpret_cast<uintptr_t>(dJdrho) & 15) == 0 &&  // copied in 16-byte pieces
+                     xfwd_fuses_step(ctx->L[0], ctx->m0_var ? SRC_RHO_M0 : SRC_RHO_POW, ctx->m0_var ? 3 : 1);
+  if (fused) {
+    ctx->pend_rho = rho;
+    ctx->pend_G = dJdrho;
+    ctx->pend_alpha = alpha;
+    ctx->pend_normalize = normalize != 0;
+  } else {
+    Timed t(ctx, KIND_OTHER, s);
+    CKL(launch_update(rho, dJdrho, n, alpha, normalize != 0, ctx->gmax, s));
+  }
+  r = tm_evaluate(ctx, rho, J_host, dJdrho, stream);
+  if (ctx->pend_rho) {
+    ctx->pend_rho = nullptr;
+    if (!r) return fail(ctx, TM_ERR_STATE, "internal: the pending step was not applied");
+  }
+  return r;
 }
 
 int tm_set_fused(tm_ctx* ctx, int on) {

@@ -34,7 +34,17 @@ struct XFwdArgs {
   float2* out;              // [slot][rows][P]
   long long out_cstride;
   const float2* tw;         // W_L^m, m < L
+  // pending projected-gradient step (RHO_POW, one slot, when upd_rho is set): rho is first
+  // replaced by min(max(rho - step upd_G, 0), 1) in place, step = upd_alpha / max|upd_G|
+  // (max read from *upd_gmax; no step when it is 0) or upd_alpha (upd_normalize == 0)
+  float* upd_rho;
+  const float* upd_G;
+  float upd_alpha;
+  int upd_normalize;
+  const unsigned int* upd_gmax;
 };
+// whether launch_xfwd applies a pending step inside the pass for this length and source
+bool xfwd_fuses_step(int L, int src, int ncomp);
 
 // Inverse x pass: half spectra -> real rows, then a sink.
 //  FIELD:     block (tile, j): H[comp[j]] = row of slot in_slot[j]

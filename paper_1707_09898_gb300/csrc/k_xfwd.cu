@@ -12,10 +12,25 @@ namespace tmk {
 
 namespace {
 
+__device__ __forceinline__ void cp16(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp4(void* sdst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Persistent: a block loops over 32-row tiles; the raw inputs of the next tile are
 // loaded into registers while the current tile is separated and stored, so global
-// latency overlaps the shared-memory work. P3: p = 3 fixed at compile time.
-template <int L, int SRC, bool P3>
+// latency overlaps the shared-memory work. P3: p = 3 fixed at compile time. UPD: the
+// pending projected-gradient step of the previous iteration (Sec. "Methodology", box
+// constraint) is applied to each rho value as it is used, and the new rho written back,
+// with the arithmetic of the stand-alone update kernel (same results bit for bit).
+template <int L, int SRC, bool P3, bool UPD>
 __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
   constexpr int S = plan_stages(L);
   using S0 = StageShape<L, 0>;
@@ -35,7 +50,22 @@ __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
   const int ntiles = (a.rows + ROWS - 1) / ROWS;
   const float* src = SRC == SRC_VECTOR ? a.vec + c * a.vec_cstride : a.rho;
   const float* m0 = withM0 ? a.M0v + c * a.M0v_cstride : nullptr;
+  static_assert(!UPD || (SRC == SRC_RHO_POW && k_per_thread<L>()), "the step is fused into the one-slot pass only");
+  // UPD: the gradient rows of the next tile are copied into shared memory (cp.async)
+  // while the current tile is separated; rows are contiguous, so a tile is one flat range
+  float* sG = reinterpret_cast<float*>(tile + L * TB);  // [ROWS][nx], nx <= L/2
   float ra[ITER][RH], rb[ITER][RH], ma[ITER][RM ? RH : 1], mb[ITER][RM ? RH : 1];
+  bool upd = false;
+  float step = 0.0f;
+  if constexpr (UPD) {
+    upd = true;
+    step = a.upd_alpha;
+    if (a.upd_normalize) {
+      const float gm = __uint_as_float(*a.upd_gmax);
+      if (!(gm > 0.0f)) upd = false;  // max|G| = 0: no step
+      step = a.upd_alpha / gm;
+    }
+  }
   auto fetch = [&](int t) {
     const int row0 = t * ROWS;
 #pragma unroll
@@ -58,9 +88,20 @@ __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
         }
       }
     }
+    if constexpr (UPD) {
+      if (upd) {  // 16-byte copies (row0 nx is a multiple of 4), the odd tail of the grid in words
+        const int nr = min(ROWS, a.rows - row0);
+        const int ne = nr * a.nx, n16 = ne >> 2;
+        const float* g = a.upd_G + (long long)row0 * a.nx;
+        for (int i = threadIdx.x; i < n16; i += kNT) cp16(sG + 4 * i, g + 4 * i);
+        for (int i = 4 * n16 + threadIdx.x; i < ne; i += kNT) cp4(sG + i, g + i);
+      }
+      cp_commit();
+    }
   };
   int t = blockIdx.x;
   if (t < ntiles) fetch(t);
+  if constexpr (UPD) cp_wait<0>();
   __syncthreads();
   for (; t < ntiles; t += gridDim.x) {
     const int row0 = t * ROWS;
@@ -72,9 +113,26 @@ __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
         cx<float> v[R];
 #pragma unroll
         for (int q = RH; q < R; q++) v[q] = zero<float>();
+        const int r = row0 + 2 * line;
+        const bool wa = r < a.rows, wb = r + 1 < a.rows;
+        const long long o = (long long)r * a.nx + j;
+        const int xn = a.nx - j;
 #pragma unroll
         for (int q = 0; q < RH; q++) {
           float va = ra[it][q], vb = rb[it][q];
+          if constexpr (UPD) {
+            if (upd && q * M < xn) {
+              const float* gl = sG + (2 * line) * a.nx + j + q * M;
+              if (wa) {
+                va = fminf(fmaxf(va - step * gl[0], 0.0f), 1.0f);
+                a.upd_rho[o + q * M] = va;
+              }
+              if (wb) {
+                vb = fminf(fmaxf(vb - step * gl[a.nx], 0.0f), 1.0f);
+                a.upd_rho[o + a.nx + q * M] = vb;
+              }
+            }
+          }
           if constexpr (SRC != SRC_VECTOR) {
             va = ipow_t<P3>(va, a.p);
             vb = ipow_t<P3>(vb, a.p);
@@ -95,16 +153,17 @@ __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
     DifRange<float, L, kNT, 1, S, true>::run(tile, tw);
     if (t + (int)gridDim.x < ntiles) fetch(t + gridDim.x);
     xseparate<L>(tile, out, row0, a.rows, a.P);
+    if constexpr (UPD) cp_wait<0>();  // the next tile's gradient rows have landed
     __syncthreads();
   }
 }
 
-template <int L, int SRC, bool P3>
+template <int L, int SRC, bool P3, bool UPD = false>
 int run_xfwd_src(const XFwdArgs& a, int ncomp, cudaStream_t s) {
-  const size_t sm = xsmem<L>();
+  const size_t sm = xsmem<L>() + (UPD ? (size_t)ROWS * (L / 2) * sizeof(float) : 0);
   static bool init = false;
   if (!init) {
-    if (cudaFuncSetAttribute(k_xfwd<L, SRC, P3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+    if (cudaFuncSetAttribute(k_xfwd<L, SRC, P3, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
         cudaSuccess)
       return -1;
     init = true;
@@ -120,24 +179,35 @@ int run_xfwd_src(const XFwdArgs& a, int ncomp, cudaStream_t s) {
   }
   const int per_comp = (2 * nsm + ncomp - 1) / ncomp;  // two resident blocks per SM in total
   const int blocks = tiles < per_comp ? tiles : per_comp;
-  k_xfwd<L, SRC, P3><<<dim3(blocks, ncomp), kNT, sm, s>>>(a);
+  k_xfwd<L, SRC, P3, UPD><<<dim3(blocks, ncomp), kNT, sm, s>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 template <int L, int SRC>
 int run_xfwd_pow(const XFwdArgs& a, int ncomp, cudaStream_t s) {
   if constexpr (k_per_thread<L>()) {
+    if constexpr (SRC == SRC_RHO_POW) {
+      if (a.upd_rho) {
+        if (ncomp != 1) return -1;
+        return a.p == 3.0f ? run_xfwd_src<L, SRC, true, true>(a, ncomp, s)
+                           : run_xfwd_src<L, SRC, false, true>(a, ncomp, s);
+      }
+    }
     if (a.p == 3.0f) return run_xfwd_src<L, SRC, true>(a, ncomp, s);
   }
+  if (a.upd_rho) return -1;  // no fused step for this length or source
   return run_xfwd_src<L, SRC, false>(a, ncomp, s);
 }
 template <int L>
 int run_xfwd(const XFwdArgs& a, int ncomp, cudaStream_t s) {
   if (a.src == SRC_RHO_POW) return run_xfwd_pow<L, SRC_RHO_POW>(a, ncomp, s);
   if (a.src == SRC_RHO_M0) return run_xfwd_pow<L, SRC_RHO_M0>(a, ncomp, s);
+  if (a.upd_rho) return -1;
   return run_xfwd_src<L, SRC_VECTOR, false>(a, ncomp, s);
 }
 
 }  // namespace
+
+bool xfwd_fuses_step(int L, int src, int ncomp) { return L == 2 * kNT && src == SRC_RHO_POW && ncomp == 1; }
 
 int launch_xfwd(int L, const XFwdArgs& a, int ncomp, cudaStream_t s) {
   switch (L) {

@@ -174,6 +174,22 @@ class Magnet:
         self._ck(self.L.tm_optimize_step(self.h, _ptr(rho), _ptr(G), float(alpha), mode, _stream(self.device)))
         return rho
 
+    def evaluate_step(self, rho, G, alpha, normalize=True, reuse_max=True, sync=True):
+        """One projected-gradient iteration: optimize_step(rho, G, alpha, ...) on the
+        gradient G holds, then evaluate(rho, G) at the new rho (G overwritten), in one
+        call; for 512-point x transforms of one spectrum the step runs inside the
+        evaluation's first pass. Returns (J, G) as evaluate."""
+        for t, name in ((rho, "rho"), (G, "G")):
+            if isinstance(t, torch.Tensor) and not t.is_contiguous():
+                raise ValueError(f"{name} is updated in place and must be contiguous")
+        rho = self._dev(rho, F32, self.design_shape, "rho")
+        G = self._dev(G, F32, self.design_shape, "G")
+        mode = (2 if reuse_max else 1) if normalize else 0
+        J = ctypes.c_double(0.0)
+        self._ck(self.L.tm_evaluate_step(self.h, _ptr(rho), float(alpha), mode, ctypes.byref(J) if sync else None,
+                                         _ptr(G), _stream(self.device)))
+        return (J.value if sync else None), G
+
     # -- per-kernel event timing ---------------------------------------------
     KINDS = ("x_forward", "y_forward", "z_pass", "y_inverse", "x_inverse", "other", "yz_forward", "zy_adjoint",
              "objective")
