@@ -52,8 +52,10 @@ __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
   const float* m0 = withM0 ? a.M0v + c * a.M0v_cstride : nullptr;
   static_assert(!UPD || (SRC == SRC_RHO_POW && k_per_thread<L>()), "the step is fused into the one-slot pass only");
   // UPD: the gradient rows of the next tile are copied into shared memory (cp.async)
-  // while the current tile is separated; rows are contiguous, so a tile is one flat range
-  float* sG = reinterpret_cast<float*>(tile + L * TB);  // [ROWS][nx], nx <= L/2
+  // while the current tile is separated, at a row stride gs = 8 (mod 16) words so that
+  // the two half-warps (rows 2 l and 2 l + 2) read distinct banks
+  float* sG = reinterpret_cast<float*>(tile + L * TB);  // [ROWS][gs], nx <= L/2
+  const int gs = a.nx + ((8 - a.nx % 16) + 16) % 16;
   float ra[ITER][RH], rb[ITER][RH], ma[ITER][RM ? RH : 1], mb[ITER][RM ? RH : 1];
   bool upd = false;
   float step = 0.0f;
@@ -89,12 +91,17 @@ __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
       }
     }
     if constexpr (UPD) {
-      if (upd) {  // 16-byte copies (row0 nx is a multiple of 4), the odd tail of the grid in words
+      if (upd) {  // a warp per row: 16-byte pieces when rows start on 16 bytes, else words
         const int nr = min(ROWS, a.rows - row0);
-        const int ne = nr * a.nx, n16 = ne >> 2;
         const float* g = a.upd_G + (long long)row0 * a.nx;
-        for (int i = threadIdx.x; i < n16; i += kNT) cp16(sG + 4 * i, g + 4 * i);
-        for (int i = 4 * n16 + threadIdx.x; i < ne; i += kNT) cp4(sG + i, g + i);
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (a.nx % 4 == 0) {
+          for (int rr = w; rr < nr; rr += kNT / 32)
+            for (int c = lane; c < a.nx / 4; c += 32) cp16(sG + rr * gs + 4 * c, g + (long long)rr * a.nx + 4 * c);
+        } else {
+          for (int rr = w; rr < nr; rr += kNT / 32)
+            for (int x = lane; x < a.nx; x += 32) cp4(sG + rr * gs + x, g + (long long)rr * a.nx + x);
+        }
       }
       cp_commit();
     }
@@ -122,13 +129,13 @@ __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
           float va = ra[it][q], vb = rb[it][q];
           if constexpr (UPD) {
             if (upd && q * M < xn) {
-              const float* gl = sG + (2 * line) * a.nx + j + q * M;
+              const float* gl = sG + (2 * line) * gs + j + q * M;
               if (wa) {
                 va = fminf(fmaxf(va - step * gl[0], 0.0f), 1.0f);
                 a.upd_rho[o + q * M] = va;
               }
               if (wb) {
-                vb = fminf(fmaxf(vb - step * gl[a.nx], 0.0f), 1.0f);
+                vb = fminf(fmaxf(vb - step * gl[gs], 0.0f), 1.0f);
                 a.upd_rho[o + a.nx + q * M] = vb;
               }
             }
@@ -160,7 +167,7 @@ __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
 
 template <int L, int SRC, bool P3, bool UPD = false>
 int run_xfwd_src(const XFwdArgs& a, int ncomp, cudaStream_t s) {
-  const size_t sm = xsmem<L>() + (UPD ? (size_t)ROWS * (L / 2) * sizeof(float) : 0);
+  const size_t sm = xsmem<L>() + (UPD ? (size_t)ROWS * (L / 2 + 15) * sizeof(float) : 0);
   static bool init = false;
   if (!init) {
     if (cudaFuncSetAttribute(k_xfwd<L, SRC, P3, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=

@@ -351,6 +351,25 @@ __device__ __forceinline__ cx<float> ws_tensor_apply(const float* tlo, const flo
   return ws_apply<C>(ws_tensor<L, C>(tlo, thi, g, q, cz), v);
 }
 
+// The stage-0 twiddle of position j + q M0 (= g R1 + q' with j = q', q = g) is W^(j q),
+// applied after the first DIF stage or before the last DIT stage. The two groups share
+// that work: the stage-0 warps take q < R0/2, the last-stage warps (their second unit,
+// g >= R0/2) the rest, with the same product on the same operands as the single-stage
+// rule (apply_twiddles), so results are unchanged bit for bit.
+template <int L, bool INV>
+__device__ __forceinline__ void twiddles_lo(cx<float>* v, int j, const cx<float>* tw) {
+  constexpr int R0 = StageShape<L, 0>::R;
+  if (j == 0) return;
+#pragma unroll
+  for (int q = 1; q < R0 / 2; q++) v[q] = INV ? cmulc(v[q], tw[j * q]) : cmul(v[q], tw[j * q]);
+}
+template <int L, bool INV>
+__device__ __forceinline__ void twiddles_hi(cx<float>* v, int g, const cx<float>* tw) {
+  constexpr int R1 = StageShape<L, 1>::R;
+#pragma unroll
+  for (int q = 1; q < R1; q++) v[q] = INV ? cmulc(v[q], tw[q * g]) : cmul(v[q], tw[q * g]);
+}
+
 template <int L>
 constexpr size_t fwd_ws_smem() {
   return (size_t)(L + 2 * L * TB + (L / 2) * TB) * sizeof(float2) + (size_t)2 * (L / 2 + 1) * TB * sizeof(float);
@@ -429,7 +448,7 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a) {
         cbn = z + 1 == a.zin0 + a.nzin ? cb + 1 : cb;
         zn = z + 1 == a.zin0 + a.nzin ? a.zin0 : z + 1;
         Dft<float, R0, false>::run(v);
-        apply_twiddles<float, L, 0, false>(v, j, tw);
+        twiddles_lo<L, false>(v, j, tw);  // q >= R0/2: applied by the accumulate warps
         cx<float>* tile = tiles + (r & 1) * L * TB;
 #pragma unroll
         for (int q = 0; q < R0; q++) tile[(j + q * M0) * TB + line] = v[q];
@@ -460,6 +479,7 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a) {
           cx<float> v[R1];
 #pragma unroll
           for (int q = 0; q < R1; q++) v[q] = tile[(g * R1 + q) * TB + line];
+          if (it == 1) twiddles_hi<L, false>(v, g, tw);  // stage-0 twiddles of g >= R0/2
           Dft<float, R1, false>::run(v);
           const float* tlo = stt + g * TB + line;
           const float* thi = stt + (L - g) * TB + line;
@@ -630,6 +650,7 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a) {
 #pragma unroll
           for (int q = 0; q < R1; q++) v[it][q] = ws_apply<C>(ws_tensor<L, C>(tlo, thi, g, q, cz), v[it][q]);
           Dft<float, R1, true>::run(v[it]);
+          if (it == 1) twiddles_hi<L, true>(v[it], g, tw);  // stage-0 twiddles of g >= R0/2
 #pragma unroll
           for (int q = 0; q < R1; q++) tile[(g * R1 + q) * TB + line] = v[it][q];
         }
@@ -651,7 +672,7 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a) {
         cx<float> v[R0];
 #pragma unroll
         for (int q = 0; q < R0; q++) v[q] = tile[(j + q * M0) * TB + line];
-        apply_twiddles<float, L, 0, true>(v, j, tw);
+        twiddles_lo<L, true>(v, j, tw);  // q >= R0/2: applied by the load warps
         Dft<float, R0, true>::run(v);
         cx<float>* o = out0 + z * a.out_zstride + kx0 + line;
 #pragma unroll
