@@ -52,6 +52,8 @@ struct tm_ctx {
   unsigned int* gmax = nullptr;
   const float* gmax_of = nullptr;  // the array whose max |.| gmax holds (set by the chain-rule pass)
   // projected-gradient step that tm_evaluate_step hands to the x forward pass of rho
+  unsigned* dstat = nullptr;       // device status word of the TMA-fed kernels (bit 0: a copy wait timed out)
+  unsigned* hstat = nullptr;       // pinned host copy
   float* pend_rho = nullptr;
   const float* pend_G = nullptr;
   float pend_alpha = 0.0f;
@@ -425,6 +427,7 @@ int yz_forward(tm_ctx* ctx, const ConvSpec& cs, int zo, cudaStream_t s, bool* yi
   }
   y.seg = ctx->yzseg;
   y.cnt = ctx->yzcnt;
+  y.status = ctx->dstat;
   y.yrows = ctx->A + cs.aout[0] * ((long long)ctx->nz * ctx->ny * P) + (long long)zo * ctx->ny * P;
   Timed t(ctx, KIND_YZF, s);
   const int r = launch_yz_fwd(Ly, y, s);
@@ -467,6 +470,7 @@ int zy_adjoint(tm_ctx* ctx, const ConvSpec& cs, int zi0, int nzi, cudaStream_t s
   z.zout0 = 0;
   z.nzout = ctx->nzd;
   z.tw = ctx->tw + ctx->L[0];
+  z.status = ctx->dstat;
   Timed t(ctx, KIND_ZYA, s);
   CKL(launch_zy_adj(Ly, z, s));
   return TM_OK;
@@ -584,6 +588,9 @@ int tm_create(tm_ctx** out, int device) {
   if (e == cudaSuccess) e = cudaMemset(ctx->Jcount, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->ext, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->Jhost, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->dstat, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(ctx->dstat, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->hstat, sizeof(unsigned));
   if (e != cudaSuccess) {
     tm_destroy(ctx);
     return TM_ERR_CUDA;
@@ -598,6 +605,8 @@ void tm_destroy(tm_ctx* ctx) {
   free_grid(ctx);
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   cudaFree(ctx->Jdev);
+  cudaFree(ctx->dstat);
+  if (ctx->hstat) cudaFreeHost(ctx->hstat);
   cudaFree(ctx->gmax);
   cudaFree(ctx->Jcount);
   cudaFree(ctx->ext);
@@ -1244,8 +1253,13 @@ int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, vo
   }
   if (J_host) {
     CK(cudaMemcpyAsync(ctx->Jhost, ctx->Jdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->hstat, ctx->dstat, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     *J_host = *ctx->Jhost;
+    if (*ctx->hstat) {
+      cudaMemset(ctx->dstat, 0, sizeof(unsigned));
+      return fail(ctx, TM_ERR_CUDA, "a tensor-copy wait of the fused y/z kernels timed out; results are invalid");
+    }
   }
   return TM_OK;
 }

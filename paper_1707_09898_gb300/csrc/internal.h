@@ -148,6 +148,7 @@ struct ZYArgs {
   long long Tc, Tdz;
   int zin0, nzin, zout0, nzout;
   const float2* tw;                         // W_Ly
+  unsigned* status;                         // device word: bit 0 set when a copy wait timed out
 };
 // Forward: the design planes of A onto one plane and one output of B.
 struct YZArgs {
@@ -172,6 +173,7 @@ struct YZArgs {
   float2* seg;
   unsigned* cnt;
   float2* yrows;
+  unsigned* status;                         // device word: bit 0 set when a copy wait timed out
 };
 int launch_zy_adj(int L, const ZYArgs& a, cudaStream_t s);
 int launch_yz_fwd(int L, const YZArgs& a, cudaStream_t s);

@@ -14,6 +14,8 @@
 //             the loader of the inverse transform and writes the real-y rows.
 // Same discrete convolution as the unfused passes, without the round trip of the
 // y spectra of all design planes through HBM.
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is taken from the driver at run time)
+
 #include "fft.cuh"
 #include "internal.h"
 
@@ -211,6 +213,38 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Tensor-memory-accelerator copies (cp.async.bulk.tensor) completing on an mbarrier.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* mb, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mb)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* mb, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* mb) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(mb))
+      : "memory");
+}
+// Wait for phase `parity` of the barrier to complete: at most kSpin polls of about a
+// microsecond each; on timeout the status word is flagged and the caller goes on (its
+// results are then invalid, and the host reports the flag), so no wait can hang.
+constexpr int kSpin = 1 << 20;
+__device__ __forceinline__ void mbar_wait(unsigned long long* mb, unsigned parity, unsigned* status) {
+  unsigned done = 0;
+  for (int i = 0; i < kSpin && !done; i++) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mb)), "r"(parity), "r"(1000u)
+        : "memory");
+  }
+  if (!done && status) atomicOr(status, 1u);
+}
+
 template <int L>
 __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_staged(YZArgs a, int c) {
   constexpr int S = plan_stages(L);
@@ -370,9 +404,24 @@ __device__ __forceinline__ void twiddles_hi(cx<float>* v, int g, const cx<float>
   for (int q = 1; q < R1; q++) v[q] = INV ? cmulc(v[q], tw[q * g]) : cmul(v[q], tw[q * g]);
 }
 
+// Tensor slices: L/2 + 1 rows of TB floats, fetched as two TMA boxes of KB = L/4 + 2 rows
+// (the rows past L/2 are not used); KB is even, so both box destinations (KB TB floats
+// apart) stay on 128-byte boundaries
+template <int L>
+__host__ __device__ constexpr int slice_box_rows() {
+  return L / 4 + 2;
+}
+template <int L>
+__host__ __device__ constexpr int slice_rows() {
+  return 2 * slice_box_rows<L>();
+}
+static_assert((slice_box_rows<512>() * TB * sizeof(float)) % 128 == 0, "128-byte aligned TMA destinations");
+static_assert((512 + 2 * 512 * TB) * sizeof(float2) % 128 == 0, "128-byte aligned TMA destinations");
+// 128 bytes of slack to align the dynamic buffer for the TMA destinations; mbarriers last
 template <int L>
 constexpr size_t fwd_ws_smem() {
-  return (size_t)(L + 2 * L * TB + (L / 2) * TB) * sizeof(float2) + (size_t)2 * (L / 2 + 1) * TB * sizeof(float);
+  return 128 + (size_t)(L + 2 * L * TB) * sizeof(float2) + (size_t)2 * slice_rows<L>() * TB * sizeof(float) +
+         2 * sizeof(unsigned long long);
 }
 
 // Forward, flattened: block b transforms the (column block, design plane) items
@@ -384,65 +433,64 @@ constexpr size_t fwd_ws_smem() {
 // block order, writes the target plane's spectrum into B and runs the inverse y
 // transform of the target plane on it (rows y < ny into A), then re-arms the counter.
 template <int L, int C>
-__global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a) {
+__global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a, const __grid_constant__ CUtensorMap mslice) {
   using S0 = StageShape<L, 0>;
   using S1 = StageShape<L, 1>;
-  constexpr int R0 = S0::R, M0 = S0::M, R1 = S1::R, KY = L / 2 + 1;
-  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int R0 = S0::R, M0 = S0::M, R1 = S1::R, KS = slice_rows<L>(), KB = slice_box_rows<L>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int fin[2];
+  unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);  // TMA destinations
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
   cx<float>* tiles = tw + L;                                      // [2][L][TB]
-  cx<float>* sin = tiles + 2 * L * TB;                            // [L/2][TB] input rows
-  float* stt0 = reinterpret_cast<float*>(sin + (L / 2) * TB);     // [2][KY][TB] tensor slices
+  float* stt0 = reinterpret_cast<float*>(tiles + 2 * L * TB);     // [2][KS][TB] tensor slices
+  unsigned long long* mb = reinterpret_cast<unsigned long long*>(stt0 + 2 * KS * TB);  // slice 0, slice 1
   load_twiddles<float, NTF>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
   if (threadIdx.x < 2) fin[threadIdx.x] = -1;
+  if (threadIdx.x == 0) {
+    mbar_init(mb, 1);
+    mbar_init(mb + 1, 1);
+    mbar_init_fence();
+  }
   const long long T = (long long)(a.P / TB) * a.nzin;
   const int i0 = (int)(T * blockIdx.x / gridDim.x), i1 = (int)(T * (blockIdx.x + 1) / gridDim.x);
   const int n = i1 - i0;
   const int cb0 = i0 / a.nzin;  // column block of segment 0
   __syncthreads();
   if (threadIdx.x < kNT) {
-    // transform warps: stage 0 of item i0 + r in round r; copies a round ahead
+    // transform warps: stage 0 of item i0 + r in round r, its 16 input values per thread
+    // loaded into registers a round ahead; thread 0 issues the TMA copy of the item's
+    // tensor slice, which the accumulate warps use in the next round
     const int t = threadIdx.x;
-    const cx<float>* in0 = reinterpret_cast<const cx<float>*>(a.in) + a.in_slot[0] * a.in_cstride;
-    const float* tc = a.Tz + C * a.Tc;
-    auto issue_rows = [&](int cb, int z) {  // 16-byte copies: 8 per input row
+    const int line = t % TB, j = t / TB;
+    const cx<float>* in0 =
+        reinterpret_cast<const cx<float>*>(a.in) + a.in_slot[0] * a.in_cstride + (long long)j * a.P + line;
+    cx<float> pre[R0 / 2];  // rows j + q M0 (q < R0/2; n_in <= L/2) of the next item
+    auto fetch = [&](int cb, int z) {
       const cx<float>* src = in0 + z * a.in_zstride + cb * TB;
-      for (int q = t; q < a.n_in * 8; q += kNT) {
-        const int row = q >> 3, part = q & 7;
-        cp16(sin + row * TB + part * 2, src + (long long)row * a.P + part * 2);
-      }
+#pragma unroll
+      for (int q = 0; q < R0 / 2; q++) pre[q] = j + q * M0 < a.n_in ? src[(long long)q * M0 * a.P] : zero<float>();
     };
-    auto issue_slice = [&](int cb, int z, int buf) {  // 4 per tensor row
+    auto issue_slice = [&](int cb, int z, int buf) {
       const int dz = a.zout - z, adz = dz < 0 ? -dz : dz;
-      const float* tsrc = tc + adz * a.Tdz + cb * TB;
-      float* stt = stt0 + buf * KY * TB;
-      for (int q = t; q < KY * 4; q += kNT) {
-        const int row = q >> 2, part = q & 3;
-        cp16(stt + row * TB + part * 4, tsrc + (long long)row * a.P + part * 4);
-      }
+      const int y = (int)((C * a.Tc + adz * a.Tdz) / a.P);
+      float* stt = stt0 + buf * KS * TB;
+      mbar_expect_tx(mb + buf, 2 * KB * TB * (int)sizeof(float));
+      tma_load_2d(stt, &mslice, cb * TB, y, mb + buf);
+      tma_load_2d(stt + KB * TB, &mslice, cb * TB, y + KB, mb + buf);
     };
     // (column block, plane) of the current item and of the next one
     int cb = cb0, z = a.zin0 + (i0 - cb0 * a.nzin);
     int cbn = z + 1 == a.zin0 + a.nzin ? cb + 1 : cb, zn = z + 1 == a.zin0 + a.nzin ? a.zin0 : z + 1;
-    if (n > 0) issue_rows(cb, z);
-    cp_commit();
-    const int line = t % TB, j = t / TB;
+    if (n > 0) fetch(cb, z);
     for (int r = 0; r <= n; r++) {
       if (r < n) {
-        cp_wait<0>();
-        bar_named(kBarGroup, kNT);  // the item's rows are in shared memory for every transform thread
         cx<float> v[R0];
 #pragma unroll
-        for (int q = 0; q < R0; q++) {
-          const int pos = j + q * M0;
-          v[q] = (q < R0 / 2 && pos < a.n_in) ? sin[pos * TB + line] : zero<float>();  // n_in <= L/2
-        }
-        bar_named(kBarGroup, kNT);  // every transform thread is done with the rows
-        issue_slice(cb, z, r & 1);
-        cp_commit();
-        if (r + 1 < n) issue_rows(cbn, zn);
-        cp_commit();
+        for (int q = 0; q < R0 / 2; q++) v[q] = pre[q];
+#pragma unroll
+        for (int q = R0 / 2; q < R0; q++) v[q] = zero<float>();
+        if (r + 1 < n) fetch(cbn, zn);
+        if (t == 0) issue_slice(cb, z, r & 1);
         cb = cbn;
         z = zn;
         cbn = z + 1 == a.zin0 + a.nzin ? cb + 1 : cb;
@@ -452,7 +500,6 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a) {
         cx<float>* tile = tiles + (r & 1) * L * TB;
 #pragma unroll
         for (int q = 0; q < R0; q++) tile[(j + q * M0) * TB + line] = v[q];
-        cp_wait<1>();  // this thread's copies of the slice have landed (the next rows may not)
       }
       bar_named(kBarAll, NTF);
     }
@@ -472,7 +519,8 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a) {
         const int dz = a.zout - z;
         const float cz = (C >= 4 && dz < 0) ? -coef : coef;
         const cx<float>* tile = tiles + ((r - 1) & 1) * L * TB;
-        const float* stt = stt0 + ((r - 1) & 1) * KY * TB;
+        const float* stt = stt0 + ((r - 1) & 1) * KS * TB;
+        mbar_wait(mb + ((r - 1) & 1), ((r - 1) >> 1) & 1, a.status);  // its tensor slice
 #pragma unroll
         for (int it = 0; it < 2; it++) {
           const int u = it * kNT + t, line = u % TB, g = u / TB;
@@ -581,20 +629,23 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a) {
 
 template <int L>
 constexpr size_t adj_ws_smem() {
-  return (size_t)(L + 2 * L * TB) * sizeof(float2) + (size_t)2 * (L / 2 + 1) * TB * sizeof(float);
+  return 128 + (size_t)(L + 2 * L * TB) * sizeof(float2) + (size_t)2 * slice_rows<L>() * TB * sizeof(float) +
+         2 * sizeof(unsigned long long);
 }
 
 // Adjoint: the (column block, design plane) items [T b / B, T (b + 1) / B) of block b,
 // T = (P / TB) nzout; one item per round and group.
 template <int L, int C>
-__global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a) {
+__global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a, const __grid_constant__ CUtensorMap mslice) {
   using S0 = StageShape<L, 0>;
   using S1 = StageShape<L, 1>;
-  constexpr int R0 = S0::R, M0 = S0::M, R1 = S1::R, KY = L / 2 + 1;
-  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int R0 = S0::R, M0 = S0::M, R1 = S1::R, KS = slice_rows<L>(), KB = slice_box_rows<L>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);  // TMA destinations
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
   cx<float>* tiles = tw + L;                                      // [2][L][TB]
-  float* stt0 = reinterpret_cast<float*>(tiles + 2 * L * TB);     // [2][KY][TB] tensor slices
+  float* stt0 = reinterpret_cast<float*>(tiles + 2 * L * TB);     // [2][KS][TB] tensor slices
+  unsigned long long* mb = reinterpret_cast<unsigned long long*>(stt0 + 2 * KS * TB);  // slice 0, slice 1
   load_twiddles<float, NTF>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
   const long long T = (long long)(a.P / TB) * a.nzout;
   const int i0 = (int)(T * blockIdx.x / gridDim.x), i1 = (int)(T * (blockIdx.x + 1) / gridDim.x);
@@ -604,21 +655,22 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a) {
     kx0 = cb * TB;
     z = a.zout0 + (i - cb * a.nzout);
   };
-  const float* tc = a.Tz + C * a.Tc;
-  auto issue_slice = [&](int i, int buf, int t) {  // 16-byte copies, 4 per tensor row
+  auto issue_slice = [&](int i, int buf) {  // one thread: two TMA boxes into slice buffer buf
     int kx0, z;
     item(i, kx0, z);
     const int dz = z - a.zin0, adz = dz < 0 ? -dz : dz;
-    const float* tsrc = tc + adz * a.Tdz + kx0;
-    float* stt = stt0 + buf * KY * TB;
-    for (int q = t; q < KY * 4; q += kNT) {
-      const int row = q >> 2, part = q & 3;
-      cp16(stt + row * TB + part * 4, tsrc + (long long)row * a.P + part * 4);
-    }
+    const int y = (int)((C * a.Tc + adz * a.Tdz) / a.P);
+    float* stt = stt0 + buf * KS * TB;
+    mbar_expect_tx(mb + buf, 2 * KB * TB * (int)sizeof(float));
+    tma_load_2d(stt, &mslice, kx0, y, mb + buf);
+    tma_load_2d(stt + KB * TB, &mslice, kx0, y + KB, mb + buf);
   };
-  if (threadIdx.x >= kNT && n > 0) issue_slice(i0, 0, threadIdx.x - kNT);
-  cp_commit();
-  cp_wait<0>();
+  if (threadIdx.x == 0) {
+    mbar_init(mb, 1);
+    mbar_init(mb + 1, 1);
+    mbar_init_fence();
+    if (n > 0) issue_slice(i0, 0);
+  }
   __syncthreads();
   if (threadIdx.x < kNT) {
     // load warps: s times the source, first inverse stage, into tile r % 2 in round r
@@ -626,33 +678,41 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a) {
     const float coef = a.coef[0][0][C];
     const cx<float>* src = reinterpret_cast<const cx<float>*>(a.src) + a.in_slot[0] * a.src_cstride +
                            a.zin0 * a.src_zstride;
+    // the source spectrum does not depend on the design plane: a thread keeps its 2 R1
+    // values (positions g R1 + q of its two units) for as long as the column block stays
+    cx<float> sv[2][R1];
+    int kx_held = -1;
     for (int r = 0; r <= n; r++) {
       if (r < n) {
         int kx0, z;
         item(i0 + r, kx0, z);
+        if (kx0 != kx_held) {
+#pragma unroll
+          for (int it = 0; it < 2; it++) {
+            const int u = it * kNT + t, line = u % TB, g = u / TB;
+            const cx<float>* s = src + (long long)(g * R1) * a.P + kx0 + line;
+#pragma unroll
+            for (int q = 0; q < R1; q++) sv[it][q] = s[q * a.P];
+          }
+          kx_held = kx0;
+        }
         const int dz = z - a.zin0;
         const float cz = (C >= 4 && dz < 0) ? -coef : coef;
-        const float* stt = stt0 + (r & 1) * KY * TB;
+        const float* stt = stt0 + (r & 1) * KS * TB;
         cx<float>* tile = tiles + (r & 1) * L * TB;
-        cx<float> v[2][R1];
-#pragma unroll
-        for (int it = 0; it < 2; it++) {
-          const int u = it * kNT + t, line = u % TB, g = u / TB;
-          const cx<float>* s = src + (long long)(g * R1) * a.P + kx0 + line;  // positions g R1 + q
-#pragma unroll
-          for (int q = 0; q < R1; q++) v[it][q] = s[q * a.P];
-        }
+        mbar_wait(mb + (r & 1), (r >> 1) & 1, a.status);  // this item's tensor slice
 #pragma unroll
         for (int it = 0; it < 2; it++) {
           const int u = it * kNT + t, line = u % TB, g = u / TB;
           const float* tlo = stt + g * TB + line;
           const float* thi = stt + (L - g) * TB + line;
+          cx<float> v[R1];
 #pragma unroll
-          for (int q = 0; q < R1; q++) v[it][q] = ws_apply<C>(ws_tensor<L, C>(tlo, thi, g, q, cz), v[it][q]);
-          Dft<float, R1, true>::run(v[it]);
-          if (it == 1) twiddles_hi<L, true>(v[it], g, tw);  // stage-0 twiddles of g >= R0/2
+          for (int q = 0; q < R1; q++) v[q] = ws_apply<C>(ws_tensor<L, C>(tlo, thi, g, q, cz), sv[it][q]);
+          Dft<float, R1, true>::run(v);
+          if (it == 1) twiddles_hi<L, true>(v, g, tw);  // stage-0 twiddles of g >= R0/2
 #pragma unroll
-          for (int q = 0; q < R1; q++) tile[(g * R1 + q) * TB + line] = v[it][q];
+          for (int q = 0; q < R1; q++) tile[(g * R1 + q) * TB + line] = v[q];
         }
       }
       bar_named(kBarAll, NTF);
@@ -663,8 +723,7 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a) {
     const int line = t % TB, j = t / TB;
     cx<float>* out0 = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[0] * a.out_cstride;
     for (int r = 0; r <= n; r++) {
-      if (r + 1 < n) issue_slice(i0 + r + 1, (r + 1) & 1, t);
-      cp_commit();
+      if (t == 0 && r + 1 < n) issue_slice(i0 + r + 1, (r + 1) & 1);
       if (r >= 1) {
         int kx0, z;
         item(i0 + r - 1, kx0, z);
@@ -681,7 +740,6 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a) {
           if (y < a.n_out) o[(long long)y * a.P] = v[q];
         }
       }
-      cp_wait<0>();  // the next item's slice has landed
       bar_named(kBarAll, NTF);
     }
   }
@@ -723,6 +781,44 @@ int launch_adj(const ZYArgs& a, int c, cudaStream_t s) {
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
+// cuTensorMapEncodeTiled from the driver (no link-time dependency on libcuda)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return fn;
+}
+// 2-D map over a row-major array of `outer` rows of `inner` elements, row pitch `pitch`
+// bytes, boxes of box_inner x box_outer elements; false if it cannot be encoded
+bool map_2d(CUtensorMap* m, CUtensorMapDataType type, const void* base, unsigned long long inner,
+            unsigned long long outer, unsigned long long pitch, unsigned box_inner, unsigned box_outer) {
+  EncodeTiledFn fn = encoder();
+  if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (pitch & 15)) return false;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {pitch};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, type, 2, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+// the tensor slices: Tz [6][nz][Ly/2 + 1][P] floats as rows of P
+bool slice_map(CUtensorMap* m, const float* Tz, long long Tc, int P, int box_rows) {
+  return map_2d(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Tz, (unsigned long long)P, 6ULL * (unsigned long long)(Tc / P),
+                (unsigned long long)P * sizeof(float), TB, box_rows);
+}
+
 int sm_count() {
   static int nsm = 0;
   if (!nsm) {
@@ -735,7 +831,7 @@ int sm_count() {
 }
 
 template <int L, int C>
-int launch_adj_ws(const ZYArgs& a, cudaStream_t s) {
+int launch_adj_ws(const ZYArgs& a, const CUtensorMap& mslice, cudaStream_t s) {
   constexpr size_t sm = adj_ws_smem<L>();
   static bool init = false;
   if (!init) {
@@ -746,7 +842,7 @@ int launch_adj_ws(const ZYArgs& a, cudaStream_t s) {
   }
   const long long items = (long long)(a.P / TB) * a.nzout;
   const int blocks = (int)(items < sm_count() ? items : sm_count());  // one resident block per SM
-  k_zy_adj_ws<L, C><<<blocks, NTF, sm, s>>>(a);
+  k_zy_adj_ws<L, C><<<blocks, NTF, sm, s>>>(a, mslice);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -756,13 +852,16 @@ int run_zy_adj(const ZYArgs& a, cudaStream_t s) {
   const int c = single_component(a.need[0][0]);
   if (a.nin == 1 && a.nout == 1 && a.nzin == 1 && c >= 0) {
     if constexpr (yz_ws_plan<L>()) {
-      switch (c) {
-        case 0: return launch_adj_ws<L, 0>(a, s);
-        case 1: return launch_adj_ws<L, 1>(a, s);
-        case 2: return launch_adj_ws<L, 2>(a, s);
-        case 3: return launch_adj_ws<L, 3>(a, s);
-        case 4: return launch_adj_ws<L, 4>(a, s);
-        default: return launch_adj_ws<L, 5>(a, s);
+      CUtensorMap ms;
+      if (slice_map(&ms, a.Tz, a.Tc, a.P, slice_box_rows<L>())) {
+        switch (c) {
+          case 0: return launch_adj_ws<L, 0>(a, ms, s);
+          case 1: return launch_adj_ws<L, 1>(a, ms, s);
+          case 2: return launch_adj_ws<L, 2>(a, ms, s);
+          case 3: return launch_adj_ws<L, 3>(a, ms, s);
+          case 4: return launch_adj_ws<L, 4>(a, ms, s);
+          default: return launch_adj_ws<L, 5>(a, ms, s);
+        }
       }
     }
     return launch_adj<L, true>(a, c, s);
@@ -804,7 +903,7 @@ int launch_fwd(const YZArgs& a, int c, int nch, cudaStream_t s) {
 }
 
 template <int L, int C>
-int launch_fwd_ws(const YZArgs& a, int nch, cudaStream_t s) {
+int launch_fwd_ws(const YZArgs& a, const CUtensorMap& mslice, cudaStream_t s) {
   constexpr size_t sm = fwd_ws_smem<L>();
   static bool init = false;
   if (!init) {
@@ -815,7 +914,7 @@ int launch_fwd_ws(const YZArgs& a, int nch, cudaStream_t s) {
   }
   const long long items = (long long)(a.P / TB) * a.nzin;
   const int blocks = (int)(items < sm_count() ? items : sm_count());  // one resident block per SM
-  k_yz_fwd_ws<L, C><<<blocks, NTF, sm, s>>>(a);
+  k_yz_fwd_ws<L, C><<<blocks, NTF, sm, s>>>(a, mslice);
   return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;  // 1: the target plane's y inverse is done
 }
 
@@ -823,14 +922,16 @@ template <int L>
 int launch_fwd_single(const YZArgs& a, int c, int nch, cudaStream_t s) {
   if constexpr (yz_ws_plan<L>()) {
     // needs the segment buffers, and at most two column blocks per block (blocks >= P / TB)
-    if (a.n_in <= L / 2 && a.seg && a.cnt && a.yrows && a.P / TB <= sm_count()) {
+    CUtensorMap ms;
+    if (a.n_in <= L / 2 && a.seg && a.cnt && a.yrows && a.P / TB <= sm_count() &&
+        slice_map(&ms, a.Tz, a.Tc, a.P, slice_box_rows<L>())) {
       switch (c) {
-        case 0: return launch_fwd_ws<L, 0>(a, nch, s);
-        case 1: return launch_fwd_ws<L, 1>(a, nch, s);
-        case 2: return launch_fwd_ws<L, 2>(a, nch, s);
-        case 3: return launch_fwd_ws<L, 3>(a, nch, s);
-        case 4: return launch_fwd_ws<L, 4>(a, nch, s);
-        default: return launch_fwd_ws<L, 5>(a, nch, s);
+        case 0: return launch_fwd_ws<L, 0>(a, ms, s);
+        case 1: return launch_fwd_ws<L, 1>(a, ms, s);
+        case 2: return launch_fwd_ws<L, 2>(a, ms, s);
+        case 3: return launch_fwd_ws<L, 3>(a, ms, s);
+        case 4: return launch_fwd_ws<L, 4>(a, ms, s);
+        default: return launch_fwd_ws<L, 5>(a, ms, s);
       }
     }
   }
