@@ -54,6 +54,8 @@ struct tm_ctx {
   // projected-gradient step that tm_evaluate_step hands to the x forward pass of rho
   unsigned* dstat = nullptr;       // device status word of the TMA-fed kernels (bit 0: a copy wait timed out)
   unsigned* hstat = nullptr;       // pinned host copy
+  bool pdl = true;                 // launch the passes with programmatic dependent launch
+  bool gmax_zeroed = false;        // the fused adjoint cleared gmax for the chain-rule pass
   float* pend_rho = nullptr;
   const float* pend_G = nullptr;
   float pend_alpha = 0.0f;
@@ -336,6 +338,7 @@ int ypass(tm_ctx* ctx, bool inv, int n, const int* aslot, const int* bslot, int 
   }
   y.z0 = z0;
   y.tw = ctx->tw + Lx;
+  y.pdl = ctx->pdl;
   Timed t(ctx, inv ? KIND_YINV : KIND_YFWD, s);
   CKL(inv ? launch_yinv(Ly, y, n, s) : launch_yfwd(Ly, y, n, s));
   return TM_OK;
@@ -429,6 +432,7 @@ int yz_forward(tm_ctx* ctx, const ConvSpec& cs, int zo, cudaStream_t s, bool* yi
   y.cnt = ctx->yzcnt;
   y.status = ctx->dstat;
   y.yrows = ctx->A + cs.aout[0] * ((long long)ctx->nz * ctx->ny * P) + (long long)zo * ctx->ny * P;
+  y.pdl = ctx->pdl;
   Timed t(ctx, KIND_YZF, s);
   const int r = launch_yz_fwd(Ly, y, s);
   if (r < 0) CKL(r);
@@ -471,8 +475,12 @@ int zy_adjoint(tm_ctx* ctx, const ConvSpec& cs, int zi0, int nzi, cudaStream_t s
   z.nzout = ctx->nzd;
   z.tw = ctx->tw + ctx->L[0];
   z.status = ctx->dstat;
+  z.zero_word = ctx->gmax;  // cleared for the chain-rule pass that follows (saves a memset between kernels)
+  z.pdl = ctx->pdl;
   Timed t(ctx, KIND_ZYA, s);
-  CKL(launch_zy_adj(Ly, z, s));
+  const int r = launch_zy_adj(Ly, z, s);
+  if (r < 0) CKL(r);
+  ctx->gmax_zeroed = r == 1;
   return TM_OK;
 }
 
@@ -496,6 +504,7 @@ int xfwd_rho(tm_ctx* ctx, const float* rho, cudaStream_t s, int* nslots) {
   x.out_cstride = (long long)ctx->nz * ctx->ny * ctx->P;
   x.tw = ctx->tw;
   *nslots = ctx->m0_var ? 3 : 1;
+  x.pdl = ctx->pdl;
   if (ctx->pend_rho && ctx->pend_rho == rho && xfwd_fuses_step(ctx->L[0], x.src, *nslots)) {
     x.upd_rho = ctx->pend_rho;
     x.upd_G = ctx->pend_G;
@@ -512,8 +521,10 @@ int xfwd_rho(tm_ctx* ctx, const float* rho, cudaStream_t s, int* nslots) {
 // inverse x pass on design rows with the chain rule into G (+ max |G|); ncomp slots:
 // 1 = already contracted with the constant M0; 3 = components x, y, z (varying M0)
 int xinv_chain(tm_ctx* ctx, const float* rho, float* G, int ncomp, const int* slots, cudaStream_t s) {
-  CK(cudaMemsetAsync(ctx->gmax, 0, sizeof(unsigned int), s));
+  if (!ctx->gmax_zeroed) CK(cudaMemsetAsync(ctx->gmax, 0, sizeof(unsigned int), s));
+  ctx->gmax_zeroed = false;
   XInvArgs x{};
+  x.pdl = ctx->pdl;
   x.rows = ctx->nzd * ctx->ny;
   x.nx = ctx->nx;
   x.P = ctx->P;
@@ -1244,6 +1255,7 @@ int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, vo
       x.Jout = ctx->Jdev;
       x.ny = ctx->ny;
       x.tw = ctx->tw;
+      x.pdl = ctx->pdl;
       {  // few target rows: the latency-bound compact kernel (one warp group per row pair)
         Timed t(ctx, KIND_OBJ, s);
         CKL(launch_xobj(ctx->L[0], x, s));

@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(kNT, 2) k_xfwd(XFwdArgs a) {
   cx<float>* tile = tw0 + L;
   load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
   load_twiddles0<L>(tw0, reinterpret_cast<const cx<float>*>(a.tw));
+  pdl_wait();  // rho, the gradient, max|G| and the spectra buffer belong to earlier kernels
   const int c = a.comp[blockIdx.y];
   cx<float>* out = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[blockIdx.y] * a.out_cstride;
   const int ntiles = (a.rows + ROWS - 1) / ROWS;
@@ -186,8 +187,8 @@ int run_xfwd_src(const XFwdArgs& a, int ncomp, cudaStream_t s) {
   }
   const int per_comp = (2 * nsm + ncomp - 1) / ncomp;  // two resident blocks per SM in total
   const int blocks = tiles < per_comp ? tiles : per_comp;
-  k_xfwd<L, SRC, P3, UPD><<<dim3(blocks, ncomp), kNT, sm, s>>>(a);
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+  return launch_k(k_xfwd<L, SRC, P3, UPD>, dim3(blocks, ncomp), dim3(kNT), sm, s, a.pdl != 0, a) == cudaSuccess ? 0
+                                                                                                       : -1;
 }
 template <int L, int SRC>
 int run_xfwd_pow(const XFwdArgs& a, int ncomp, cudaStream_t s) {

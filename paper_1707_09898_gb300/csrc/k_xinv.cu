@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
   __shared__ double red[kNT / 32];
   load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
   load_twiddles0<L>(tw0, reinterpret_cast<const cx<float>*>(a.tw));
+  pdl_wait();  // the spectra, rho and the outputs belong to earlier kernels
   const int row0 = a.row_base + blockIdx.x * ROWS;
   const cx<float>* in0 = reinterpret_cast<const cx<float>*>(a.in);
 
@@ -268,8 +269,8 @@ int run_xinv_sink(const XInvArgs& a, cudaStream_t s) {
   const int blocks = (a.rows - a.row_base + ROWS - 1) / ROWS;
   if (blocks <= 0 || a.ncomp == 0) return 0;
   const int gy = SINK == SINK_CHAIN ? 1 : a.ncomp;
-  k_xinv<L, SINK, MINB, P3><<<dim3(blocks, gy), kNT, sm, s>>>(a);
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+  return launch_k(k_xinv<L, SINK, MINB, P3>, dim3(blocks, gy), dim3(kNT), sm, s, a.pdl != 0, a) == cudaSuccess ? 0
+                                                                                                        : -1;
 }
 template <int L>
 int run_xinv(const XInvArgs& a, cudaStream_t s) {

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(OW * 32) k_xobj(XInvArgs a, int L) {
   cx<float>* b1 = b0 + L;
   for (int i = threadIdx.x; i < L; i += OW * 32) tw[i] = reinterpret_cast<const cx<float>*>(a.tw)[i];
   if (gt == 0) any_mask[g] = 0;
+  pdl_wait();  // the spectra, J partials and outputs belong to earlier kernels
   __syncthreads();
   const int jc = blockIdx.y, c = a.comp[jc];
   const float wc = a.w[c];
@@ -279,6 +280,7 @@ __global__ void __launch_bounds__(NT8) k_xobj512(XInvArgs a) {
   cx<float>* b1 = b0 + L;
   for (int i = threadIdx.x; i < L; i += NT8) tw[i] = reinterpret_cast<const cx<float>*>(a.tw)[i];
   if (gt == 0) any_mask[g] = 0;
+  pdl_wait();  // the spectra, J partials and outputs belong to earlier kernels
   __syncthreads();
   const int jc = blockIdx.y, c = a.comp[jc];
   const float wc = a.w[c];
@@ -408,8 +410,7 @@ int launch_xobj(int L, const XInvArgs& a, cudaStream_t s) {
     const int blocks = (rows + 2 * NG8 - 1) / (2 * NG8);
     if (blocks <= 0 || a.ncomp == 0) return 0;
     if (!a.Jcount || !a.adj_out) return -1;
-    k_xobj512<<<dim3(blocks, a.ncomp), NT8, sm8, s>>>(a);
-    return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+    return launch_k(k_xobj512, dim3(blocks, a.ncomp), dim3(NT8), sm8, s, a.pdl != 0, a) == cudaSuccess ? 0 : -1;
   }
   const size_t sm = xobj_smem(L);
   static bool init = false;
@@ -422,8 +423,7 @@ int launch_xobj(int L, const XInvArgs& a, cudaStream_t s) {
   const int rows = a.rows - a.row_base;
   const int blocks = (rows + 2 * NG - 1) / (2 * NG);
   if (blocks <= 0 || a.ncomp == 0 || !a.Jcount || !a.adj_out) return blocks <= 0 || a.ncomp == 0 ? 0 : -1;
-  k_xobj<<<dim3(blocks, a.ncomp), OW * 32, sm, s>>>(a, L);
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+  return launch_k(k_xobj, dim3(blocks, a.ncomp), dim3(OW * 32), sm, s, a.pdl != 0, a, L) == cudaSuccess ? 0 : -1;
 }
 
 int xobj_rows_per_block() { return 2 * NG; }  // 2 NG8 = 8 for L = 512: a multiple of this

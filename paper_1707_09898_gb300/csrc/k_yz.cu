@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(kNT, 3) k_ypass(YArgs a) {
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
   cx<float>* tile = tw + L;
   load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
+  pdl_wait();  // the input planes, the plane extent and the outputs belong to earlier kernels
   const int chunk = blockIdx.x;
   int z = a.z0 + blockIdx.y;
   if (a.ext) {
@@ -342,8 +343,7 @@ int run_y(const YArgs& a, int ncomp, cudaStream_t s) {
   }
   if (a.nplanes == 0 || ncomp == 0) return 0;
   dim3 grid(a.P / TB, a.nplanes, ncomp);
-  k_ypass<L, INV><<<grid, kNT, sm, s>>>(a);
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+  return launch_k(k_ypass<L, INV>, grid, dim3(kNT), sm, s, a.pdl != 0, a) == cudaSuccess ? 0 : -1;
 }
 
 template <int L>

@@ -451,6 +451,7 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a, const __grid_con
     mbar_init(mb + 1, 1);
     mbar_init_fence();
   }
+  pdl_wait();  // the x spectra, the counters and the outputs belong to earlier kernels
   const long long T = (long long)(a.P / TB) * a.nzin;
   const int i0 = (int)(T * blockIdx.x / gridDim.x), i1 = (int)(T * (blockIdx.x + 1) / gridDim.x);
   const int n = i1 - i0;
@@ -669,8 +670,10 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a, const __grid_con
     mbar_init(mb, 1);
     mbar_init(mb + 1, 1);
     mbar_init_fence();
-    if (n > 0) issue_slice(i0, 0);
+    if (n > 0) issue_slice(i0, 0);  // the tensor is constant: no need to wait for earlier kernels
   }
+  pdl_wait();  // the source plane and the outputs belong to earlier kernels
+  if (a.zero_word && blockIdx.x == 0 && threadIdx.x == 0) *a.zero_word = 0u;
   __syncthreads();
   if (threadIdx.x < kNT) {
     // load warps: s times the source, first inverse stage, into tile r % 2 in round r
@@ -842,8 +845,9 @@ int launch_adj_ws(const ZYArgs& a, const CUtensorMap& mslice, cudaStream_t s) {
   }
   const long long items = (long long)(a.P / TB) * a.nzout;
   const int blocks = (int)(items < sm_count() ? items : sm_count());  // one resident block per SM
-  k_zy_adj_ws<L, C><<<blocks, NTF, sm, s>>>(a, mslice);
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+  return launch_k(k_zy_adj_ws<L, C>, dim3(blocks), dim3(NTF), sm, s, a.pdl != 0, a, mslice) == cudaSuccess
+             ? (a.zero_word ? 1 : 0)  // 1: *zero_word is cleared
+             : -1;
 }
 
 template <int L>
@@ -914,8 +918,9 @@ int launch_fwd_ws(const YZArgs& a, const CUtensorMap& mslice, cudaStream_t s) {
   }
   const long long items = (long long)(a.P / TB) * a.nzin;
   const int blocks = (int)(items < sm_count() ? items : sm_count());  // one resident block per SM
-  k_yz_fwd_ws<L, C><<<blocks, NTF, sm, s>>>(a, mslice);
-  return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;  // 1: the target plane's y inverse is done
+  return launch_k(k_yz_fwd_ws<L, C>, dim3(blocks), dim3(NTF), sm, s, a.pdl != 0, a, mslice) == cudaSuccess
+             ? 1  // 1: the target plane's y inverse is done
+             : -1;
 }
 
 template <int L>
