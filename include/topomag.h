@@ -157,6 +157,15 @@ int tm_set_stencil_objective(tm_ctx* ctx, long long K, const long long* row_ptr,
 int tm_get_objective(tm_ctx* ctx, double* J_host, void* stream);
 
 /*
+ * Asynchronous form: enqueue on `stream` a copy of that J (one double) to dst, pinned
+ * host or device memory (any address cudaMemcpyAsync accepts with cudaMemcpyDefault).
+ * Returns at once; dst holds J once the stream reaches the copy (record an event after
+ * the call and wait for it). Lets a loop read each iteration's J without stalling the
+ * GPU: queue iteration i + 1, then wait for J(i).
+ */
+int tm_copy_objective(tm_ctx* ctx, double* dst, void* stream);
+
+/*
  * Projected-gradient step on the box 0 <= rho <= 1 (box constraint of Sec.
  * "Methodology"): rho <- clip(rho - alpha G / max|G|, 0, 1) if normalize != 0
  * (no change when max|G| = 0), else rho <- clip(rho - alpha G, 0, 1).

@@ -39,6 +39,7 @@ _SIGS = {
     "tm_objective_and_gradient": (ctypes.c_int, [vp, vp, vp, vp, c_float3, c_float3, ctypes.POINTER(ctypes.c_double),
                                                  vp, vp, vp]),
     "tm_get_objective": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), vp]),
+    "tm_copy_objective": (ctypes.c_int, [vp, vp, vp]),
     "tm_set_target": (ctypes.c_int, [vp, vp, vp, c_float3, c_float3, vp]),
     "tm_evaluate": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp]),
     "tm_set_stencil_objective": (ctypes.c_int, [vp, ctypes.c_longlong, vp, vp, vp, vp, vp, vp]),

@@ -1285,6 +1285,13 @@ int tm_get_objective(tm_ctx* ctx, double* J_host, void* stream) {
   return TM_OK;
 }
 
+int tm_copy_objective(tm_ctx* ctx, double* dst, void* stream) {
+  if (!ctx || !dst) return fail(ctx, TM_ERR_ARG, "null argument");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaMemcpyAsync(dst, ctx->Jdev, sizeof(double), cudaMemcpyDefault, S(stream)));
+  return TM_OK;
+}
+
 int tm_optimize_step(tm_ctx* ctx, float* rho, const float* dJdrho, float alpha, int normalize, void* stream) {
   if (!ctx) return TM_ERR_ARG;
   if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");

@@ -816,10 +816,29 @@ bool map_2d(CUtensorMap* m, CUtensorMapDataType type, const void* base, unsigned
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
-// the tensor slices: Tz [6][nz][Ly/2 + 1][P] floats as rows of P
+// the tensor slices: Tz [6][nz][Ly/2 + 1][P] floats as rows of P; the last map made on
+// this host thread is kept, since a context launches with the same one every time
 bool slice_map(CUtensorMap* m, const float* Tz, long long Tc, int P, int box_rows) {
-  return map_2d(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Tz, (unsigned long long)P, 6ULL * (unsigned long long)(Tc / P),
-                (unsigned long long)P * sizeof(float), TB, box_rows);
+  struct Cached {
+    const float* Tz = nullptr;
+    long long Tc = 0;
+    int P = 0, box = 0;
+    CUtensorMap map;
+  };
+  thread_local Cached c;
+  if (c.Tz == Tz && c.Tc == Tc && c.P == P && c.box == box_rows) {
+    *m = c.map;
+    return true;
+  }
+  if (!map_2d(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Tz, (unsigned long long)P, 6ULL * (unsigned long long)(Tc / P),
+              (unsigned long long)P * sizeof(float), TB, box_rows))
+    return false;
+  c.Tz = Tz;
+  c.Tc = Tc;
+  c.P = P;
+  c.box = box_rows;
+  c.map = *m;
+  return true;
 }
 
 int sm_count() {

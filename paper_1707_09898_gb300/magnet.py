@@ -167,6 +167,15 @@ class Magnet:
         self._ck(self.L.tm_get_objective(self.h, ctypes.byref(J), _stream(self.device)))
         return J.value
 
+    def copy_objective(self, out):
+        """Enqueue a copy of the last J into out (a float64 tensor element, pinned host or
+        device memory) on the current stream; returns at once (wait on an event)."""
+        if not isinstance(out, torch.Tensor) or out.dtype != torch.float64 or out.numel() != 1:
+            raise TypeError("out must be a one-element float64 tensor")
+        if out.device.type == "cpu" and not out.is_pinned():
+            raise ValueError("a host destination must be pinned memory")
+        self._ck(self.L.tm_copy_objective(self.h, _ptr(out), _stream(self.device)))
+
     def optimize_step(self, rho, G, alpha, normalize=True, reuse_max=False):
         """rho <- clip(rho - alpha G / max|G|, 0, 1) (normalize) or clip(rho - alpha G, 0, 1).
         reuse_max: take max|G| from the evaluation that wrote G (G unchanged since)."""
