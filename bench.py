@@ -36,18 +36,18 @@ METRIC = "adjoint-gradient evals/s at 256^3 cells, FP32 vs FP64 oracle; % of HBM
 UNIT = "evals/s"
 
 # DRAM bytes (read + write) per launch of the main kernel kinds of the prepared 256^3 step,
-# each from one ncu capture (profiles/fused_yz_c4_256cube_ncu.md; the direct z sum of the
+# each from one ncu capture (profiles/traffic_c4_256cube.md; the direct z sum of the
 # separate path: profiles/zdir_c4_256cube_ncu.md, forward and adjoint launch averaged);
 # valid only while the kernel's source file is unchanged.
 MEASURED_TRAFFIC = {
-    "x_forward": {"bytes": 289.0e6, "source": "paper_1707_09898_gb300/csrc/k_xfwd.cu",  # with the fused step
-                  "source_sha1": "5541bd41889835a995e70892d0cda0365d1db444"},
-    "yz_forward": {"bytes": 222.7e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
-                   "source_sha1": "369bbcdb73f3a500e1d409dab041f6b4ad923acb"},
-    "zy_adjoint": {"bytes": 165.6e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
-                   "source_sha1": "369bbcdb73f3a500e1d409dab041f6b4ad923acb"},
-    "x_inverse": {"bytes": 254.5e6, "source": "paper_1707_09898_gb300/csrc/k_xinv.cu",
-                  "source_sha1": "cd8d1b264cefcf85f6e2b7cf4c0376b661a56014"},
+    "x_forward": {"bytes": 288.8e6, "source": "paper_1707_09898_gb300/csrc/k_xfwd.cu",  # with the fused step
+                  "source_sha1": "f565c14a45fdfca0a5b06e81872532755122bc43"},
+    "yz_forward": {"bytes": 219.8e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
+                   "source_sha1": "50aa594f002a85d5a8d7b5eee73b945d151660f5"},
+    "zy_adjoint": {"bytes": 161.8e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
+                   "source_sha1": "50aa594f002a85d5a8d7b5eee73b945d151660f5"},
+    "x_inverse": {"bytes": 251.7e6, "source": "paper_1707_09898_gb300/csrc/k_xinv.cu",
+                  "source_sha1": "345f3293ba7ccb8c712e7f6ea5240f1b65f6db48"},
     "z_pass": {"bytes": 330.5e6, "source": "paper_1707_09898_gb300/csrc/k_zdir.cu",
                "source_sha1": "1e01034aaa7e24a5aeb9221956bd20b7f6d468eb"},
 }
