@@ -543,6 +543,7 @@ int xinv_chain(tm_ctx* ctx, const float* rho, float* G, int ncomp, const int* sl
   x.G = G;
   x.gmax = ctx->gmax;
   x.tw = ctx->tw;
+  x.status = ctx->dstat;
   Timed t(ctx, KIND_XINV, s);
   CKL(launch_xinv(ctx->L[0], x, s));
   ctx->gmax_of = G;

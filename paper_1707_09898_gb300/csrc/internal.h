@@ -107,6 +107,7 @@ struct XInvArgs {
   int row_base;             // first row of block 0 (host-known); rows < `rows` are valid
   const float2* tw;
   int pdl;                  // launch with programmatic dependent launch
+  unsigned* status;         // device word: bit 0 set when a copy wait timed out (CHAIN, L = 512)
 };
 
 // y pass over [slot][planes][points][P] arrays, tiles of 16 kx columns; blockIdx.z -> in_slot[], out_slot[].

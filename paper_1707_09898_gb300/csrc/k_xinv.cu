@@ -7,6 +7,7 @@
 // dJ/drho = p rho^(p-1) M0 . (D g) (Sec. "Methodology", Eqs. (adjoint1)-(adjoint2)).
 // The last inverse stage maps consecutive threads to consecutive x of one row pair,
 // so global rows are written in 64-byte runs straight from registers.
+#include "tma.cuh"
 #include "xpass.cuh"
 
 namespace tmk {
@@ -256,6 +257,199 @@ __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Chain rule for L = 2 kNT with one contracted slot, warp-specialized: a block of 512
+// threads per SM loops over 32-row tiles; warps 0-7 build the Hermitian extension of
+// tile r from its spectrum rows (one TMA bulk copy into shared memory, a tile ahead)
+// and run the first inverse stage into one of two tiles, while warps 8-15 run the last
+// inverse stage of tile r - 1 from the other and apply G = p rho^(p-1) D, with rho
+// loaded into registers a round ahead. The stage-0 twiddles are shared as in the fused
+// y/z kernels (same products, same results). One block barrier per tile.
+template <int L>
+constexpr size_t xinv_ws_smem(int P) {
+  return 128 + (size_t)(2 * L + 2 * L * TB) * sizeof(float2) + (size_t)ROWS * P * sizeof(float2) + 16;
+}
+
+template <int L, bool P3>
+__global__ void __launch_bounds__(2 * kNT, 1) k_xinv_ws(XInvArgs a) {
+  using S0 = StageShape<L, 0>;
+  using S1 = StageShape<L, 1>;
+  static_assert(k_per_thread<L>() && S0::M == TB && S1::R == TB && S1::M == 1, "two-stage plan 32 x 16");
+  constexpr int R0 = S0::R, M0 = S0::M, R1 = S1::R, RH = R0 / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
+  cx<float>* tw0 = tw + L;
+  cx<float>* tiles = tw0 + L;                       // [2][L][TB], swizzled
+  cx<float>* raw = tiles + 2 * L * TB;              // [ROWS][P] spectrum rows of the next tile
+  unsigned long long* mb = reinterpret_cast<unsigned long long*>(raw + ROWS * a.P);
+  __shared__ float wmax[kNT / 32];
+  for (int i = threadIdx.x; i < L; i += 2 * kNT) tw[i] = reinterpret_cast<const cx<float>*>(a.tw)[i];
+  if (threadIdx.x < kNT) load_twiddles0<L>(tw0, reinterpret_cast<const cx<float>*>(a.tw));
+  if (threadIdx.x == 0) {
+    mbar_init(mb, 1);
+    mbar_init_fence();
+  }
+  pdl_wait();  // the spectra, rho and G belong to earlier kernels
+  __syncthreads();
+  const int ntiles = (a.rows + ROWS - 1) / ROWS;
+  const int nr = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const cx<float>* in = reinterpret_cast<const cx<float>*>(a.in) + a.in_slot[0] * a.in_cstride;
+  auto issue = [&](int r) {  // spectrum rows of tile blockIdx.x + r gridDim.x, one bulk copy
+    const int row0 = (blockIdx.x + r * gridDim.x) * ROWS;
+    const int n = min(ROWS, a.rows - row0);
+    mbar_expect_tx(mb, (unsigned)(n * a.P * sizeof(float2)));
+    bulk_load(raw, in + (long long)row0 * a.P, (unsigned)(n * a.P * sizeof(float2)), mb);
+  };
+  if (threadIdx.x < kNT) {
+    // Hermitian extension and first inverse stage of tile r into tiles[r & 1]
+    const int t = threadIdx.x;
+    // the spectrum rows were written by the previous kernel through ordinary stores; make
+    // them visible to the tensor-copy (async) proxy before its first read
+    if (t == 0) asm volatile("fence.proxy.async.global;\n" ::: "memory");
+    if (t == 0 && nr > 0) issue(0);
+    const int k = t;  // one frequency per thread
+    const int pa = pos_of_k<L>(k), pb = pos_of_k<L>((L - k) % L), pn = pos_of_k<L>(L / 2);
+    const int ca = swz(pa), cb = swz(pb);
+    for (int r = 0; r <= nr; r++) {
+      if (r < nr) {
+        const int row0 = (blockIdx.x + r * gridDim.x) * ROWS;
+        const int nrow = a.rows - row0;
+        cx<float>* tile = tiles + (r & 1) * L * TB;
+        mbar_wait(mb, r & 1, a.status);
+        cx<float> A[TB], B[TB];
+#pragma unroll
+        for (int l = 0; l < TB; l++) {
+          A[l] = 2 * l < nrow ? raw[(2 * l) * a.P + k] : zero<float>();
+          B[l] = 2 * l + 1 < nrow ? raw[(2 * l + 1) * a.P + k] : zero<float>();
+        }
+        cx<float> An = zero<float>(), Bn = zero<float>();  // k = L/2 of line t
+        if (t < TB) {
+          if (2 * t < nrow) An = raw[(2 * t) * a.P + L / 2];
+          if (2 * t + 1 < nrow) Bn = raw[(2 * t + 1) * a.P + L / 2];
+        }
+        bar_named(2, kNT);  // every thread of the group is done with the raw rows
+        if (t == 0 && r + 1 < nr) {
+          fence_proxy_async_smem();  // those reads before the copy that overwrites them
+          issue(r + 1);
+        }
+        cx<float>* ta = tile + pa * TB;
+        cx<float>* tb = tile + pb * TB;
+        if (k == 0) {
+#pragma unroll
+          for (int l = 0; l < TB; l++) ta[l ^ ca] = mk(A[l].x, B[l].x);
+        } else {
+#pragma unroll
+          for (int l = 0; l < TB; l++) {
+            ta[l ^ ca] = mk(A[l].x - B[l].y, A[l].y + B[l].x);  // A + iB
+            tb[l ^ cb] = mk(A[l].x + B[l].y, B[l].x - A[l].y);  // conj(A) + i conj(B)
+          }
+        }
+        if (t < TB) tile[tix(pn, t)] = mk(An.x, Bn.x);
+        bar_named(2, kNT);  // the tile is complete
+        // first inverse stage (positions g R1 + q, 2 kNT units); the stage-0 twiddles of
+        // g >= R0/2 are applied here
+#pragma unroll
+        for (int it = 0; it < 2; it++) {
+          const int u = it * kNT + t, line = u % TB, g = u / TB;
+          cx<float> v[R1];
+#pragma unroll
+          for (int q = 0; q < R1; q++) v[q] = tile[unit_idx<R1, 1, true>(g, g * R1, q, line)];
+          Dft<float, R1, true>::run(v);
+          if (it == 1) {
+#pragma unroll
+            for (int q = 1; q < R1; q++) v[q] = cmulc(v[q], tw[q * g]);
+          }
+#pragma unroll
+          for (int q = 0; q < R1; q++) tile[unit_idx<R1, 1, true>(g, g * R1, q, line)] = v[q];
+        }
+      }
+      bar_named(1, 2 * kNT);
+    }
+  } else {
+    // last inverse stage of tile r - 1 and the chain rule
+    const int t = threadIdx.x - kNT;
+    const int j = t % M0, line = t / M0;
+    float pa[RH], pb[RH];
+    auto fetch_rho = [&](int r) {
+      const int rw = (blockIdx.x + r * gridDim.x) * ROWS + 2 * line;
+      const bool va = rw < a.rows, vb = rw + 1 < a.rows;
+      const long long o = (long long)rw * a.nx + j;
+      const int xn = a.nx - j;
+#pragma unroll
+      for (int q = 0; q < RH; q++) {
+        const bool in_x = q * M0 < xn;
+        pa[q] = (in_x && va) ? a.rho[o + q * M0] : 0.0f;
+        pb[q] = (in_x && vb) ? a.rho[o + a.nx + q * M0] : 0.0f;
+      }
+    };
+    if (nr > 0) fetch_rho(0);
+    float gm = 0.0f;
+    for (int r = 0; r <= nr; r++) {
+      if (r >= 1) {
+        const cx<float>* tile = tiles + ((r - 1) & 1) * L * TB;
+        cx<float> v[R0];
+#pragma unroll
+        for (int q = 0; q < R0; q++) v[q] = tile[tix0<M0>(j, q, line)];
+        if (j != 0) {  // q >= R0/2: applied by the other group
+#pragma unroll
+          for (int q = 1; q < R0 / 2; q++) v[q] = cmulc(v[q], tw0[q * M0 + j]);
+        }
+        Dft<float, R0, true>::run(v);
+        const int rw = (blockIdx.x + (r - 1) * gridDim.x) * ROWS + 2 * line;
+        const bool va = rw < a.rows, vb = rw + 1 < a.rows;
+        float* g = a.G + (long long)rw * a.nx + j;
+        const int xn = a.nx - j;
+#pragma unroll
+        for (int q = 0; q < RH; q++) {
+          if (q * M0 >= xn) continue;
+          if (va) {
+            const float G = dpow_t<P3>(pa[q], a.p) * v[q].x;
+            g[q * M0] = G;
+            gm = fmaxf(gm, fabsf(G));
+          }
+          if (vb) {
+            const float G = dpow_t<P3>(pb[q], a.p) * v[q].y;
+            g[a.nx + q * M0] = G;
+            gm = fmaxf(gm, fabsf(G));
+          }
+        }
+        if (r < nr) fetch_rho(r);  // rho of the tile the other group is preparing
+      }
+      bar_named(1, 2 * kNT);
+    }
+    for (int off = 16; off > 0; off >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, off));
+    if ((t & 31) == 0) wmax[t >> 5] = gm;
+    bar_named(3, kNT);
+    if (t == 0) {
+      for (int w = 1; w < kNT / 32; w++) gm = fmaxf(gm, wmax[w]);
+      if (gm > 0.0f) atomicMax(a.gmax, __float_as_uint(gm));
+    }
+  }
+}
+
+template <int L, bool P3>
+int run_xinv_ws(const XInvArgs& a, cudaStream_t s) {
+  const size_t sm = xinv_ws_smem<L>(a.P);
+  static size_t init = 0;
+  if (init < sm) {
+    if (cudaFuncSetAttribute(k_xinv_ws<L, P3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+      return -1;
+    init = sm;
+  }
+  const int ntiles = (a.rows + ROWS - 1) / ROWS;
+  if (ntiles <= 0) return 0;
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+  }
+  const int blocks = ntiles < nsm ? ntiles : nsm;
+  return launch_k(k_xinv_ws<L, P3>, dim3(blocks), dim3(2 * kNT), sm, s, a.pdl != 0, a) == cudaSuccess ? 0 : -1;
+}
+
 template <int L, int SINK, int MINB, bool P3>
 int run_xinv_sink(const XInvArgs& a, cudaStream_t s) {
   const size_t sm = xsmem<L>();
@@ -278,6 +472,9 @@ int run_xinv(const XInvArgs& a, cudaStream_t s) {
   if (a.sink == SINK_OBJECTIVE) return run_xinv_sink<L, SINK_OBJECTIVE, 2, false>(a, s);
   if (a.ncomp == 1 && a.M0v == nullptr) {  // contracted slot
     if constexpr (k_per_thread<L>()) {
+      // warp-specialized form when the block's raw rows fit beside the two tiles
+      if (a.row_base == 0 && xinv_ws_smem<L>(a.P) <= 227 * 1024 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0)
+        return a.p == 3.0f ? run_xinv_ws<L, true>(a, s) : run_xinv_ws<L, false>(a, s);
       if (a.p == 3.0f) return run_xinv_sink<L, SINK_CHAIN, 2, true>(a, s);
     }
     return run_xinv_sink<L, SINK_CHAIN, 2, false>(a, s);

@@ -18,6 +18,7 @@
 
 #include "fft.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace tmk {
 
@@ -213,37 +214,6 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Tensor-memory-accelerator copies (cp.async.bulk.tensor) completing on an mbarrier.
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned long long* mb, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mb)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* mb, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* mb) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
-          smem_u32(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(smem_u32(mb))
-      : "memory");
-}
-// Wait for phase `parity` of the barrier to complete: at most kSpin polls of about a
-// microsecond each; on timeout the status word is flagged and the caller goes on (its
-// results are then invalid, and the host reports the flag), so no wait can hang.
-constexpr int kSpin = 1 << 20;
-__device__ __forceinline__ void mbar_wait(unsigned long long* mb, unsigned parity, unsigned* status) {
-  unsigned done = 0;
-  for (int i = 0; i < kSpin && !done; i++) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(mb)), "r"(parity), "r"(1000u)
-        : "memory");
-  }
-  if (!done && status) atomicOr(status, 1u);
-}
 
 template <int L>
 __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_staged(YZArgs a, int c) {
@@ -358,9 +328,6 @@ __host__ __device__ constexpr bool yz_ws_plan() {
   return plan_stages(L) == 2 && StageShape<L, 0>::NU == kNT && StageShape<L, 1>::NU == 2 * kNT;
 }
 
-__device__ __forceinline__ void bar_named(int id, int n) {
-  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
-}
 constexpr int kBarAll = 1, kBarGroup = 2;  // named barriers (0 is __syncthreads)
 
 // tensor factor of last-stage element q of group g, C's sign rules applied;
@@ -491,7 +458,10 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a, const __grid_con
 #pragma unroll
         for (int q = R0 / 2; q < R0; q++) v[q] = zero<float>();
         if (r + 1 < n) fetch(cbn, zn);
-        if (t == 0) issue_slice(cb, z, r & 1);
+        if (t == 0) {
+          fence_proxy_async_smem();  // the other group read this slice buffer a round ago
+          issue_slice(cb, z, r & 1);
+        }
         cb = cbn;
         z = zn;
         cbn = z + 1 == a.zin0 + a.nzin ? cb + 1 : cb;
@@ -726,7 +696,10 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a, const __grid_con
     const int line = t % TB, j = t / TB;
     cx<float>* out0 = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[0] * a.out_cstride;
     for (int r = 0; r <= n; r++) {
-      if (t == 0 && r + 1 < n) issue_slice(i0 + r + 1, (r + 1) & 1);
+      if (t == 0 && r + 1 < n) {
+        fence_proxy_async_smem();  // the other group read this slice buffer a round ago
+        issue_slice(i0 + r + 1, (r + 1) & 1);
+      }
       if (r >= 1) {
         int kx0, z;
         item(i0 + r - 1, kx0, z);
