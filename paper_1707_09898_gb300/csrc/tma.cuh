@@ -47,6 +47,12 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
+// Orders global memory written by ordinary stores (of earlier kernels, seen through the
+// dependent-launch wait) before this thread's following TMA reads of it.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;\n" ::: "memory");
+}
+
 // named barrier `id` over n threads (0 is __syncthreads)
 __device__ __forceinline__ void bar_named(int id, int n) {
   asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
