@@ -505,6 +505,7 @@ int xfwd_rho(tm_ctx* ctx, const float* rho, cudaStream_t s, int* nslots) {
   x.tw = ctx->tw;
   *nslots = ctx->m0_var ? 3 : 1;
   x.pdl = ctx->pdl;
+  x.status = ctx->dstat;
   if (ctx->pend_rho && ctx->pend_rho == rho && xfwd_fuses_step(ctx->L[0], x.src, *nslots)) {
     x.upd_rho = ctx->pend_rho;
     x.upd_G = ctx->pend_G;

@@ -68,6 +68,7 @@ struct XFwdArgs {
   int upd_normalize;
   const unsigned int* upd_gmax;
   int pdl;                  // launch with programmatic dependent launch
+  unsigned* status;         // device word: bit 0 set when a copy wait timed out (L = 512 one-slot pass)
 };
 // whether launch_xfwd applies a pending step inside the pass for this length and source
 bool xfwd_fuses_step(int L, int src, int ncomp);

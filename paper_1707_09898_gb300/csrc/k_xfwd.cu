@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(2 * kNT, 1) k_xfwd_ws(XFwdArgs a) {
         const bool wa = rw < a.rows, wb = rw + 1 < a.rows;
         const long long o = (long long)rw * a.nx + j;
         const int xn = a.nx - j;
-        mbar_wait(mb, r & 1, nullptr);
+        mbar_wait(mb, r & 1, a.status);
         float va[RH], vb[RH];
 #pragma unroll
         for (int q = 0; q < RH; q++) {
