@@ -43,9 +43,9 @@ MEASURED_TRAFFIC = {
     "x_forward": {"bytes": 287.7e6, "source": "paper_1707_09898_gb300/csrc/k_xfwd.cu",  # with the fused step
                   "source_sha1": "f565c14a45fdfca0a5b06e81872532755122bc43"},
     "yz_forward": {"bytes": 219.8e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
-                   "source_sha1": "d5a73c58d556ec2b130bd1e6652490cce4283da6"},
+                   "source_sha1": "a8060f1ef153b7d453354ebcd0021d119cf4472b"},
     "zy_adjoint": {"bytes": 161.7e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
-                   "source_sha1": "d5a73c58d556ec2b130bd1e6652490cce4283da6"},
+                   "source_sha1": "a8060f1ef153b7d453354ebcd0021d119cf4472b"},
     "x_inverse": {"bytes": 250.3e6, "source": "paper_1707_09898_gb300/csrc/k_xinv.cu",
                   "source_sha1": "c25200c4e8f371b6b97bad7060d274435af13925"},
     "z_pass": {"bytes": 330.5e6, "source": "paper_1707_09898_gb300/csrc/k_zdir.cu",

@@ -311,15 +311,16 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_staged(YZArgs a, int c) {
 // whose first stage has kNT units and whose last stage has 2 kNT (L = 512): a block of
 // 512 threads runs two groups of eight warps on one plane each, a plane apart, with a
 // tile per group and one block barrier per plane:
-//   forward: the "transform" warps read the staged input rows of plane z + 1 and run
-//            the first DIF stage into one tile while the "accumulate" warps finish
-//            plane z from the other tile (the last stage in registers) and add
-//            s(zo - z) times it into their sums;
-//   adjoint: the "load" warps form s(z - zp) times the source spectrum for plane z + 1
-//            and run the first inverse stage into one tile while the "store" warps
-//            finish plane z from the other tile and write its rows.
-// The tensor slices (and, forward, the next plane's input rows) are copied into shared
-// memory with cp.async a round ahead. C is the tensor component, so the sign rules of
+//   forward: the "transform" warps take the input rows of plane z + 1 (loaded into
+//            registers a round ahead) and run the first DIF stage into one tile while
+//            the "accumulate" warps finish plane z from the other tile (the last stage
+//            in registers) and add s(zo - z) times it into their sums;
+//   adjoint: the "load" warps form s(z - zp) times the source spectrum (held in
+//            registers per column block) for plane z + 1 and run the first inverse
+//            stage into one tile while the "store" warps finish plane z from the other
+//            tile and write its rows.
+// The tensor slices arrive in shared memory by TMA (two boxes per slice, mbarrier
+// completion) a round ahead. C is the tensor component, so the sign rules of
 // the folded tensor are resolved at compile time; the positions of the last stage are
 // g R1 + q with frequency ky = g + q L/R1, so the tensor row of every element is a
 // compile-time offset from one of two per-thread bases.
