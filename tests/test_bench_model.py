@@ -38,7 +38,18 @@ def test_main_kernels(model):
 def test_fused_step_adds_gradient_in_and_rho_out(model):
     ab, abs_ = model
     assert abs_["x_forward"] - ab["x_forward"] == 8 * CELLS
-    assert {k: v for k, v in abs_.items() if k != "x_forward"} == {k: v for k, v in ab.items() if k != "x_forward"}
+    # without the fusion the update is a kernel of its own: rho and G in, rho out
+    assert ab["other"] == 12 * CELLS and "other" not in abs_
+    rest = ("x_forward", "other")
+    assert {k: v for k, v in abs_.items() if k not in rest} == {k: v for k, v in ab.items() if k not in rest}
+
+
+def test_stray_field_model():
+    sf = bench.stray_field_bytes(W.config4(N), (512, 512, 512))
+    T = (512 // 2 + 1) ** 2 * K * 4  # one folded tensor component
+    assert sf["x_forward"] == 4 * CELLS + SPEC
+    assert sf["z_pass"] == 8 * K * 512 * (N + 3 * N) + 3 * T   # M0 along z reaches xz, yz, zz
+    assert sf["x_inverse"] == 3 * (SPEC + 4 * CELLS)
 
 
 def test_step_total_is_about_a_gigabyte(model):

@@ -17,6 +17,8 @@ from oracle import optimizer as P
 from oracle import tensor as T
 from paper_1707_09898_gb300 import workloads as W
 
+from errlog import record
+
 pytestmark = pytest.mark.gpu
 
 DEV = torch.device("cuda", 0)
@@ -101,6 +103,7 @@ def test_config1_against_oracle_and_direct_sum():
     Jr, Gr, Hr = O.objective_and_gradient(fft, rho, wl.M0_const(), wl.p, mask, wl.Ht_const_vec(), wl.w)
     Jd, Gd, Hd = O.objective_and_gradient(direct, rho, wl.M0_const(), wl.p, mask, wl.Ht_const_vec(), wl.w)
     assert rel_l2(Hr, Hd) <= 1e-12 and rel_l2(Gr, Gd) <= 1e-12
+    record("c1 16x16x17", H=rel_l2(H, Hr), J=abs(J - Jr) / abs(Jr), G=rel_l2(G.cpu().numpy(), Gr))
     assert rel_l2(H, Hr) <= 1e-5
     assert rel_l2(G.cpu().numpy(), Gr) <= 1e-4
     assert abs(J - Jr) <= 1e-5 * abs(Jr)

@@ -6,6 +6,7 @@ time-critical loop that cannot absorb cudaMalloc's implicit synchronisation).
 Its scratch is a static device array shared by every call, so this checks two
 calls in a row (the second with fewer elements, over the first call's leftover
 scratch contents), the unnormalised form, a zero gradient, and the size limit.
+One case also goes straight to the float64 oracle's projected-gradient step.
 This file is collected last on purpose.
 """
 
@@ -58,6 +59,29 @@ def test_noalloc_step_matches_context_step(env):
         torch.cuda.synchronize()
         assert torch.equal(new, ref), float((new - ref).abs().max())
         m.close()
+
+
+def test_noalloc_step_matches_oracle(env):
+    """The step against oracle.optimizer.projected_gradient_step on the same float32 inputs:
+    the float32 step alpha / max|G| and one rounding per update, so within a few float32
+    ulps of rho (<= 1) of the float64 result; the clip to [0, 1] is exact on both sides."""
+    from oracle import optimizer as P
+
+    _, _lib = env
+    L = _lib.lib()
+    rng = np.random.default_rng(21)
+    for n, alpha, normalize in [(70_001, 0.1, True), (70_001, 0.05, False), (3, 0.3, True)]:
+        rho_np = rng.random(n, dtype=np.float64).astype(np.float32)
+        G_np = (rng.normal(size=n) * (0.2 if not normalize else 1e11)).astype(np.float32)
+        rho, G = torch.from_numpy(rho_np).to(DEV), torch.from_numpy(G_np).to(DEV)
+        for _ in range(2):  # two calls in a row over the scratch the first one left
+            out = rho.clone()
+            assert L.tm_optimize_step_noalloc(_p(out), _p(G), n, alpha, int(normalize), _stream()) == 0
+            torch.cuda.synchronize()
+        ref = P.projected_gradient_step(rho_np, G_np, alpha, normalize)
+        err = np.abs(out.cpu().numpy().astype(np.float64) - ref).max()
+        assert err <= 4 * 2.0**-24, (n, normalize, err)
+        assert ((out >= 0) & (out <= 1)).all()
 
 
 def test_noalloc_zero_gradient_and_size_limit(env):
