@@ -27,6 +27,9 @@
  *   context must not overlap on the GPU (they share its workspace).
  * Errors. Every int-returning call returns TM_OK (0) or a negative code and then
  *   leaves a message for tm_last_error(). Nothing is thrown across the ABI.
+ *   Kernels never spin without a bound: a wait that runs out sets a bit of the
+ *   context's device status word, which tm_evaluate / tm_evaluate_step (with
+ *   J_host != NULL) and tm_get_objective read and report as TM_ERR_TIMEOUT.
  */
 #ifndef TOPOMAG_H
 #define TOPOMAG_H
@@ -44,6 +47,8 @@ extern "C" {
 #define TM_ERR_STATE (-3)    /* call order: e.g. no grid, no tensor, no M0 */
 #define TM_ERR_CUDA (-4)     /* a CUDA call failed (message has the CUDA error) */
 #define TM_ERR_NOMEM (-5)    /* device allocation failed */
+#define TM_ERR_TIMEOUT (-6)  /* a bounded wait inside a kernel ran out; that call's results are invalid */
+#define TM_ERR_INJECTED (-7) /* failure forced by the fault-injection hook (tm_inject_fault) */
 
 typedef struct tm_ctx tm_ctx;
 
@@ -218,6 +223,50 @@ int tm_evaluate_step(tm_ctx* ctx, float* rho, float alpha, int normalize, double
  */
 int tm_optimize_step_noalloc(float* rho, const float* dJdrho, long long n, float alpha, int normalize,
                              void* stream);
+
+/*
+ * Validation of a density (the box constraint 0 <= rho <= 1 of Sec. "Methodology",
+ * after Eq. 1): counts the entries of rho [nzd][ny][nx] that are NaN or outside
+ * [0, 1] and stores the count in *n_bad (host). Synchronises `stream`. Returns
+ * TM_ERR_ARG (with the count in the message) when any entry is bad, else TM_OK.
+ * The evaluation calls do not check their input; a loop calls this where it takes
+ * rho from outside (a start, a resume).
+ */
+int tm_check_design(tm_ctx* ctx, const float* rho, long long* n_bad, void* stream);
+
+/*
+ * Per-iteration quantities of an optimisation run (the volume fraction is the
+ * quantity of Fig. 4, the share of intermediate densities that of Fig. 3, Sec.
+ * "Validation and Benchmarks"): out[0] = max_j |dJdrho_j|, out[1] = sum_j rho_j / N,
+ * out[2] = #{j : 0.1 < rho_j < 0.9} / N over the N design cells. float64 sums in a
+ * fixed order (the same bits on every call). Synchronises `stream`.
+ */
+int tm_iteration_stats(tm_ctx* ctx, const float* rho, const float* dJdrho, double out[3], void* stream);
+
+/*
+ * Fault injection (test support; the paper has no counterpart). After
+ * tm_inject_fault(call, nth), the nth following call of the entry point named
+ * `call` (e.g. "tm_evaluate") in this process returns TM_ERR_INJECTED before it
+ * does anything, so the context is left as it was; later calls run normally.
+ * nth <= 0 or call == NULL disarms. The environment variable
+ * TM_FAULT_INJECT=<call>[:<nth>] (nth default 1), read when the library loads,
+ * arms it the same way. Every int-returning tm_* entry point that takes a context
+ * honours it.
+ */
+int tm_inject_fault(const char* call, long long nth);
+
+/*
+ * Self-test of the bounded waits (test support; no counterpart in the paper).
+ * The kernels that receive copies from the tensor memory accelerator wait on an
+ * mbarrier with a bounded number of polls; when the bound runs out they set a bit
+ * of the context's device status word and return instead of hanging, and the host
+ * reports TM_ERR_TIMEOUT. This call launches one block that waits, at most `polls`
+ * polls (1 <= polls <= 65536, about a microsecond each), on an mbarrier phase that
+ * no copy and no thread completes; it synchronises `stream` and returns
+ * TM_ERR_TIMEOUT with the status bit seen (the bit is then cleared), or TM_ERR_CUDA
+ * if the bit was not set.
+ */
+int tm_selftest_wait_timeout(tm_ctx* ctx, int polls, void* stream);
 
 /*
  * Prepared path (tm_evaluate): 1 (default) fuses the y transform of the design

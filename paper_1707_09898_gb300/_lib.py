@@ -15,7 +15,8 @@ NET_HEADER = os.path.join(os.path.dirname(HERE), "include", "topomag_net.h")
 LBFGSB_HEADER = os.path.join(os.path.dirname(HERE), "include", "topomag_lbfgsb.h")
 
 TM_OK = 0
-ERRORS = {-1: "TM_ERR_ARG", -2: "TM_ERR_SIZE", -3: "TM_ERR_STATE", -4: "TM_ERR_CUDA", -5: "TM_ERR_NOMEM"}
+ERRORS = {-1: "TM_ERR_ARG", -2: "TM_ERR_SIZE", -3: "TM_ERR_STATE", -4: "TM_ERR_CUDA", -5: "TM_ERR_NOMEM",
+          -6: "TM_ERR_TIMEOUT", -7: "TM_ERR_INJECTED"}
 
 _lib = None
 
@@ -46,6 +47,10 @@ _SIGS = {
     "tm_optimize_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_float, ctypes.c_int, vp]),
     "tm_evaluate_step": (ctypes.c_int, [vp, vp, ctypes.c_float, ctypes.c_int, vp, vp, vp]),
     "tm_optimize_step_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_longlong, ctypes.c_float, ctypes.c_int, vp]),
+    "tm_check_design": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_longlong), vp]),
+    "tm_iteration_stats": (ctypes.c_int, [vp, vp, vp, ctypes.c_double * 3, vp]),
+    "tm_inject_fault": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_longlong]),
+    "tm_selftest_wait_timeout": (ctypes.c_int, [vp, ctypes.c_int, vp]),
     "tm_profile": (ctypes.c_int, [vp, ctypes.c_int]),
     "tm_set_fused": (ctypes.c_int, [vp, ctypes.c_int]),
     "tm_profile_read": (ctypes.c_int, [vp, ctypes.c_double * 9, ctypes.c_int * 9]),

@@ -6,7 +6,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "../../include/topomag.h"
@@ -68,6 +72,8 @@ struct tm_ctx {
   unsigned* yzcnt = nullptr;       // [P / TB] item counters of the flattened fused forward
   int nsm = 0;
   int* ext = nullptr;       // [2]: z range of the target planes
+  double* stats = nullptr;  // [2 * kStatBlocks + 2] scratch of tm_iteration_stats
+  unsigned long long* nbad = nullptr;  // count of tm_check_design
   double* Jhost = nullptr;  // pinned
   // per-kernel event timing (tm_profile)
   bool prof_on = false;
@@ -89,6 +95,49 @@ int fail(tm_ctx* c, int code, const char* fmt, ...) {
   return code;
 }
 
+// Fault injection (tm_inject_fault / TM_FAULT_INJECT=<call>[:<nth>]): the armed call
+// fails with TM_ERR_INJECTED on its nth invocation, before it touches any state.
+struct Injection {
+  std::mutex mu;
+  std::string call;
+  long long left = 0;
+  Injection() {
+    const char* e = getenv("TM_FAULT_INJECT");
+    if (!e || !*e) return;
+    std::string v(e);
+    const size_t c = v.find(':');
+    call = v.substr(0, c);
+    left = c == std::string::npos ? 1 : atoll(v.c_str() + c + 1);
+  }
+};
+Injection& injection() {
+  static Injection inj;
+  return inj;
+}
+bool injected(const char* name) {
+  Injection& in = injection();
+  std::lock_guard<std::mutex> lock(in.mu);
+  if (in.left <= 0 || in.call != name) return false;
+  if (--in.left > 0) return false;
+  in.call.clear();
+  return true;
+}
+// Entry points called from inside another one (tm_evaluate_step -> tm_evaluate) do not
+// count: only calls made by the caller of the library do.
+thread_local int tl_depth = 0;
+struct DepthGuard {
+  DepthGuard() { tl_depth++; }
+  ~DepthGuard() { tl_depth--; }
+};
+#define INJECT(ctx, name)                                                                       \
+  if (tl_depth == 0 && injected(name))                                                          \
+    return fail(ctx, TM_ERR_INJECTED, "%s: failure injected by tm_inject_fault", name);         \
+  DepthGuard depth_guard_
+
+// Reads the device status word (synchronising `s`); a set bit 0 means that a bounded
+// wait ran out in some kernel since the word was last cleared.
+int check_status(tm_ctx* ctx, cudaStream_t s);
+
 #define CK(call)                                                                                   \
   do {                                                                                             \
     cudaError_t e_ = (call);                                                                       \
@@ -106,6 +155,18 @@ int fail(tm_ctx* c, int code, const char* fmt, ...) {
                   cudaGetErrorString(e_));                                                         \
     }                                                                                              \
   } while (0)
+
+int check_status(tm_ctx* ctx, cudaStream_t s) {
+  CK(cudaMemcpyAsync(ctx->hstat, ctx->dstat, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (*ctx->hstat) {
+    CK(cudaMemsetAsync(ctx->dstat, 0, sizeof(unsigned), s));
+    CK(cudaStreamSynchronize(s));
+    return fail(ctx, TM_ERR_TIMEOUT, "a bounded wait for a tensor-memory-accelerator copy ran out in a kernel; "
+                                     "the results since the last check are invalid");
+  }
+  return TM_OK;
+}
 
 int pick_length(int n) {
   static const int ls[] = {
@@ -623,6 +684,8 @@ void tm_destroy(tm_ctx* ctx) {
   cudaFree(ctx->gmax);
   cudaFree(ctx->Jcount);
   cudaFree(ctx->ext);
+  cudaFree(ctx->stats);
+  cudaFree(ctx->nbad);
   if (ctx->Jhost) cudaFreeHost(ctx->Jhost);
   delete ctx;
 }
@@ -630,6 +693,7 @@ void tm_destroy(tm_ctx* ctx) {
 const char* tm_last_error(const tm_ctx* ctx) { return ctx ? ctx->err : "null context"; }
 
 int tm_set_grid(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[3]) {
+  INJECT(ctx, "tm_set_grid");
   if (!ctx || !n_out || !cellsize) return fail(ctx, TM_ERR_ARG, "null argument");
   for (int a = 0; a < 3; a++) {
     if (n_out[a] < 4 || n_out[a] > kMaxL / 2)
@@ -690,6 +754,7 @@ int tm_get_fft_lengths(const tm_ctx* ctx, int L[3]) {
 }
 
 int tm_set_penalty(tm_ctx* ctx, double p) {
+  INJECT(ctx, "tm_set_penalty");
   if (!ctx) return TM_ERR_ARG;
   if (!(p >= 1.0) || !isfinite(p)) return fail(ctx, TM_ERR_ARG, "penalty p = %g must be >= 1", p);
   ctx->p = p;
@@ -697,6 +762,7 @@ int tm_set_penalty(tm_ctx* ctx, double p) {
 }
 
 int tm_set_M0(tm_ctx* ctx, const float* M0_dev, const double M0_const[3], void* stream) {
+  INJECT(ctx, "tm_set_M0");
   if (!ctx) return TM_ERR_ARG;
   if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
   CK(cudaSetDevice(ctx->device));
@@ -719,6 +785,7 @@ int tm_set_M0(tm_ctx* ctx, const float* M0_dev, const double M0_const[3], void* 
 }
 
 int tm_set_tensor(tm_ctx* ctx, void* stream) {
+  INJECT(ctx, "tm_set_tensor");
   if (!ctx) return TM_ERR_ARG;
   if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
   CK(cudaSetDevice(ctx->device));
@@ -730,6 +797,7 @@ int tm_set_tensor(tm_ctx* ctx, void* stream) {
 }
 
 int tm_stray_field(tm_ctx* ctx, const float* rho, float* H, void* stream) {
+  INJECT(ctx, "tm_stray_field");
   int r = check_ready(ctx);
   if (r) return r;
   if (!rho || !H) return fail(ctx, TM_ERR_ARG, "null array");
@@ -759,6 +827,7 @@ int tm_stray_field(tm_ctx* ctx, const float* rho, float* H, void* stream) {
 }
 
 int tm_stray_field_adjoint(tm_ctx* ctx, const float* rho, const float* gH, float* dJdrho, void* stream) {
+  INJECT(ctx, "tm_stray_field_adjoint");
   int r = check_ready(ctx);
   if (r) return r;
   if (!rho || !gH || !dJdrho) return fail(ctx, TM_ERR_ARG, "null array");
@@ -810,6 +879,7 @@ int tm_stray_field_adjoint(tm_ctx* ctx, const float* rho, const float* gH, float
 int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask, const float* H_target,
                               const float Ht_const[3], const float w[3], double* J_host, float* dJdrho,
                               float* H_out, void* stream) {
+  INJECT(ctx, "tm_objective_and_gradient");
   int r = check_ready(ctx);
   if (r) return r;
   if (!rho || !mask || !w || !dJdrho) return fail(ctx, TM_ERR_ARG, "null array");
@@ -916,6 +986,7 @@ int tm_objective_and_gradient(tm_ctx* ctx, const float* rho, const uint8_t* mask
 
 int tm_set_target(tm_ctx* ctx, const uint8_t* mask, const float* H_target, const float Ht_const[3], const float w[3],
                   void* stream) {
+  INJECT(ctx, "tm_set_target");
   if (!ctx) return TM_ERR_ARG;
   if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
   if (!mask || !w) return fail(ctx, TM_ERR_ARG, "null array");
@@ -1128,6 +1199,7 @@ int evaluate_stencil(tm_ctx* ctx, const float* rho, float* dJdrho, cudaStream_t 
 
 int tm_set_stencil_objective(tm_ctx* ctx, long long K, const long long* row_ptr, const int* comp,
                              const long long* cell, const double* a, const double* c, void* stream) {
+  INJECT(ctx, "tm_set_stencil_objective");
   if (!ctx) return TM_ERR_ARG;
   if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
   if (K < 0 || (K > 0 && (!row_ptr || !comp || !cell || !a || !c))) return fail(ctx, TM_ERR_ARG, "null array");
@@ -1204,6 +1276,7 @@ int tm_set_stencil_objective(tm_ctx* ctx, long long K, const long long* row_ptr,
 }
 
 int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, void* stream) {
+  INJECT(ctx, "tm_evaluate");
   int r = check_ready(ctx);
   if (r) return r;
   if (!ctx->have_target) return fail(ctx, TM_ERR_STATE, "no target: call tm_set_target first");
@@ -1267,27 +1340,25 @@ int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, vo
   }
   if (J_host) {
     CK(cudaMemcpyAsync(ctx->Jhost, ctx->Jdev, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(ctx->hstat, ctx->dstat, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    if ((r = check_status(ctx, s))) return r;  // synchronises s
     *J_host = *ctx->Jhost;
-    if (*ctx->hstat) {
-      cudaMemset(ctx->dstat, 0, sizeof(unsigned));
-      return fail(ctx, TM_ERR_CUDA, "a tensor-copy wait of the fused y/z kernels timed out; results are invalid");
-    }
   }
   return TM_OK;
 }
 
 int tm_get_objective(tm_ctx* ctx, double* J_host, void* stream) {
+  INJECT(ctx, "tm_get_objective");
   if (!ctx || !J_host) return fail(ctx, TM_ERR_ARG, "null argument");
   CK(cudaSetDevice(ctx->device));
   CK(cudaMemcpyAsync(ctx->Jhost, ctx->Jdev, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
-  CK(cudaStreamSynchronize(S(stream)));
+  int r = check_status(ctx, S(stream));  // synchronises the stream
+  if (r) return r;
   *J_host = *ctx->Jhost;
   return TM_OK;
 }
 
 int tm_copy_objective(tm_ctx* ctx, double* dst, void* stream) {
+  INJECT(ctx, "tm_copy_objective");
   if (!ctx || !dst) return fail(ctx, TM_ERR_ARG, "null argument");
   CK(cudaSetDevice(ctx->device));
   CK(cudaMemcpyAsync(dst, ctx->Jdev, sizeof(double), cudaMemcpyDefault, S(stream)));
@@ -1295,6 +1366,7 @@ int tm_copy_objective(tm_ctx* ctx, double* dst, void* stream) {
 }
 
 int tm_optimize_step(tm_ctx* ctx, float* rho, const float* dJdrho, float alpha, int normalize, void* stream) {
+  INJECT(ctx, "tm_optimize_step");
   if (!ctx) return TM_ERR_ARG;
   if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
   if (!rho || !dJdrho) return fail(ctx, TM_ERR_ARG, "null array");
@@ -1315,6 +1387,7 @@ int tm_optimize_step(tm_ctx* ctx, float* rho, const float* dJdrho, float alpha, 
 
 int tm_evaluate_step(tm_ctx* ctx, float* rho, float alpha, int normalize, double* J_host, float* dJdrho,
                      void* stream) {
+  INJECT(ctx, "tm_evaluate_step");
   int r = check_ready(ctx);
   if (r) return r;
   if (!ctx->have_target) return fail(ctx, TM_ERR_STATE, "no target: call tm_set_target first");
@@ -1353,13 +1426,87 @@ int tm_evaluate_step(tm_ctx* ctx, float* rho, float alpha, int normalize, double
   return r;
 }
 
+int tm_check_design(tm_ctx* ctx, const float* rho, long long* n_bad, void* stream) {
+  INJECT(ctx, "tm_check_design");
+  if (!ctx) return TM_ERR_ARG;
+  if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
+  if (!rho || !n_bad) return fail(ctx, TM_ERR_ARG, "null argument");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = S(stream);
+  if (!ctx->nbad) CK(cudaMalloc(&ctx->nbad, sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(ctx->nbad, 0, sizeof(unsigned long long), s));
+  CKL(launch_check_design(rho, design_cells(ctx), ctx->nbad, s));
+  unsigned long long nb = 0;
+  CK(cudaMemcpyAsync(&nb, ctx->nbad, sizeof(nb), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *n_bad = (long long)nb;
+  if (nb) return fail(ctx, TM_ERR_ARG, "rho: %llu of %lld entries are NaN or outside [0, 1]", nb, design_cells(ctx));
+  return TM_OK;
+}
+
+int tm_iteration_stats(tm_ctx* ctx, const float* rho, const float* dJdrho, double out[3], void* stream) {
+  INJECT(ctx, "tm_iteration_stats");
+  if (!ctx) return TM_ERR_ARG;
+  if (!ctx->have_grid) return fail(ctx, TM_ERR_STATE, "no grid: call tm_set_grid first");
+  if (!rho || !dJdrho || !out) return fail(ctx, TM_ERR_ARG, "null argument");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = S(stream);
+  constexpr int kStatBlocks = 512;
+  if (!ctx->stats) CK(cudaMalloc(&ctx->stats, (2 * kStatBlocks + 2) * sizeof(double)));
+  const long long n = design_cells(ctx);
+  if (ctx->gmax_of != dJdrho) {  // max|G| of this array (the evaluation that wrote it keeps it otherwise)
+    CK(cudaMemsetAsync(ctx->gmax, 0, sizeof(unsigned int), s));
+    CKL(launch_absmax(dJdrho, n, ctx->gmax, s));
+    ctx->gmax_of = dJdrho;
+  }
+  CKL(launch_rho_stats(rho, n, ctx->stats, kStatBlocks, ctx->stats + 2 * kStatBlocks, s));
+  double h[2];
+  unsigned gbits = 0;
+  CK(cudaMemcpyAsync(h, ctx->stats + 2 * kStatBlocks, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&gbits, ctx->gmax, sizeof(gbits), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  float gm;
+  memcpy(&gm, &gbits, sizeof(gm));
+  out[0] = gm;
+  out[1] = h[0] / (double)n;
+  out[2] = h[1] / (double)n;
+  return TM_OK;
+}
+
+int tm_inject_fault(const char* call, long long nth) {
+  Injection& in = injection();
+  std::lock_guard<std::mutex> lock(in.mu);
+  if (!call || nth <= 0) {
+    in.call.clear();
+    in.left = 0;
+    return TM_OK;
+  }
+  in.call = call;
+  in.left = nth;
+  return TM_OK;
+}
+
+int tm_selftest_wait_timeout(tm_ctx* ctx, int polls, void* stream) {
+  INJECT(ctx, "tm_selftest_wait_timeout");
+  if (!ctx) return TM_ERR_ARG;
+  if (polls < 1 || polls > 65536) return fail(ctx, TM_ERR_ARG, "polls = %d outside [1, 65536]", polls);
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = S(stream);
+  CKL(launch_wait_selftest(ctx->dstat, polls, s));
+  const int r = check_status(ctx, s);
+  if (r == TM_OK) return fail(ctx, TM_ERR_CUDA, "the self-test wait did not set the status word");
+  return r;
+}
+
 int tm_set_fused(tm_ctx* ctx, int on) {
+  INJECT(ctx, "tm_set_fused");
   if (!ctx) return TM_ERR_ARG;
   ctx->fuse_yz = on != 0;
   return TM_OK;
 }
 
 int tm_profile(tm_ctx* ctx, int on) {
+  INJECT(ctx, "tm_profile");
   if (!ctx) return TM_ERR_ARG;
   ctx->prof_on = on != 0;
   ctx->ev_used = 0;
@@ -1367,6 +1514,7 @@ int tm_profile(tm_ctx* ctx, int on) {
 }
 
 int tm_profile_read(tm_ctx* ctx, double ms[9], int launches[9]) {
+  INJECT(ctx, "tm_profile_read");
   if (!ctx || !ms || !launches) return fail(ctx, TM_ERR_ARG, "null argument");
   CK(cudaSetDevice(ctx->device));
   for (int k = 0; k < KIND_N; k++) {

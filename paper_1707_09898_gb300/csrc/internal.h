@@ -235,6 +235,14 @@ int launch_mask_extent(const uint8_t* mask, int nz, long long plane, int* ext, c
 int launch_update(float* rho, const float* G, long long n, float alpha, int normalize, const unsigned int* gmax,
                   cudaStream_t s);
 
+// Validation, per-iteration statistics, wait self-test -- misc.cu
+// count of entries that are NaN or outside [0, 1] into *bad (zeroed by the caller)
+int launch_check_design(const float* rho, long long n, unsigned long long* bad, cudaStream_t s);
+// part [2 * nblk] doubles of scratch, out [2]: sum rho, count of 0.1 < rho < 0.9 (fixed order)
+int launch_rho_stats(const float* rho, long long n, double* part, int nblk, double* out, cudaStream_t s);
+// one block waits at most `polls` polls on an mbarrier phase nothing completes; sets bit 0 of *status
+int launch_wait_selftest(unsigned* status, int polls, cudaStream_t s);
+
 // Quadratic stencil objective -- misc.cu
 struct StencilArgs {
   long long K, U;                                 // rows, distinct referenced values

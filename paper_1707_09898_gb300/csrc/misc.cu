@@ -7,6 +7,7 @@
 
 #include "../../include/topomag.h"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace tmk {
 
@@ -127,6 +128,68 @@ __global__ void k_reduce_slices(float* scratch, int nb) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Validation of rho (box constraint 0 <= rho <= 1, Sec. "Methodology"): count of
+// entries that are NaN or outside [0, 1] (integer count, any order gives the same).
+__global__ void k_check_design(const float* rho, long long n, unsigned long long* bad) {
+  unsigned c = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    c += !(rho[i] >= 0.0f && rho[i] <= 1.0f);  // NaN fails both comparisons
+  for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(bad, (unsigned long long)c);
+}
+
+// Per-block float64 partials of sum rho and of the count of intermediate densities
+// 0.1 < rho < 0.9 (the quantities of Figs. 4 and 3), grid-stride in a fixed
+// assignment; k_rho_stats_final sums them in block order.
+__global__ void k_rho_stats(const float* rho, long long n, double* part) {
+  __shared__ double rs[256], rc[256];
+  double s = 0.0, c = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float r = rho[i];
+    s += (double)r;
+    c += (r > 0.1f && r < 0.9f) ? 1.0 : 0.0;
+  }
+  rs[threadIdx.x] = s;
+  rc[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      rs[threadIdx.x] += rs[threadIdx.x + w];
+      rc[threadIdx.x] += rc[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = rs[0];
+    part[2 * blockIdx.x + 1] = rc[0];
+  }
+}
+__global__ void k_rho_stats_final(const double* part, int nblk, double* out) {
+  if (threadIdx.x == 0) {
+    double s = 0.0, c = 0.0;
+    for (int b = 0; b < nblk; b++) {
+      s += part[2 * b];
+      c += part[2 * b + 1];
+    }
+    out[0] = s;
+    out[1] = c;
+  }
+}
+
+// Self-test of the bounded mbarrier wait: the barrier expects one arrival that never
+// comes, so the wait runs out after `polls` polls, flags the status word and returns.
+__global__ void k_wait_selftest(unsigned* status, int polls) {
+  __shared__ __align__(8) unsigned long long mb;
+  if (threadIdx.x == 0) {
+    mbar_init(&mb, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait_limit(&mb, 0, polls, status);
+  __syncthreads();
+}
+
 std::mutex g_noalloc_mu;
 float* g_noalloc_ptr[256] = {nullptr};  // device address of g_noalloc_scratch, per device ordinal
 
@@ -173,6 +236,20 @@ int launch_stencil(const StencilArgs& a, cudaStream_t s) {
   const long long b = (a.U + 255) / 256;
   k_stencil_cols<<<(int)(b < 1 ? 1 : (b > 4096 ? 4096 : b)), 256, 0, s>>>(a.U, a.cp, a.cidx, a.crow, a.ca, a.c, a.r,
                                                                          a.gH);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_check_design(const float* rho, long long n, unsigned long long* bad, cudaStream_t s) {
+  k_check_design<<<grid_for(n, 256 * 8), 256, 0, s>>>(rho, n, bad);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+int launch_rho_stats(const float* rho, long long n, double* part, int nblk, double* out, cudaStream_t s) {
+  k_rho_stats<<<nblk, 256, 0, s>>>(rho, n, part);
+  k_rho_stats_final<<<1, 32, 0, s>>>(part, nblk, out);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
+int launch_wait_selftest(unsigned* status, int polls, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(status, polls);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 

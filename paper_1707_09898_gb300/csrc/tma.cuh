@@ -40,6 +40,20 @@ __device__ __forceinline__ void mbar_wait(unsigned long long* mb, unsigned parit
   if (!done && status) atomicOr(status, 1u);
 }
 
+// The same wait with a caller-given bound (polls >= 1); true if the phase completed.
+__device__ __forceinline__ bool mbar_wait_limit(unsigned long long* mb, unsigned parity, int polls, unsigned* status) {
+  unsigned done = 0;
+  for (int i = 0; i < polls && !done; i++) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mb)), "r"(parity), "r"(1000u)
+        : "memory");
+  }
+  if (!done && status) atomicOr(status, 1u);
+  return done != 0;
+}
+
 // Orders this thread's view of shared memory (including what other threads read before
 // a barrier it passed) before its following copies into shared memory by the async proxy:
 // needed before a TMA overwrites a buffer that threads read with ordinary loads.

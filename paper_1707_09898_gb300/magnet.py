@@ -199,6 +199,25 @@ class Magnet:
                                          _ptr(G), _stream(self.device)))
         return (J.value if sync else None), G
 
+    def check_design(self, rho):
+        """Raise TopomagError (TM_ERR_ARG) if rho has entries that are NaN or outside [0, 1]."""
+        rho = self._dev(rho, F32, self.design_shape, "rho")
+        n = ctypes.c_longlong(0)
+        self._ck(self.L.tm_check_design(self.h, _ptr(rho), ctypes.byref(n), _stream(self.device)))
+        return 0
+
+    def iteration_stats(self, rho, G):
+        """(max|G|, volume fraction sum(rho)/N, share of cells with 0.1 < rho < 0.9)."""
+        rho = self._dev(rho, F32, self.design_shape, "rho")
+        G = self._dev(G, F32, self.design_shape, "G")
+        out = (ctypes.c_double * 3)()
+        self._ck(self.L.tm_iteration_stats(self.h, _ptr(rho), _ptr(G), out, _stream(self.device)))
+        return tuple(out)
+
+    def selftest_wait_timeout(self, polls=300):
+        """Run the bounded-wait self-test; returns the library's return code (TM_ERR_TIMEOUT expected)."""
+        return self.L.tm_selftest_wait_timeout(self.h, int(polls), _stream(self.device))
+
     # -- per-kernel event timing ---------------------------------------------
     KINDS = ("x_forward", "y_forward", "z_pass", "y_inverse", "x_inverse", "other", "yz_forward", "zy_adjoint",
              "objective")

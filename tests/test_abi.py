@@ -33,3 +33,34 @@ def test_null_handles_are_rejected(lib):
     assert L.tm_create(None, 0) == -1
     assert L.tm_set_grid(None, lib.c_int3(8, 8, 8), 8, lib.c_double3(1, 1, 1)) == -1
     assert L.tm_last_error(None) == b"null context"
+
+
+def test_fault_injection_hook_without_a_gpu(lib):
+    """The nth call of the armed entry point fails with TM_ERR_INJECTED before any work;
+    the calls around it behave as without the hook (here: a null context, TM_ERR_ARG)."""
+    L = lib.lib()
+    assert L.tm_inject_fault(b"tm_set_penalty", 2) == 0
+    codes = [L.tm_set_penalty(None, 3.0) for _ in range(4)]
+    assert codes == [-1, -7, -1, -1]
+    L.tm_inject_fault(b"tm_set_penalty", 1)
+    assert L.tm_set_fused(None, 1) == -1  # another entry point: not armed
+    assert L.tm_set_penalty(None, 3.0) == -7
+    L.tm_inject_fault(b"tm_set_penalty", 3)
+    L.tm_inject_fault(None, 0)  # disarmed
+    assert [L.tm_set_penalty(None, 3.0) for _ in range(4)] == [-1] * 4
+
+
+def test_fault_injection_from_the_environment(lib):
+    """TM_FAULT_INJECT=<call>:<nth> arms the hook when the library loads (a fresh process)."""
+    import os
+    import subprocess
+    import sys
+
+    code = ("import ctypes, sys; L = ctypes.CDLL(sys.argv[1]); "
+            "L.tm_set_penalty.argtypes = [ctypes.c_void_p, ctypes.c_double]; "
+            "print([L.tm_set_penalty(None, 3.0) for _ in range(3)])")
+    env = dict(os.environ, TM_FAULT_INJECT="tm_set_penalty:3")
+    out = subprocess.run([sys.executable, "-c", code, lib.LIB_PATH], env=env, capture_output=True, text=True,
+                         timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "[-1, -1, -7]"
