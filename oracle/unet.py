@@ -14,6 +14,16 @@ Architecture (channels-last arrays [N][D][H][W][C]):
     rho0 = sigmoid(d1 . w_head + b_head);  loss = mean (rho0 - target)^2
 conv: 3x3x3, zero padding 1, weights [27][Cin][Cout] with tap = (dz+1)*9+(dy+1)*3+(dx+1);
 pool: 2x2x2 mean; up: nearest 2x.
+
+Two precisions, both from the network's definition ("bfloat16 weights, float32
+accumulation"):
+* q = None: every value in float64 (the exact network for the given weights);
+* q = a rounding to bfloat16: every product of a convolution takes bfloat16
+  operands -- the weights, the layer inputs (so the activations handed from layer
+  to layer are bfloat16) and, in the backward pass, the output gradient in both
+  the data-gradient and the weight-gradient product -- while every sum is exact
+  and the element-wise steps (bias, ReLU and its mask, pooling, upsampling, the
+  head, the bias gradient) act on unrounded values.
 """
 
 import numpy as np
@@ -38,8 +48,8 @@ def conv(x, W, b):
 
 
 def conv_backward(x, W, g, q=None):
-    """(dx, dW, db) of conv(x, W, b) for the output gradient g; q, if given, is applied to g
-    before the data and the weight gradient (a storage precision), not before db."""
+    """(dx, dW, db) of conv(x, W, b) for the output gradient g; q, if given, rounds g where
+    it is an operand of a product (the data and the weight gradient), not in the sum db."""
     gq = q(g) if q is not None else g
     dW = np.stack([np.einsum("nzyxi,nzyxo->io", _shift(x, dz, dy, dx), gq) for (dz, dy, dx) in TAPS])
     db = g.sum(axis=(0, 1, 2, 3))
@@ -73,8 +83,8 @@ def relu(x):
 
 def forward(params, x, q=None):
     """Returns (rho0, cache). params: {name: (W, b)} for LAYERS and 'head': (w[16], b[1]).
-    q, if given, rounds every stored activation (conv and pool outputs) to a storage precision;
-    without it the whole network is float64."""
+    q, if given, rounds every activation that becomes a convolution's input (conv and pool
+    outputs) to the product-operand precision; without it the whole network is float64."""
     c = {"x": x}
     q = q if q is not None else (lambda a: a)
 
@@ -102,7 +112,7 @@ def forward(params, x, q=None):
 
 def loss_and_grads(params, x, target, q=None):
     """(loss, grads) of mean (rho0 - target)^2; q as in forward(), also applied to each output
-    gradient before it enters a data- or weight-gradient product."""
+    gradient where it enters a data- or weight-gradient product."""
     rho, c = forward(params, x, q)
     n = rho.size
     loss = float(np.mean((rho - target) ** 2))

@@ -69,7 +69,13 @@ struct tm_ctx {
   float2* yzpart = nullptr;        // [z chunks][Ly][P] partial planes of the fused forward
   int yzpart_chunks = 0;
   float2* yzseg = nullptr;         // [2 * SMs][Ly][TB] segment partials of the flattened fused forward
-  unsigned* yzcnt = nullptr;       // [P / TB] item counters of the flattened fused forward
+  // one tensor component times its coupling coefficient, for the fused forward (0) and
+  // adjoint (1): [nz][Ly/2+1][P], rebuilt when the component, the coefficient or the tensor change
+  float* Ts[2] = {nullptr, nullptr};
+  int Ts_comp[2] = {-1, -1};
+  float Ts_coef[2] = {0.0f, 0.0f};
+  long long Ts_gen[2] = {-1, -1};
+  long long tensor_gen = 0;        // counts tm_set_tensor calls
   int nsm = 0;
   int* ext = nullptr;       // [2]: z range of the target planes
   double* stats = nullptr;  // [2 * kStatBlocks + 2] scratch of tm_iteration_stats
@@ -195,8 +201,11 @@ void free_grid(tm_ctx* c) {
   c->yzpart_chunks = 0;
   cudaFree(c->yzseg);
   c->yzseg = nullptr;
-  cudaFree(c->yzcnt);
-  c->yzcnt = nullptr;
+  for (int k = 0; k < 2; k++) {
+    cudaFree(c->Ts[k]);
+    c->Ts[k] = nullptr;
+    c->Ts_comp[k] = -1;
+  }
   cudaFree(c->sH);
   cudaFree(c->sgH);
   c->sH = c->sgH = nullptr;
@@ -440,6 +449,26 @@ int zdirect(tm_ctx* ctx, const ConvSpec& cs, int zi0, int nzi, int zo0, int nzo,
   return TM_OK;
 }
 
+// Tensor component c times coef, [nz][Ly/2+1][P], for the fused kernel `which` (0 forward,
+// 1 adjoint); kept until the component, the coefficient or the tensor change. *rebuilt:
+// it was (re)computed on the stream just now, so the next launch must not overlap it.
+int scaled_component(tm_ctx* ctx, int which, int c, float coef, cudaStream_t s, const float** out, bool* rebuilt) {
+  *rebuilt = false;
+  const long long n = (long long)ctx->nz * (ctx->L[1] / 2 + 1) * ctx->P;
+  if (!ctx->Ts[which]) CK(cudaMalloc(&ctx->Ts[which], n * sizeof(float)));
+  if (ctx->Ts_comp[which] != c || ctx->Ts_coef[which] != coef || ctx->Ts_gen[which] != ctx->tensor_gen) {
+    CKL(launch_scale(ctx->Ts[which], ctx->Tz + c * n, n, coef, s));
+    *rebuilt = true;
+    ctx->Ts_comp[which] = c;
+    ctx->Ts_coef[which] = coef;
+    ctx->Ts_gen[which] = ctx->tensor_gen;
+  }
+  *out = ctx->Ts[which];
+  return TM_OK;
+}
+
+int one_component(int need) { return (need != 0 && (need & (need - 1)) == 0) ? __builtin_ctz(need) : -1; }
+
 // forward y transform of the design planes fused with the direct z sum onto the
 // single target plane (cs.nout == 1); *yinv_done: the kernel also wrote the target
 // plane's inverse y transform into A
@@ -484,13 +513,15 @@ int yz_forward(tm_ctx* ctx, const ConvSpec& cs, int zo, cudaStream_t s, bool* yi
   y.zchunk = zchunk;
   y.zout = zo;
   y.tw = ctx->tw + ctx->L[0];
-  if (!ctx->yzseg) {
-    CK(cudaMalloc(&ctx->yzseg, (size_t)2 * ctx->nsm * Ly * TB * sizeof(float2)));
-    CK(cudaMalloc(&ctx->yzcnt, (size_t)chunks * sizeof(unsigned)));
-    CK(cudaMemsetAsync(ctx->yzcnt, 0, (size_t)chunks * sizeof(unsigned), s));
-  }
+  if (!ctx->yzseg) CK(cudaMalloc(&ctx->yzseg, (size_t)2 * ctx->nsm * Ly * TB * sizeof(float2)));
   y.seg = ctx->yzseg;
-  y.cnt = ctx->yzcnt;
+  const int c1 = cs.nin == 1 ? one_component(y.need[0]) : -1;
+  if (c1 >= 0) {
+    int r;
+    bool rebuilt;
+    if ((r = scaled_component(ctx, 0, c1, y.coef[0][c1], s, &y.Ts, &rebuilt))) return r;
+    y.nz_total = ctx->nz;
+  }
   y.status = ctx->dstat;
   y.yrows = ctx->A + cs.aout[0] * ((long long)ctx->nz * ctx->ny * P) + (long long)zo * ctx->ny * P;
   y.pdl = ctx->pdl;
@@ -538,6 +569,16 @@ int zy_adjoint(tm_ctx* ctx, const ConvSpec& cs, int zi0, int nzi, cudaStream_t s
   z.status = ctx->dstat;
   z.zero_word = ctx->gmax;  // cleared for the chain-rule pass that follows (saves a memset between kernels)
   z.pdl = ctx->pdl;
+  const int c1 = cs.nin == 1 && cs.nout == 1 ? one_component(z.need[0][0]) : -1;
+  if (c1 >= 0) {
+    int r;
+    bool rebuilt;
+    if ((r = scaled_component(ctx, 1, c1, z.coef[0][0][c1], s, &z.Ts, &rebuilt))) return r;
+    z.nzin_total = ctx->nz;
+    // the adjoint reads its first tensor slice before it waits for the preceding kernel:
+    // after a rebuild it must start only once the scaling kernel has finished
+    if (rebuilt) z.pdl = 0;
+  }
   Timed t(ctx, KIND_ZYA, s);
   const int r = launch_zy_adj(Ly, z, s);
   if (r < 0) CKL(r);
@@ -793,6 +834,7 @@ int tm_set_tensor(tm_ctx* ctx, void* stream) {
                        nullptr, S(stream), ctx->err, sizeof(ctx->err));
   if (r != 0) return TM_ERR_CUDA;
   ctx->have_tensor = true;
+  ctx->tensor_gen++;
   return TM_OK;
 }
 

@@ -133,6 +133,96 @@ struct Dft<T, 3, INV> {
 };
 
 // ---------------------------------------------------------------------------
+// The radix-2 DFTs again (float only), with every butterfly whose twiddle is not 1 or
+// -+i in fused multiply-adds: lo = a + W b in four FMAs and hi = a - W b as 2 a - lo in
+// two, six instructions where the plain form takes eight (four for W b, four for the
+// sum and difference). hi then carries the rounding error of lo with the opposite sign,
+// a few float32 ulps more per transform. The compute-bound fused y/z kernels use them.
+template <bool INV>
+__device__ __forceinline__ void bfly_tw(cx<float>& lo, cx<float>& hi, cx<float> a, cx<float> b, int m) {
+  // W = exp(-2 pi i / 32) forward, exp(+2 pi i / 32) inverse; m in [0, 16)
+  if (m == 0) {
+    lo = a + b;
+    hi = a - b;
+    return;
+  }
+  if (m == 8) {
+    const cx<float> t = INV ? mk(-b.y, b.x) : mk(b.y, -b.x);
+    lo = a + t;
+    hi = a - t;
+    return;
+  }
+  const float c = float(cos32(m)), s = INV ? -float(sin32(m)) : float(sin32(m));
+  lo.x = __fmaf_rn(b.y, s, __fmaf_rn(b.x, c, a.x));   // a.x + (W b).x
+  lo.y = __fmaf_rn(-b.x, s, __fmaf_rn(b.y, c, a.y));  // a.y + (W b).y
+  hi.x = __fmaf_rn(2.0f, a.x, -lo.x);
+  hi.y = __fmaf_rn(2.0f, a.y, -lo.y);
+}
+// a + W^m b only (the lower half of a butterfly)
+template <bool INV>
+__device__ __forceinline__ cx<float> bfly_lo(cx<float> a, cx<float> b, int m) {
+  if (m == 0) return a + b;
+  if (m == 8) return a + (INV ? mk(-b.y, b.x) : mk(b.y, -b.x));
+  const float c = float(cos32(m)), s = INV ? -float(sin32(m)) : float(sin32(m));
+  return mk(__fmaf_rn(b.y, s, __fmaf_rn(b.x, c, a.x)), __fmaf_rn(-b.x, s, __fmaf_rn(b.y, c, a.y)));
+}
+
+template <int N, bool INV>
+struct DftF {
+  static __device__ __forceinline__ void run(cx<float>* v) {
+    static_assert(N == 2 || N == 4 || N == 8 || N == 16 || N == 32, "radix");
+    cx<float> e[N / 2], o[N / 2];
+#pragma unroll
+    for (int i = 0; i < N / 2; i++) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    DftF<N / 2, INV>::run(e);
+    DftF<N / 2, INV>::run(o);
+#pragma unroll
+    for (int k = 0; k < N / 2; k++) bfly_tw<INV>(v[k], v[k + N / 2], e[k], o[k], k * (32 / N));
+  }
+};
+template <bool INV>
+struct DftF<1, INV> {
+  static __device__ __forceinline__ void run(cx<float>*) {}
+};
+
+// Outputs 0 .. N/2 - 1 only (an inverse transform whose upper half is cropped).
+template <int N, bool INV>
+__device__ __forceinline__ void dft_low_half(cx<float>* v) {
+  cx<float> e[N / 2], o[N / 2];
+#pragma unroll
+  for (int i = 0; i < N / 2; i++) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  DftF<N / 2, INV>::run(e);
+  DftF<N / 2, INV>::run(o);
+#pragma unroll
+  for (int k = 0; k < N / 2; k++) v[k] = bfly_lo<INV>(e[k], o[k], k * (32 / N));
+}
+
+// 32-point DFT of inputs 0 .. 15 (inputs 16 .. 31 zero, a zero-padded transform):
+// X[2m] = DFT16(x)[m] and X[2m+1] = DFT16(x[n] W32^n)[m]. v[0..15] in, v[0..31] out.
+template <bool INV>
+__device__ __forceinline__ void dft32_half_input(cx<float>* v) {
+  cx<float> a[16], b[16];
+#pragma unroll
+  for (int n = 0; n < 16; n++) {
+    a[n] = v[n];
+    b[n] = tw32<float, INV>(v[n], n);
+  }
+  DftF<16, INV>::run(a);
+  DftF<16, INV>::run(b);
+#pragma unroll
+  for (int m = 0; m < 16; m++) {
+    v[2 * m] = a[m];
+    v[2 * m + 1] = b[m];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Plans: L = 2^a 3^b. The power-of-two part is one stage (when b > 0 and
 // a <= 5) or two near-equal stages; then b radix-3 stages. Every plan has at
 // least two stages.

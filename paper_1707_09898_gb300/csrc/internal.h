@@ -178,6 +178,9 @@ struct ZYArgs {
   long long Tc, Tdz;
   int zin0, nzin, zout0, nzout;
   const float2* tw;                         // W_Ly
+  // warp-specialized path (one tensor component c): Ts = coef[0][0][c] * Tz[c], [nzin_total][Ly/2+1][P]
+  const float* Ts;
+  int nzin_total;                           // z offsets held by Ts
   unsigned* status;                         // device word: bit 0 set when a copy wait timed out
   unsigned* zero_word;                      // if set, zeroed by the warp-specialized kernel (launch_zy_adj returns 1)
   int pdl;                                  // launch with programmatic dependent launch
@@ -199,12 +202,13 @@ struct YZArgs {
   int zin0, nzin, zchunk, zout;
   const float2* tw;
   // single-component path on two-stage plans (when set): per-block segment partials
-  // [2 * blocks][Ly][TB], per-column-block item counters (zero between launches), and the
-  // target plane's rows in A [ny][P]; launch_yz_fwd then also writes the inverse y
-  // transform of the target plane there and returns 1
+  // [2 * blocks][Ly][TB], the target plane's rows in A [ny][P], and the tensor component
+  // scaled by its coefficient, Ts = coef[0][c] * Tz[c] [nz_total][Ly/2+1][P]; launch_yz_fwd
+  // then also writes the inverse y transform of the target plane there and returns 1
   float2* seg;
-  unsigned* cnt;
   float2* yrows;
+  const float* Ts;
+  int nz_total;
   unsigned* status;                         // device word: bit 0 set when a copy wait timed out
   int pdl;                                  // launch with programmatic dependent launch
 };
@@ -234,6 +238,8 @@ int launch_absmax(const float* G, long long n, unsigned int* gmax, cudaStream_t 
 int launch_mask_extent(const uint8_t* mask, int nz, long long plane, int* ext, cudaStream_t s);
 int launch_update(float* rho, const float* G, long long n, float alpha, int normalize, const unsigned int* gmax,
                   cudaStream_t s);
+// dst[i] = coef * src[i] (float32 products)
+int launch_scale(float* dst, const float* src, long long n, float coef, cudaStream_t s);
 
 // Validation, per-iteration statistics, wait self-test -- misc.cu
 // count of entries that are NaN or outside [0, 1] into *bad (zeroed by the caller)

@@ -308,9 +308,9 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_staged(YZArgs a, int c) {
 
 // ---------------------------------------------------------------------------
 // Warp-specialized versions of the two single-component kernels for two-stage plans
-// whose first stage has kNT units and whose last stage has 2 kNT (L = 512): a block of
-// 512 threads runs two groups of eight warps on one plane each, a plane apart, with a
-// tile per group and one block barrier per plane:
+// whose first stage has kNT units and whose last stage has 2 kNT (L = 512 = 32 x 16): a
+// block of 512 threads runs two groups of eight warps on one plane each, a plane apart,
+// with a tile per group and one block barrier per plane:
 //   forward: the "transform" warps take the input rows of plane z + 1 (loaded into
 //            registers a round ahead) and run the first DIF stage into one tile while
 //            the "accumulate" warps finish plane z from the other tile (the last stage
@@ -319,45 +319,49 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_staged(YZArgs a, int c) {
 //            registers per column block) for plane z + 1 and run the first inverse
 //            stage into one tile while the "store" warps finish plane z from the other
 //            tile and write its rows.
-// The tensor slices arrive in shared memory by TMA (two boxes per slice, mbarrier
-// completion) a round ahead. C is the tensor component, so the sign rules of
-// the folded tensor are resolved at compile time; the positions of the last stage are
-// g R1 + q with frequency ky = g + q L/R1, so the tensor row of every element is a
-// compile-time offset from one of two per-thread bases.
+// The (column block, plane) items are spread evenly over one block per SM, z fastest;
+// each block follows its item's column block and plane by increments (no divisions in
+// the loop). The tensor slices arrive in shared memory by TMA (two boxes per slice,
+// mbarrier completion) a round ahead, from a copy of the one tensor component C with
+// the coupling coefficient already multiplied in (s = coef N^_C, the same float32
+// products as multiplying in the kernel). C fixes the sign rules of the folded tensor at
+// compile time; the positions of the last stage are g R1 + q with frequency
+// ky = g + q L/R1, so the tensor row of every element is a compile-time offset from one
+// of two per-thread bases. The first stage of the forward transform skips the zero
+// half of its inputs (rows y >= L/2) and the last stage of the inverse computes only
+// the rows y < L/2 it keeps; both stages' radix-2 butterflies run in fused
+// multiply-adds (DftF). FULL: every row y < L/2 is valid (n = L/2), no predicates.
 template <int L>
 __host__ __device__ constexpr bool yz_ws_plan() {
-  return plan_stages(L) == 2 && StageShape<L, 0>::NU == kNT && StageShape<L, 1>::NU == 2 * kNT;
+  return plan_stages(L) == 2 && StageShape<L, 0>::NU == kNT && StageShape<L, 1>::NU == 2 * kNT &&
+         StageShape<L, 0>::R == 2 * TB && StageShape<L, 0>::M == TB && StageShape<L, 1>::R == TB;
 }
 
 constexpr int kBarAll = 1, kBarGroup = 2;  // named barriers (0 is __syncthreads)
 
-// tensor factor of last-stage element q of group g, C's sign rules applied;
-// tlo = slice + g TB + line (rows g + q L/R1), thi = slice + (L - g) TB + line
+// tensor factor of last-stage element q of group g from the scaled slice, with C's sign
+// rules: odd in ky for xy and yz (C = 3, 5), odd in dz for xz and yz (C = 4, 5; neg means
+// dz < 0); tlo = slice + g TB + line (rows g + q L/R1), thi = slice + (L - g) TB + line
 template <int L, int C>
-__device__ __forceinline__ float ws_tensor(const float* tlo, const float* thi, int g, int q, float cz) {
+__device__ __forceinline__ float ws_tensor(const float* tlo, const float* thi, int g, int q, bool neg) {
   constexpr int R1 = StageShape<L, 1>::R, QS = L / R1;
-  float f = cz * (q < R1 / 2 ? tlo[q * QS * TB] : thi[-q * QS * TB]);
+  const float f = q < R1 / 2 ? tlo[q * QS * TB] : thi[-q * QS * TB];
+  bool flip = C >= 4 && neg;
   // ky = g + q QS lies above L/2 for q > R1/2, and for q = R1/2 unless g = 0
   if constexpr (C == 3 || C == 5) {
-    if (q > R1 / 2 || (q == R1 / 2 && g > 0)) f = -f;
+    if (q > R1 / 2 || (q == R1 / 2 && g > 0)) flip = !flip;
   }
-  return f;
+  return flip ? -f : f;
 }
 template <int C>
 __device__ __forceinline__ cx<float> ws_apply(float f, cx<float> v) {  // (-i f) v for xz, yz
   return C >= 4 ? mk(f * v.y, -f * v.x) : mk(f * v.x, f * v.y);
 }
-template <int L, int C>
-__device__ __forceinline__ cx<float> ws_tensor_apply(const float* tlo, const float* thi, int g, int q, float cz,
-                                                     cx<float> v) {
-  return ws_apply<C>(ws_tensor<L, C>(tlo, thi, g, q, cz), v);
-}
 
 // The stage-0 twiddle of position j + q M0 (= g R1 + q' with j = q', q = g) is W^(j q),
 // applied after the first DIF stage or before the last DIT stage. The two groups share
 // that work: the stage-0 warps take q < R0/2, the last-stage warps (their second unit,
-// g >= R0/2) the rest, with the same product on the same operands as the single-stage
-// rule (apply_twiddles), so results are unchanged bit for bit.
+// g >= R0/2) the rest.
 template <int L, bool INV>
 __device__ __forceinline__ void twiddles_lo(cx<float>* v, int j, const cx<float>* tw) {
   constexpr int R0 = StageShape<L, 0>::R;
@@ -387,43 +391,51 @@ static_assert((slice_box_rows<512>() * TB * sizeof(float)) % 128 == 0, "128-byte
 static_assert((512 + 2 * 512 * TB) * sizeof(float2) % 128 == 0, "128-byte aligned TMA destinations");
 // 128 bytes of slack to align the dynamic buffer for the TMA destinations; mbarriers last
 template <int L>
-constexpr size_t fwd_ws_smem() {
+constexpr size_t ws_smem() {
   return 128 + (size_t)(L + 2 * L * TB) * sizeof(float2) + (size_t)2 * slice_rows<L>() * TB * sizeof(float) +
          2 * sizeof(unsigned long long);
 }
 
+// (column block, plane) of an item index i, planes z0 .. z0 + nz - 1 per column block,
+// and the step to the next item
+struct Item {
+  int cb, z;
+};
+__device__ __forceinline__ Item item_of(long long i, int z0, int nz) {
+  const int cb = (int)(i / nz);
+  return {cb, z0 + (int)(i - (long long)cb * nz)};
+}
+__device__ __forceinline__ Item next_item(Item it, int z0, int nz) {
+  return it.z + 1 == z0 + nz ? Item{it.cb + 1, z0} : Item{it.cb, it.z + 1};
+}
+
 // Forward, flattened: block b transforms the (column block, design plane) items
-// [T b / B, T (b + 1) / B), T = (P / TB) nzin, z fastest, so that every SM holds one block
-// with the same share of the work. The sums of a column block are flushed as a segment
-// partial after the block's last item of it (at most two segments per block, as long as
-// B >= P / TB); each segment adds its item count to the column block's counter, and the
-// block whose segment completes the nzin items sums that column block's segments in
-// block order, writes the target plane's spectrum into B and runs the inverse y
-// transform of the target plane on it (rows y < ny into A), then re-arms the counter.
-template <int L, int C>
+// [T b / B, T (b + 1) / B), T = (P / TB) nzin. The sums of a column block are written as
+// a segment partial after the block's last item of it (at most two segments per block,
+// as long as B >= P / TB); k_yz_finish adds the segments of each column block in block
+// order and runs the target plane's inverse y transform.
+template <int L, int C, bool FULL>
 __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a, const __grid_constant__ CUtensorMap mslice) {
   using S0 = StageShape<L, 0>;
   using S1 = StageShape<L, 1>;
   constexpr int R0 = S0::R, M0 = S0::M, R1 = S1::R, KS = slice_rows<L>(), KB = slice_box_rows<L>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int fin[2];
   unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);  // TMA destinations
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
   cx<float>* tiles = tw + L;                                      // [2][L][TB]
   float* stt0 = reinterpret_cast<float*>(tiles + 2 * L * TB);     // [2][KS][TB] tensor slices
   unsigned long long* mb = reinterpret_cast<unsigned long long*>(stt0 + 2 * KS * TB);  // slice 0, slice 1
   load_twiddles<float, NTF>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
-  if (threadIdx.x < 2) fin[threadIdx.x] = -1;
   if (threadIdx.x == 0) {
     mbar_init(mb, 1);
     mbar_init(mb + 1, 1);
     mbar_init_fence();
   }
-  pdl_wait();  // the x spectra, the counters and the outputs belong to earlier kernels
+  pdl_wait();  // the x spectra and the segment buffer belong to earlier kernels
   const long long T = (long long)(a.P / TB) * a.nzin;
-  const int i0 = (int)(T * blockIdx.x / gridDim.x), i1 = (int)(T * (blockIdx.x + 1) / gridDim.x);
-  const int n = i1 - i0;
-  const int cb0 = i0 / a.nzin;  // column block of segment 0
+  const long long i0 = T * blockIdx.x / gridDim.x, i1 = T * (blockIdx.x + 1) / gridDim.x;
+  const int n = (int)(i1 - i0);
+  const Item first = item_of(i0, a.zin0, a.nzin);
   __syncthreads();
   if (threadIdx.x < kNT) {
     // transform warps: stage 0 of item i0 + r in round r, its 16 input values per thread
@@ -434,40 +446,35 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a, const __grid_con
     const cx<float>* in0 =
         reinterpret_cast<const cx<float>*>(a.in) + a.in_slot[0] * a.in_cstride + (long long)j * a.P + line;
     cx<float> pre[R0 / 2];  // rows j + q M0 (q < R0/2; n_in <= L/2) of the next item
-    auto fetch = [&](int cb, int z) {
-      const cx<float>* src = in0 + z * a.in_zstride + cb * TB;
+    auto fetch = [&](Item it) {
+      const cx<float>* src = in0 + it.z * a.in_zstride + it.cb * TB;
 #pragma unroll
-      for (int q = 0; q < R0 / 2; q++) pre[q] = j + q * M0 < a.n_in ? src[(long long)q * M0 * a.P] : zero<float>();
+      for (int q = 0; q < R0 / 2; q++)
+        pre[q] = (FULL || j + q * M0 < a.n_in) ? src[(long long)q * M0 * a.P] : zero<float>();
     };
-    auto issue_slice = [&](int cb, int z, int buf) {
-      const int dz = a.zout - z, adz = dz < 0 ? -dz : dz;
-      const int y = (int)((C * a.Tc + adz * a.Tdz) / a.P);
+    auto issue_slice = [&](Item it, int buf) {
+      const int dz = a.zout - it.z, adz = dz < 0 ? -dz : dz;
       float* stt = stt0 + buf * KS * TB;
       mbar_expect_tx(mb + buf, 2 * KB * TB * (int)sizeof(float));
-      tma_load_2d(stt, &mslice, cb * TB, y, mb + buf);
-      tma_load_2d(stt + KB * TB, &mslice, cb * TB, y + KB, mb + buf);
+      tma_load_2d(stt, &mslice, it.cb * TB, adz * (L / 2 + 1), mb + buf);
+      tma_load_2d(stt + KB * TB, &mslice, it.cb * TB, adz * (L / 2 + 1) + KB, mb + buf);
     };
-    // (column block, plane) of the current item and of the next one
-    int cb = cb0, z = a.zin0 + (i0 - cb0 * a.nzin);
-    int cbn = z + 1 == a.zin0 + a.nzin ? cb + 1 : cb, zn = z + 1 == a.zin0 + a.nzin ? a.zin0 : z + 1;
-    if (n > 0) fetch(cb, z);
+    Item cur = first;
+    if (n > 0) fetch(cur);
     for (int r = 0; r <= n; r++) {
       if (r < n) {
         cx<float> v[R0];
 #pragma unroll
         for (int q = 0; q < R0 / 2; q++) v[q] = pre[q];
-#pragma unroll
-        for (int q = R0 / 2; q < R0; q++) v[q] = zero<float>();
-        if (r + 1 < n) fetch(cbn, zn);
+        const Item nxt = next_item(cur, a.zin0, a.nzin);
+        if (r + 1 < n) fetch(nxt);
         if (t == 0) {
+          if (r == 0) fence_proxy_async_global();  // the scaled tensor was written by ordinary stores
           fence_proxy_async_smem();  // the other group read this slice buffer a round ago
-          issue_slice(cb, z, r & 1);
+          issue_slice(cur, r & 1);
         }
-        cb = cbn;
-        z = zn;
-        cbn = z + 1 == a.zin0 + a.nzin ? cb + 1 : cb;
-        zn = z + 1 == a.zin0 + a.nzin ? a.zin0 : z + 1;
-        Dft<float, R0, false>::run(v);
+        cur = nxt;
+        dft32_half_input<false>(v);
         twiddles_lo<L, false>(v, j, tw);  // q >= R0/2: applied by the accumulate warps
         cx<float>* tile = tiles + (r & 1) * L * TB;
 #pragma unroll
@@ -478,18 +485,15 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a, const __grid_con
   } else {
     // accumulate warps: last stage of item i0 + r - 1 in round r, times s, into the sums
     const int t = threadIdx.x - kNT;
-    const float coef = a.coef[0][C];
     cx<float> acc[2][R1];
 #pragma unroll
     for (int it = 0; it < 2; it++)
 #pragma unroll
       for (int q = 0; q < R1; q++) acc[it][q] = zero<float>();
-    int cb = cb0, z = a.zin0 + (i0 - cb0 * a.nzin);  // the item of the next round
+    Item cur = first;  // the item of the next round
     for (int r = 0; r <= n; r++) {
       if (r >= 1) {
-        const int i = i0 + r - 1;
-        const int dz = a.zout - z;
-        const float cz = (C >= 4 && dz < 0) ? -coef : coef;
+        const bool neg = a.zout - cur.z < 0;
         const cx<float>* tile = tiles + ((r - 1) & 1) * L * TB;
         const float* stt = stt0 + ((r - 1) & 1) * KS * TB;
         mbar_wait(mb + ((r - 1) & 1), ((r - 1) >> 1) & 1, a.status);  // its tensor slice
@@ -500,15 +504,15 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a, const __grid_con
 #pragma unroll
           for (int q = 0; q < R1; q++) v[q] = tile[(g * R1 + q) * TB + line];
           if (it == 1) twiddles_hi<L, false>(v, g, tw);  // stage-0 twiddles of g >= R0/2
-          Dft<float, R1, false>::run(v);
+          DftF<R1, false>::run(v);
           const float* tlo = stt + g * TB + line;
           const float* thi = stt + (L - g) * TB + line;
 #pragma unroll
-          for (int q = 0; q < R1; q++) acc[it][q] = acc[it][q] + ws_tensor_apply<L, C>(tlo, thi, g, q, cz, v[q]);
+          for (int q = 0; q < R1; q++) acc[it][q] = acc[it][q] + ws_apply<C>(ws_tensor<L, C>(tlo, thi, g, q, neg), v[q]);
         }
-        const bool last = z + 1 == a.zin0 + a.nzin;  // the last plane of column block cb
-        if (i + 1 == i1 || last) {  // the block's last item of column block cb
-          const int sg = cb == cb0 ? 0 : 1;
+        const bool last = cur.z + 1 == a.zin0 + a.nzin;  // the last plane of column block cur.cb
+        if (r == n || last) {  // the block's last item of column block cur.cb
+          const int sg = cur.cb == first.cb ? 0 : 1;
           cx<float>* seg = reinterpret_cast<cx<float>*>(a.seg) + (long long)(blockIdx.x * 2 + sg) * L * TB;
 #pragma unroll
           for (int it = 0; it < 2; it++) {
@@ -519,95 +523,80 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a, const __grid_con
               acc[it][q] = zero<float>();
             }
           }
-          __threadfence();
-          bar_named(kBarGroup + 1, kNT);  // every accumulate thread's partial is written and fenced
-          if (t == 0) {
-            const int cnt = i + 1 - max(i0, cb * a.nzin);
-            if ((int)atomicAdd(a.cnt + cb, (unsigned)cnt) + cnt == a.nzin) fin[sg] = cb;
-          }
         }
-        if (last) {
-          cb++;
-          z = a.zin0;
-        } else {
-          z++;
-        }
+        cur = next_item(cur, a.zin0, a.nzin);
       }
       bar_named(kBarAll, NTF);
     }
   }
-  __syncthreads();
-  for (int sg = 0; sg < 2; sg++) {
-    const int cb = fin[sg];
-    if (cb < 0) continue;
-    // this block completed column block cb: sum its segments in block order
-    __threadfence();
-    const int B = gridDim.x;
-    const long long x0 = (long long)cb * a.nzin, x1 = x0 + a.nzin - 1;  // first and last item of cb
-    const int b_lo = (int)(((x0 + 1) * B - 1) / T), b_hi = (int)(((x1 + 1) * B - 1) / T);
-    const cx<float>* segs = reinterpret_cast<const cx<float>*>(a.seg);
-    cx<float>* tile = tiles;
-    cx<float>* bplane =
-        reinterpret_cast<cx<float>*>(a.out) + a.out_slot * a.out_cstride + (long long)a.zout * L * a.P + cb * TB;
-    static_assert((L * TB) % NTF == 0, "elements per thread");
-    constexpr int NE = L * TB / NTF;
-    cx<float> acc[NE];
-#pragma unroll
-    for (int k = 0; k < NE; k++) acc[k] = zero<float>();
-    for (int b = b_lo; b <= b_hi; b++) {  // a segment's loads are all in flight together
-      const int sgb = (int)(T * b / B) / a.nzin == cb ? 0 : 1;
-      const float2* sp = reinterpret_cast<const float2*>(segs + (long long)(b * 2 + sgb) * L * TB) + threadIdx.x;
-      float2 v[NE];
-#pragma unroll
-      for (int k = 0; k < NE; k++) v[k] = __ldcg(sp + k * NTF);
-#pragma unroll
-      for (int k = 0; k < NE; k++) acc[k] = acc[k] + mk(v[k].x, v[k].y);
-    }
-#pragma unroll
-    for (int k = 0; k < NE; k++) {
-      const int e = threadIdx.x + k * NTF;
-      tile[e] = acc[k];
-      bplane[(long long)(e / TB) * a.P + (e % TB)] = acc[k];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) a.cnt[cb] = 0u;
-    {  // first inverse stage (last plan stage, positions g R1 + q), 2 kNT units
-      const int u = threadIdx.x, line = u % TB, g = u / TB;
-      cx<float> v[R1];
-#pragma unroll
-      for (int q = 0; q < R1; q++) v[q] = tile[(g * R1 + q) * TB + line];
-      Dft<float, R1, true>::run(v);
-#pragma unroll
-      for (int q = 0; q < R1; q++) tile[(g * R1 + q) * TB + line] = v[q];
-    }
-    __syncthreads();
-    if (threadIdx.x < kNT) {  // last inverse stage (plan stage 0), rows y < ny out
-      const int line = threadIdx.x % TB, j = threadIdx.x / TB;
-      cx<float> v[R0];
-#pragma unroll
-      for (int q = 0; q < R0; q++) v[q] = tile[(j + q * M0) * TB + line];
-      apply_twiddles<float, L, 0, true>(v, j, tw);
-      Dft<float, R0, true>::run(v);
-      cx<float>* o = reinterpret_cast<cx<float>*>(a.yrows) + cb * TB + line;
-#pragma unroll
-      for (int q = 0; q < R0; q++) {
-        const int y = j + q * M0;
-        if (y < a.n_in) o[(long long)y * a.P] = v[q];
-      }
-    }
-    __syncthreads();
-  }
 }
 
+// The target plane after the forward: for column block cb (blockIdx.x), the segment
+// partials of the blocks that held its items, added in block order, then its inverse y
+// transform (the inverse of the two DIF stages) into rows y < n_in of A. Each block takes
+// FL of the column block's TB lines (blockIdx.y).
+constexpr int kFinishLines = 2;
 template <int L>
-constexpr size_t adj_ws_smem() {
-  return 128 + (size_t)(L + 2 * L * TB) * sizeof(float2) + (size_t)2 * slice_rows<L>() * TB * sizeof(float) +
-         2 * sizeof(unsigned long long);
+__global__ void __launch_bounds__(128) k_yz_finish(YZArgs a, int B) {
+  using S0 = StageShape<L, 0>;
+  using S1 = StageShape<L, 1>;
+  constexpr int R0 = S0::R, M0 = S0::M, R1 = S1::R, FL = kFinishLines, NE = L * FL / 128;
+  __shared__ cx<float> tw[L];
+  __shared__ cx<float> tile[L * FL];
+  load_twiddles<float, 128>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
+  pdl_wait();  // the segment partials come from the forward kernel
+  const int cb = blockIdx.x, l0 = blockIdx.y * FL;
+  const long long T = (long long)(a.P / TB) * a.nzin;
+  const long long x0 = (long long)cb * a.nzin, x1 = x0 + a.nzin - 1;  // first and last item of cb
+  const int b_lo = (int)(((x0 + 1) * B - 1) / T), b_hi = (int)(((x1 + 1) * B - 1) / T);
+  const cx<float>* segs = reinterpret_cast<const cx<float>*>(a.seg);
+  cx<float> acc[NE];
+#pragma unroll
+  for (int k = 0; k < NE; k++) acc[k] = zero<float>();
+  for (int b = b_lo; b <= b_hi; b++) {  // a segment's loads are all in flight together
+    const int sgb = (int)((T * b / B) / a.nzin) == cb ? 0 : 1;
+    const cx<float>* sp = segs + (long long)(b * 2 + sgb) * L * TB + l0;
+    cx<float> v[NE];
+#pragma unroll
+    for (int k = 0; k < NE; k++) {
+      const int e = threadIdx.x + 128 * k;
+      v[k] = sp[(e / FL) * TB + e % FL];
+    }
+#pragma unroll
+    for (int k = 0; k < NE; k++) acc[k] = acc[k] + v[k];
+  }
+#pragma unroll
+  for (int k = 0; k < NE; k++) tile[threadIdx.x + 128 * k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < (L / R1) * FL) {  // first inverse stage: groups g, positions g R1 + q
+    const int g = threadIdx.x / FL, l = threadIdx.x % FL;
+    cx<float> v[R1];
+#pragma unroll
+    for (int q = 0; q < R1; q++) v[q] = tile[(g * R1 + q) * FL + l];
+    Dft<float, R1, true>::run(v);
+#pragma unroll
+    for (int q = 0; q < R1; q++) tile[(g * R1 + q) * FL + l] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < M0 * FL) {  // last inverse stage (plan stage 0): rows y = j + q M0 < n_in
+    const int j = threadIdx.x / FL, l = threadIdx.x % FL;
+    cx<float> v[R0];
+#pragma unroll
+    for (int q = 0; q < R0; q++) v[q] = tile[(j + q * M0) * FL + l];
+    apply_twiddles<float, L, 0, true>(v, j, tw);
+    Dft<float, R0, true>::run(v);
+    cx<float>* o = reinterpret_cast<cx<float>*>(a.yrows) + cb * TB + l0 + l;
+#pragma unroll
+    for (int q = 0; q < R0; q++) {
+      const int y = j + q * M0;
+      if (y < a.n_in) o[(long long)y * a.P] = v[q];
+    }
+  }
 }
 
 // Adjoint: the (column block, design plane) items [T b / B, T (b + 1) / B) of block b,
 // T = (P / TB) nzout; one item per round and group.
-template <int L, int C>
+template <int L, int C, bool FULL>
 __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a, const __grid_constant__ CUtensorMap mslice) {
   using S0 = StageShape<L, 0>;
   using S1 = StageShape<L, 1>;
@@ -620,28 +609,22 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a, const __grid_con
   unsigned long long* mb = reinterpret_cast<unsigned long long*>(stt0 + 2 * KS * TB);  // slice 0, slice 1
   load_twiddles<float, NTF>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
   const long long T = (long long)(a.P / TB) * a.nzout;
-  const int i0 = (int)(T * blockIdx.x / gridDim.x), i1 = (int)(T * (blockIdx.x + 1) / gridDim.x);
-  const int n = i1 - i0;
-  auto item = [&](int i, int& kx0, int& z) {
-    const int cb = i / a.nzout;
-    kx0 = cb * TB;
-    z = a.zout0 + (i - cb * a.nzout);
-  };
-  auto issue_slice = [&](int i, int buf) {  // one thread: two TMA boxes into slice buffer buf
-    int kx0, z;
-    item(i, kx0, z);
-    const int dz = z - a.zin0, adz = dz < 0 ? -dz : dz;
-    const int y = (int)((C * a.Tc + adz * a.Tdz) / a.P);
+  const long long i0 = T * blockIdx.x / gridDim.x, i1 = T * (blockIdx.x + 1) / gridDim.x;
+  const int n = (int)(i1 - i0);
+  const Item first = item_of(i0, a.zout0, a.nzout);
+  auto issue_slice = [&](Item it, int buf) {  // one thread: two TMA boxes into slice buffer buf
+    const int dz = it.z - a.zin0, adz = dz < 0 ? -dz : dz;
     float* stt = stt0 + buf * KS * TB;
     mbar_expect_tx(mb + buf, 2 * KB * TB * (int)sizeof(float));
-    tma_load_2d(stt, &mslice, kx0, y, mb + buf);
-    tma_load_2d(stt + KB * TB, &mslice, kx0, y + KB, mb + buf);
+    tma_load_2d(stt, &mslice, it.cb * TB, adz * (L / 2 + 1), mb + buf);
+    tma_load_2d(stt + KB * TB, &mslice, it.cb * TB, adz * (L / 2 + 1) + KB, mb + buf);
   };
   if (threadIdx.x == 0) {
     mbar_init(mb, 1);
     mbar_init(mb + 1, 1);
     mbar_init_fence();
-    if (n > 0) issue_slice(i0, 0);  // the tensor is constant: no need to wait for earlier kernels
+    fence_proxy_async_global();  // the scaled tensor was written by ordinary stores
+    if (n > 0) issue_slice(first, 0);  // the tensor is constant: no need to wait for earlier kernels
   }
   pdl_wait();  // the source plane and the outputs belong to earlier kernels
   if (a.zero_word && blockIdx.x == 0 && threadIdx.x == 0) *a.zero_word = 0u;
@@ -649,29 +632,26 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a, const __grid_con
   if (threadIdx.x < kNT) {
     // load warps: s times the source, first inverse stage, into tile r % 2 in round r
     const int t = threadIdx.x;
-    const float coef = a.coef[0][0][C];
     const cx<float>* src = reinterpret_cast<const cx<float>*>(a.src) + a.in_slot[0] * a.src_cstride +
                            a.zin0 * a.src_zstride;
     // the source spectrum does not depend on the design plane: a thread keeps its 2 R1
     // values (positions g R1 + q of its two units) for as long as the column block stays
     cx<float> sv[2][R1];
-    int kx_held = -1;
+    int cb_held = -1;
+    Item cur = first;
     for (int r = 0; r <= n; r++) {
       if (r < n) {
-        int kx0, z;
-        item(i0 + r, kx0, z);
-        if (kx0 != kx_held) {
+        if (cur.cb != cb_held) {
 #pragma unroll
           for (int it = 0; it < 2; it++) {
             const int u = it * kNT + t, line = u % TB, g = u / TB;
-            const cx<float>* s = src + (long long)(g * R1) * a.P + kx0 + line;
+            const cx<float>* s = src + (long long)(g * R1) * a.P + cur.cb * TB + line;
 #pragma unroll
             for (int q = 0; q < R1; q++) sv[it][q] = s[q * a.P];
           }
-          kx_held = kx0;
+          cb_held = cur.cb;
         }
-        const int dz = z - a.zin0;
-        const float cz = (C >= 4 && dz < 0) ? -coef : coef;
+        const bool neg = cur.z - a.zin0 < 0;
         const float* stt = stt0 + (r & 1) * KS * TB;
         cx<float>* tile = tiles + (r & 1) * L * TB;
         mbar_wait(mb + (r & 1), (r >> 1) & 1, a.status);  // this item's tensor slice
@@ -682,12 +662,13 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a, const __grid_con
           const float* thi = stt + (L - g) * TB + line;
           cx<float> v[R1];
 #pragma unroll
-          for (int q = 0; q < R1; q++) v[q] = ws_apply<C>(ws_tensor<L, C>(tlo, thi, g, q, cz), sv[it][q]);
-          Dft<float, R1, true>::run(v);
+          for (int q = 0; q < R1; q++) v[q] = ws_apply<C>(ws_tensor<L, C>(tlo, thi, g, q, neg), sv[it][q]);
+          DftF<R1, true>::run(v);
           if (it == 1) twiddles_hi<L, true>(v, g, tw);  // stage-0 twiddles of g >= R0/2
 #pragma unroll
           for (int q = 0; q < R1; q++) tile[(g * R1 + q) * TB + line] = v[q];
         }
+        cur = next_item(cur, a.zout0, a.nzout);
       }
       bar_named(kBarAll, NTF);
     }
@@ -696,26 +677,34 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a, const __grid_con
     const int t = threadIdx.x - kNT;
     const int line = t % TB, j = t / TB;
     cx<float>* out0 = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[0] * a.out_cstride;
+    Item cur = first;                                   // the item of round r - 1
+    Item ahead = next_item(first, a.zout0, a.nzout);    // the item whose slice is issued in round r
     for (int r = 0; r <= n; r++) {
       if (t == 0 && r + 1 < n) {
         fence_proxy_async_smem();  // the other group read this slice buffer a round ago
-        issue_slice(i0 + r + 1, (r + 1) & 1);
+        issue_slice(ahead, (r + 1) & 1);
       }
+      if (r + 1 < n) ahead = next_item(ahead, a.zout0, a.nzout);
       if (r >= 1) {
-        int kx0, z;
-        item(i0 + r - 1, kx0, z);
         const cx<float>* tile = tiles + ((r - 1) & 1) * L * TB;
         cx<float> v[R0];
 #pragma unroll
         for (int q = 0; q < R0; q++) v[q] = tile[(j + q * M0) * TB + line];
         twiddles_lo<L, true>(v, j, tw);  // q >= R0/2: applied by the load warps
-        Dft<float, R0, true>::run(v);
-        cx<float>* o = out0 + z * a.out_zstride + kx0 + line;
+        cx<float>* o = out0 + cur.z * a.out_zstride + cur.cb * TB + line;
+        if constexpr (FULL) {  // rows y = j + q M0 < L/2: the first half of the outputs
+          dft_low_half<R0, true>(v);
 #pragma unroll
-        for (int q = 0; q < R0; q++) {
-          const int y = j + q * M0;
-          if (y < a.n_out) o[(long long)y * a.P] = v[q];
+          for (int q = 0; q < R0 / 2; q++) o[(long long)(j + q * M0) * a.P] = v[q];
+        } else {
+          DftF<R0, true>::run(v);
+#pragma unroll
+          for (int q = 0; q < R0; q++) {
+            const int y = j + q * M0;
+            if (y < a.n_out) o[(long long)y * a.P] = v[q];
+          }
         }
+        cur = next_item(cur, a.zout0, a.nzout);
       }
       bar_named(kBarAll, NTF);
     }
@@ -790,28 +779,33 @@ bool map_2d(CUtensorMap* m, CUtensorMapDataType type, const void* base, unsigned
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
-// the tensor slices: Tz [6][nz][Ly/2 + 1][P] floats as rows of P; the last map made on
-// this host thread is kept, since a context launches with the same one every time
-bool slice_map(CUtensorMap* m, const float* Tz, long long Tc, int P, int box_rows) {
+// the tensor slices: a scaled single component Ts [nz][Ly/2 + 1][P] floats as rows of P;
+// the last two maps made on this host thread are kept (a context launches the forward
+// and the adjoint with the same two every time)
+bool slice_map(CUtensorMap* m, const float* Ts, long long rows, int P, int box_rows) {
   struct Cached {
-    const float* Tz = nullptr;
-    long long Tc = 0;
+    const float* Ts = nullptr;
+    long long rows = 0;
     int P = 0, box = 0;
     CUtensorMap map;
   };
-  thread_local Cached c;
-  if (c.Tz == Tz && c.Tc == Tc && c.P == P && c.box == box_rows) {
-    *m = c.map;
-    return true;
-  }
-  if (!map_2d(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Tz, (unsigned long long)P, 6ULL * (unsigned long long)(Tc / P),
+  thread_local Cached c[2];
+  thread_local int next = 0;
+  for (Cached& e : c)
+    if (e.Ts == Ts && e.rows == rows && e.P == P && e.box == box_rows) {
+      *m = e.map;
+      return true;
+    }
+  if (!map_2d(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, Ts, (unsigned long long)P, (unsigned long long)rows,
               (unsigned long long)P * sizeof(float), TB, box_rows))
     return false;
-  c.Tz = Tz;
-  c.Tc = Tc;
-  c.P = P;
-  c.box = box_rows;
-  c.map = *m;
+  Cached& e = c[next];
+  next ^= 1;
+  e.Ts = Ts;
+  e.rows = rows;
+  e.P = P;
+  e.box = box_rows;
+  e.map = *m;
   return true;
 }
 
@@ -826,21 +820,32 @@ int sm_count() {
   return nsm;
 }
 
-template <int L, int C>
+template <int L, int C, bool FULL>
 int launch_adj_ws(const ZYArgs& a, const CUtensorMap& mslice, cudaStream_t s) {
-  constexpr size_t sm = adj_ws_smem<L>();
+  constexpr size_t sm = ws_smem<L>();
   static bool init = false;
   if (!init) {
-    if (cudaFuncSetAttribute(k_zy_adj_ws<L, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+    if (cudaFuncSetAttribute(k_zy_adj_ws<L, C, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
         cudaSuccess)
       return -1;
     init = true;
   }
   const long long items = (long long)(a.P / TB) * a.nzout;
   const int blocks = (int)(items < sm_count() ? items : sm_count());  // one resident block per SM
-  return launch_k(k_zy_adj_ws<L, C>, dim3(blocks), dim3(NTF), sm, s, a.pdl != 0, a, mslice) == cudaSuccess
+  return launch_k(k_zy_adj_ws<L, C, FULL>, dim3(blocks), dim3(NTF), sm, s, a.pdl != 0, a, mslice) == cudaSuccess
              ? (a.zero_word ? 1 : 0)  // 1: *zero_word is cleared
              : -1;
+}
+template <int L, bool FULL>
+int launch_adj_ws_c(const ZYArgs& a, int c, const CUtensorMap& ms, cudaStream_t s) {
+  switch (c) {
+    case 0: return launch_adj_ws<L, 0, FULL>(a, ms, s);
+    case 1: return launch_adj_ws<L, 1, FULL>(a, ms, s);
+    case 2: return launch_adj_ws<L, 2, FULL>(a, ms, s);
+    case 3: return launch_adj_ws<L, 3, FULL>(a, ms, s);
+    case 4: return launch_adj_ws<L, 4, FULL>(a, ms, s);
+    default: return launch_adj_ws<L, 5, FULL>(a, ms, s);
+  }
 }
 
 template <int L>
@@ -850,16 +855,8 @@ int run_zy_adj(const ZYArgs& a, cudaStream_t s) {
   if (a.nin == 1 && a.nout == 1 && a.nzin == 1 && c >= 0) {
     if constexpr (yz_ws_plan<L>()) {
       CUtensorMap ms;
-      if (slice_map(&ms, a.Tz, a.Tc, a.P, slice_box_rows<L>())) {
-        switch (c) {
-          case 0: return launch_adj_ws<L, 0>(a, ms, s);
-          case 1: return launch_adj_ws<L, 1>(a, ms, s);
-          case 2: return launch_adj_ws<L, 2>(a, ms, s);
-          case 3: return launch_adj_ws<L, 3>(a, ms, s);
-          case 4: return launch_adj_ws<L, 4>(a, ms, s);
-          default: return launch_adj_ws<L, 5>(a, ms, s);
-        }
-      }
+      if (a.Ts && a.nzin_total > 0 && slice_map(&ms, a.Ts, (long long)a.nzin_total * (L / 2 + 1), a.P, slice_box_rows<L>()))
+        return a.n_out == L / 2 ? launch_adj_ws_c<L, true>(a, c, ms, s) : launch_adj_ws_c<L, false>(a, c, ms, s);
     }
     return launch_adj<L, true>(a, c, s);
   }
@@ -899,39 +896,47 @@ int launch_fwd(const YZArgs& a, int c, int nch, cudaStream_t s) {
   return 0;
 }
 
-template <int L, int C>
+template <int L, int C, bool FULL>
 int launch_fwd_ws(const YZArgs& a, const CUtensorMap& mslice, cudaStream_t s) {
-  constexpr size_t sm = fwd_ws_smem<L>();
+  constexpr size_t sm = ws_smem<L>();
   static bool init = false;
   if (!init) {
-    if (cudaFuncSetAttribute(k_yz_fwd_ws<L, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+    if (cudaFuncSetAttribute(k_yz_fwd_ws<L, C, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
         cudaSuccess)
       return -1;
     init = true;
   }
   const long long items = (long long)(a.P / TB) * a.nzin;
   const int blocks = (int)(items < sm_count() ? items : sm_count());  // one resident block per SM
-  return launch_k(k_yz_fwd_ws<L, C>, dim3(blocks), dim3(NTF), sm, s, a.pdl != 0, a, mslice) == cudaSuccess
+  if (launch_k(k_yz_fwd_ws<L, C, FULL>, dim3(blocks), dim3(NTF), sm, s, a.pdl != 0, a, mslice) != cudaSuccess)
+    return -1;
+  // the segment partials of each column block, then the target plane's y inverse
+  return launch_k(k_yz_finish<L>, dim3(a.P / TB, TB / kFinishLines), dim3(128), 0, s, a.pdl != 0, a, blocks) ==
+                 cudaSuccess
              ? 1  // 1: the target plane's y inverse is done
              : -1;
+}
+template <int L, bool FULL>
+int launch_fwd_ws_c(const YZArgs& a, int c, const CUtensorMap& ms, cudaStream_t s) {
+  switch (c) {
+    case 0: return launch_fwd_ws<L, 0, FULL>(a, ms, s);
+    case 1: return launch_fwd_ws<L, 1, FULL>(a, ms, s);
+    case 2: return launch_fwd_ws<L, 2, FULL>(a, ms, s);
+    case 3: return launch_fwd_ws<L, 3, FULL>(a, ms, s);
+    case 4: return launch_fwd_ws<L, 4, FULL>(a, ms, s);
+    default: return launch_fwd_ws<L, 5, FULL>(a, ms, s);
+  }
 }
 
 template <int L>
 int launch_fwd_single(const YZArgs& a, int c, int nch, cudaStream_t s) {
   if constexpr (yz_ws_plan<L>()) {
-    // needs the segment buffers, and at most two column blocks per block (blocks >= P / TB)
+    // needs the segment buffers, the scaled tensor component, and at most two column
+    // blocks per block (blocks >= P / TB)
     CUtensorMap ms;
-    if (a.n_in <= L / 2 && a.seg && a.cnt && a.yrows && a.P / TB <= sm_count() &&
-        slice_map(&ms, a.Tz, a.Tc, a.P, slice_box_rows<L>())) {
-      switch (c) {
-        case 0: return launch_fwd_ws<L, 0>(a, ms, s);
-        case 1: return launch_fwd_ws<L, 1>(a, ms, s);
-        case 2: return launch_fwd_ws<L, 2>(a, ms, s);
-        case 3: return launch_fwd_ws<L, 3>(a, ms, s);
-        case 4: return launch_fwd_ws<L, 4>(a, ms, s);
-        default: return launch_fwd_ws<L, 5>(a, ms, s);
-      }
-    }
+    if (a.n_in <= L / 2 && a.seg && a.yrows && a.Ts && a.P / TB <= sm_count() &&
+        slice_map(&ms, a.Ts, (long long)a.nz_total * (L / 2 + 1), a.P, slice_box_rows<L>()))
+      return a.n_in == L / 2 ? launch_fwd_ws_c<L, true>(a, c, ms, s) : launch_fwd_ws_c<L, false>(a, c, ms, s);
   }
   return launch_fwd_staged<L>(a, c, nch, s);
 }

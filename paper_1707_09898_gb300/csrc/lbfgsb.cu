@@ -691,144 +691,167 @@ bool solve_inplace(std::vector<double>& A, std::vector<double>& B, int n, int nr
   return true;
 }
 
-// ---- More-Thuente line search (safeguarded cubic / quadratic steps) -------------------
-struct Dcsrch {
-  double ftol = 1e-3, gtol = 0.9, xtol = 0.1, stpmin = 0.0, stpmax = 0.0;
-  bool brackt = false;
-  int stage = 1;
-  double ginit = 0, gtest = 0, gx = 0, gy = 0, finit = 0, fx = 0, fy = 0, stx = 0, sty = 0, stmin = 0, stmax = 0,
-         width = 0, width1 = 0;
+// ---- Line search of More and Thuente (ACM TOMS 20:286-307, 1994) ---------------------
+// Looks for a step a > 0 along the direction with phi(a) = f(x + a d) satisfying the strong
+// Wolfe conditions phi(a) <= phi(0) + mu a phi'(0) and |phi'(a)| <= eta |phi'(0)|, inside
+// [amin, amax]. The paper's scheme: an interval of uncertainty [best, other] whose end
+// "best" has the lowest value seen and a derivative that points into the interval; each
+// trial step comes from cubic, quadratic and secant interpolation of the end points and
+// the last trial (its four cases), safeguarded by a 0.66 shrink of bracketed steps, by
+// bisection when two trials did not shrink the interval to 0.66 of its width, and by
+// extrapolation limits [1.1, 4] times the last move while no minimiser is bracketed.
+// Until a step with psi(a) = phi(a) - a mu phi'(0) - phi(0) <= 0 and phi'(a) >= 0 is
+// seen (stage 1), trial values are taken on psi, afterwards on phi.
+struct Probe {
+  double a, f, g;  // step, value, derivative along d
+};
 
-  void start(double f, double g, double stp) {
-    brackt = false;
-    stage = 1;
-    finit = f;
-    ginit = g;
-    gtest = ftol * ginit;
-    width = stpmax - stpmin;
-    width1 = width / 0.5;
-    stx = 0.0;
-    fx = finit;
-    gx = ginit;
-    sty = 0.0;
-    fy = finit;
-    gy = ginit;
-    stmin = 0.0;
-    stmax = stp + 4.0 * stp;
+// Minimiser of the cubic with values and slopes p and q at p.a and q.a (the same cubic,
+// and so the same point, whichever end is p). With t = p.g + q.g - 3 (secant slope) the
+// slope of the cubic has the roots p.a + h (t - p.g +- sqrt(t^2 - p.g q.g)) / (...);
+// the minimiser takes the root whose sign follows h = q.a - p.a. Values are divided by
+// the largest of |t|, |p.g|, |q.g| before squaring, so nothing overflows.
+double cubic_min(const Probe& p, const Probe& q) {
+  const double h = q.a - p.a;
+  const double t = 3.0 * (p.f - q.f) / h + p.g + q.g;
+  const double m = std::max(std::fabs(t), std::max(std::fabs(p.g), std::fabs(q.g)));
+  const double disc = (t / m) * (t / m) - (p.g / m) * (q.g / m);
+  const double root = (h > 0.0 ? 1.0 : -1.0) * m * std::sqrt(disc);
+  const double r = ((root - p.g) + t) / (((root - p.g) + root) + q.g);
+  return p.a + r * h;
+}
+
+// the same cubic in the form used where the minimiser is only accepted when it lies on
+// the side of q away from p (stage 3): *valid is false when there is no such minimiser
+double cubic_min_beyond(const Probe& p, const Probe& q, bool* valid) {
+  const double h = p.a - q.a;
+  const double t = 3.0 * (p.f - q.f) / (q.a - p.a) + p.g + q.g;
+  const double m = std::max(std::fabs(t), std::max(std::fabs(p.g), std::fabs(q.g)));
+  const double disc = std::max(0.0, (t / m) * (t / m) - (p.g / m) * (q.g / m));
+  const double root = (q.a > p.a ? -1.0 : 1.0) * m * std::sqrt(disc);
+  const double num = (root - q.g) + t, den = (root + (p.g - q.g)) + root;
+  const double r = num / den;
+  *valid = r < 0.0 && root != 0.0;
+  return q.a + r * h;
+}
+
+// minimiser of the quadratic with value and slope p at p.a and value qf at qa
+double quad_min(const Probe& p, double qa, double qf) {
+  const double h = qa - p.a;
+  return p.a + (p.g / ((p.f - qf) / h + p.g)) / 2.0 * h;
+}
+
+// zero of the straight line through the slopes of p and q
+double secant_min(const Probe& p, const Probe& q) { return q.a + (q.g / (q.g - p.g)) * (p.a - q.a); }
+
+class MoreThuente {
+ public:
+  double mu = 1e-3, eta = 0.9, xtol = 0.1;  // sufficient decrease, curvature, relative interval width
+  double amin = 0.0, amax = 0.0;
+
+  // phi(0) = f0, phi'(0) = g0 < 0, first trial a1
+  void begin(double f0, double g0, double a1) {
+    f0_ = f0;
+    g0_ = g0;
+    dec_ = mu * g0;
+    bracketed_ = false;
+    stage2_ = false;
+    width_ = amax - amin;
+    width_old_ = 2.0 * width_;
+    best_ = {0.0, f0, g0};
+    other_ = {0.0, f0, g0};
+    lo_ = 0.0;
+    hi_ = a1 + 4.0 * a1;
   }
 
-  static void cstep(double& stx, double& fx, double& dx, double& sty, double& fy, double& dy, double& stp, double fp,
-                    double dp, bool& brackt, double lo, double hi) {
-    const double sgnd = dp * (dx / std::fabs(dx));
-    double stpf;
-    if (fp > fx) {  // higher value: the minimum is bracketed
-      const double theta = 3.0 * (fx - fp) / (stp - stx) + dx + dp;
-      const double s = std::max(std::fabs(theta), std::max(std::fabs(dx), std::fabs(dp)));
-      double gamma = s * std::sqrt((theta / s) * (theta / s) - (dx / s) * (dp / s));
-      if (stp < stx) gamma = -gamma;
-      const double p = (gamma - dx) + theta, q = ((gamma - dx) + gamma) + dp, r = p / q;
-      const double stpc = stx + r * (stp - stx);
-      const double stpq = stx + ((dx / ((fx - fp) / (stp - stx) + dx)) / 2.0) * (stp - stx);
-      stpf = std::fabs(stpc - stx) < std::fabs(stpq - stx) ? stpc : stpc + (stpq - stpc) / 2.0;
-      brackt = true;
-    } else if (sgnd < 0.0) {  // lower value, derivatives of opposite sign
-      const double theta = 3.0 * (fx - fp) / (stp - stx) + dx + dp;
-      const double s = std::max(std::fabs(theta), std::max(std::fabs(dx), std::fabs(dp)));
-      double gamma = s * std::sqrt((theta / s) * (theta / s) - (dx / s) * (dp / s));
-      if (stp > stx) gamma = -gamma;
-      const double p = (gamma - dp) + theta, q = ((gamma - dp) + gamma) + dx, r = p / q;
-      const double stpc = stp + r * (stx - stp);
-      const double stpq = stp + (dp / (dp - dx)) * (stx - stp);
-      stpf = std::fabs(stpc - stp) > std::fabs(stpq - stp) ? stpc : stpq;
-      brackt = true;
-    } else if (std::fabs(dp) < std::fabs(dx)) {  // same sign, |derivative| decreases
-      const double theta = 3.0 * (fx - fp) / (stp - stx) + dx + dp;
-      const double s = std::max(std::fabs(theta), std::max(std::fabs(dx), std::fabs(dp)));
-      double gamma = s * std::sqrt(std::max(0.0, (theta / s) * (theta / s) - (dx / s) * (dp / s)));
-      if (stp > stx) gamma = -gamma;
-      const double p = (gamma - dp) + theta, q = (gamma + (dx - dp)) + gamma, r = p / q;
-      double stpc;
-      if (r < 0.0 && gamma != 0.0)
-        stpc = stp + r * (stx - stp);
-      else if (stp > stx)
-        stpc = hi;
-      else
-        stpc = lo;
-      const double stpq = stp + (dp / (dp - dx)) * (stx - stp);
-      if (brackt) {
-        stpf = std::fabs(stpc - stp) < std::fabs(stpq - stp) ? stpc : stpq;
-        stpf = stp > stx ? std::min(stp + 0.66 * (sty - stp), stpf) : std::max(stp + 0.66 * (sty - stp), stpf);
-      } else {
-        stpf = std::fabs(stpc - stp) > std::fabs(stpq - stp) ? stpc : stpq;
-        stpf = std::max(lo, std::min(hi, stpf));
-      }
-    } else {  // same sign, |derivative| does not decrease
-      if (brackt) {
-        const double theta = 3.0 * (fp - fy) / (sty - stp) + dy + dp;
-        const double s = std::max(std::fabs(theta), std::max(std::fabs(dy), std::fabs(dp)));
-        double gamma = s * std::sqrt((theta / s) * (theta / s) - (dy / s) * (dp / s));
-        if (stp > sty) gamma = -gamma;
-        const double p = (gamma - dp) + theta, q = ((gamma - dp) + gamma) + dy, r = p / q;
-        stpf = stp + r * (sty - stp);
-      } else {
-        stpf = stp > stx ? hi : lo;
-      }
-    }
-    if (fp > fx) {
-      sty = stp;
-      fy = fp;
-      dy = dp;
+  // phi(a) = f, phi'(a) = g at the trial a; true: accept a; false: a holds the next trial
+  bool advance(double f, double g, double& a) {
+    const double fsuff = f0_ + a * dec_;  // sufficient-decrease line
+    if (!stage2_ && f <= fsuff && g >= 0.0) stage2_ = true;
+    if (converged(f, g, a, fsuff)) return true;
+    Probe t = {a, f, g};
+    if (!stage2_ && f <= best_.f && f > fsuff) {
+      // stage 1 on psi: shift every value and slope by the sufficient-decrease line
+      Probe b = shifted(best_), o = shifted(other_), ts = shifted(t);
+      a = trial(b, o, ts);
+      best_ = unshifted(b);
+      other_ = unshifted(o);
     } else {
-      if (sgnd < 0.0) {
-        sty = stx;
-        fy = fx;
-        dy = dx;
-      }
-      stx = stp;
-      fx = fp;
-      dx = dp;
+      a = trial(best_, other_, t);
     }
-    stp = stpf;
-  }
-
-  // returns true when the step is accepted (convergence or a warning), else stp = next trial
-  bool next(double f, double g, double& stp) {
-    const double ftest = finit + stp * gtest;
-    if (stage == 1 && f <= ftest && g >= 0.0) stage = 2;
-    bool done = false;
-    if (brackt && (stp <= stmin || stp >= stmax)) done = true;
-    if (brackt && stmax - stmin <= xtol * stmax) done = true;
-    if (stp == stpmax && f <= ftest && g <= gtest) done = true;
-    if (stp == stpmin && (f > ftest || g >= gtest)) done = true;
-    if (f <= ftest && std::fabs(g) <= gtol * (-ginit)) done = true;
-    if (done) return true;
-    if (stage == 1 && f <= fx && f > ftest) {
-      double fm = f - stp * gtest, fxm = fx - stx * gtest, fym = fy - sty * gtest;
-      double gm = g - gtest, gxm = gx - gtest, gym = gy - gtest;
-      cstep(stx, fxm, gxm, sty, fym, gym, stp, fm, gm, brackt, stmin, stmax);
-      fx = fxm + stx * gtest;
-      fy = fym + sty * gtest;
-      gx = gxm + gtest;
-      gy = gym + gtest;
+    if (bracketed_) {
+      const double w = std::fabs(other_.a - best_.a);
+      if (w >= 0.66 * width_old_) a = best_.a + 0.5 * (other_.a - best_.a);  // bisection
+      width_old_ = width_;
+      width_ = w;
+      lo_ = std::min(best_.a, other_.a);
+      hi_ = std::max(best_.a, other_.a);
     } else {
-      cstep(stx, fx, gx, sty, fy, gy, stp, f, g, brackt, stmin, stmax);
+      lo_ = a + 1.1 * (a - best_.a);
+      hi_ = a + 4.0 * (a - best_.a);
     }
-    if (brackt) {
-      if (std::fabs(sty - stx) >= 0.66 * width1) stp = stx + 0.5 * (sty - stx);
-      width1 = width;
-      width = std::fabs(sty - stx);
-    }
-    if (brackt) {
-      stmin = std::min(stx, sty);
-      stmax = std::max(stx, sty);
-    } else {
-      stmin = stp + 1.1 * (stp - stx);
-      stmax = stp + 4.0 * (stp - stx);
-    }
-    stp = std::max(stp, stpmin);
-    stp = std::min(stp, stpmax);
-    if ((brackt && (stp <= stmin || stp >= stmax)) || (brackt && stmax - stmin <= xtol * stmax)) stp = stx;
+    a = std::min(std::max(a, amin), amax);
+    // no progress possible within the interval: fall back to the best step
+    if (bracketed_ && (a <= lo_ || a >= hi_ || hi_ - lo_ <= xtol * hi_)) a = best_.a;
     return false;
+  }
+
+ private:
+  double f0_ = 0, g0_ = 0, dec_ = 0, width_ = 0, width_old_ = 0, lo_ = 0, hi_ = 0;
+  bool bracketed_ = false, stage2_ = false;
+  Probe best_{}, other_{};
+
+  Probe shifted(const Probe& p) const { return {p.a, p.f - p.a * dec_, p.g - dec_}; }
+  Probe unshifted(const Probe& p) const { return {p.a, p.f + p.a * dec_, p.g + dec_}; }
+
+  bool converged(double f, double g, double a, double fsuff) const {
+    if (bracketed_ && (a <= lo_ || a >= hi_)) return true;          // rounding stops progress
+    if (bracketed_ && hi_ - lo_ <= xtol * hi_) return true;         // interval below tolerance
+    if (a == amax && f <= fsuff && g <= dec_) return true;          // at the upper bound
+    if (a == amin && (f > fsuff || g >= dec_)) return true;         // at the lower bound
+    return f <= fsuff && std::fabs(g) <= eta * (-g0_);              // strong Wolfe conditions
+  }
+
+  // Next trial from the interval ends b (best), o (other) and the trial t (the paper's four
+  // cases), then the interval update: t replaces o when its value is higher than b's;
+  // otherwise t becomes the best end, and o moves to the old best when the slopes of b
+  // and t have opposite signs.
+  double trial(Probe& b, Probe& o, const Probe& t) {
+    const bool opposite = t.g * (b.g / std::fabs(b.g)) < 0.0;
+    double next;
+    if (t.f > b.f) {  // case 1: higher value, a minimiser lies between b and t
+      const double c = cubic_min(b, t);
+      const double q = quad_min(b, t.a, t.f);
+      next = std::fabs(c - b.a) < std::fabs(q - b.a) ? c : c + (q - c) / 2.0;
+      bracketed_ = true;
+    } else if (opposite) {  // case 2: lower value, slopes of opposite signs
+      const double c = cubic_min(b, t);
+      const double sc = secant_min(b, t);
+      next = std::fabs(c - t.a) > std::fabs(sc - t.a) ? c : sc;
+      bracketed_ = true;
+    } else if (std::fabs(t.g) < std::fabs(b.g)) {  // case 3: lower value, slope shrinking
+      bool valid = false;
+      double c = cubic_min_beyond(b, t, &valid);
+      if (!valid) c = t.a > b.a ? hi_ : lo_;
+      const double sc = secant_min(b, t);
+      if (bracketed_) {
+        next = std::fabs(c - t.a) < std::fabs(sc - t.a) ? c : sc;
+        const double lim = t.a + 0.66 * (o.a - t.a);
+        next = t.a > b.a ? std::min(lim, next) : std::max(lim, next);
+      } else {
+        next = std::fabs(c - t.a) > std::fabs(sc - t.a) ? c : sc;
+        next = std::max(lo_, std::min(hi_, next));
+      }
+    } else {  // case 4: lower value, slope not shrinking
+      next = bracketed_ ? cubic_min(o, t) : (t.a > b.a ? hi_ : lo_);
+    }
+    if (t.f > b.f) {
+      o = t;
+    } else {
+      if (opposite) o = b;
+      b = t;
+    }
+    return next;
   }
 };
 
@@ -862,7 +885,7 @@ struct tm_lbfgsb {
   long long iter = 0, nfev = 0, nbreak = 0, nfree = 0;
   int phase = 0;  // 0 created, 1 waiting for f(x0), 2 in a line search, 3 new x reported, 4 stopped
   // line search state
-  Dcsrch ls;
+  MoreThuente ls;
   double stp = 1.0, gd = 0.0, dtd = 0.0, stpmx = 0.0;
   int nls = 0;
 };
@@ -1104,9 +1127,9 @@ int begin_search(tm_lbfgsb* o, float* e32, double* e64, cudaStream_t s, bool& as
   ascent = !(o->gd < 0.0);
   if (ascent) return TM_OK;
   o->stp = 1.0;  // every variable has both bounds
-  o->ls.stpmin = 0.0;
-  o->ls.stpmax = o->stpmx;
-  o->ls.start(o->f, o->gd, o->stp);
+  o->ls.amin = 0.0;
+  o->ls.amax = o->stpmx;
+  o->ls.begin(o->f, o->gd, o->stp);
   o->nls = 0;
   k_trial<<<gb, NT, 0, s>>>(o->x, o->d, o->xbar, n, o->stp, o->xt, e32, e64);
   LCKL();
@@ -1268,7 +1291,7 @@ int tm_lbfgsb_iterate(tm_lbfgsb* o, double f, const float* g32, const double* g6
   if (int e = fetch_sums(o, gb, 1, s)) return e;
   const double gdt = o->hbuf[0];
   double stp = o->stp;
-  const bool accepted = o->ls.next(f, gdt, stp);
+  const bool accepted = o->ls.advance(f, gdt, stp);
   if (!accepted) {
     if (o->nls >= o->maxls) {  // too many trials: drop the memory and restart from x, or stop
       if (o->col == 0) {

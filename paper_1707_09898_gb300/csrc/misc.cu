@@ -67,6 +67,11 @@ __global__ void k_update(float* rho, const float* G, long long n, float alpha, i
     rho[i] = fminf(fmaxf(rho[i] - step * G[i], 0.0f), 1.0f);
 }
 
+__global__ void k_scale(float* dst, const float* src, long long n, float coef) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = coef * src[i];
+}
+
 // [zlo, zhi) of the planes that hold a nonzero mask entry (ext preset to (INT_MAX-ish, 0))
 __global__ void k_mask_extent(const uint8_t* mask, int nz, long long plane, int* ext) {
   for (int z = blockIdx.y; z < nz; z += gridDim.y) {
@@ -239,6 +244,10 @@ int launch_stencil(const StencilArgs& a, cudaStream_t s) {
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
 }
 
+int launch_scale(float* dst, const float* src, long long n, float coef, cudaStream_t s) {
+  k_scale<<<grid_for(n, 256 * 8), 256, 0, s>>>(dst, src, n, coef);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+}
 int launch_check_design(const float* rho, long long n, unsigned long long* bad, cudaStream_t s) {
   k_check_design<<<grid_for(n, 256 * 8), 256, 0, s>>>(rho, n, bad);
   return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;

@@ -235,35 +235,50 @@ def test_spec_input(L):
     assert fp.shape == (64, 64) and fp.sum() >= 64 and 1 <= h <= 8 and 0.05 <= ht <= 0.3
 
 
-def test_network_against_oracle():
+def _net_vs_oracle(N, D, target, q, seed=21):
+    """GPU network loss, rho and parameter gradients next to the oracle's (same bfloat16
+    weights; q = None: all-float64 oracle; q = bf16_round: bfloat16 product operands)."""
     from paper_1707_09898_gb300.warmstart import WarmStartNet, init_params
 
-    params = init_params(seed=21)
+    params = init_params(seed=seed)
     # the oracle multiplies the same bfloat16 weights the tensor cores see
     oparams = {k: ((bf16_round(w) if k != "head" else w.astype(np.float64)), b.astype(np.float64))
                for k, (w, b) in params.items()}
     rng = np.random.default_rng(22)
-    N, D = 2, 8
     x = np.zeros((N, D, D, D, 16))
     x[..., :3] = bf16_round(rng.random((N, D, D, D, 3)))
-    tgt = rng.random((N, D, D, D)).astype(np.float32)
+    tgt = (rng.random((N, D, D, D)) if target == "random" else np.ones((N, D, D, D))).astype(np.float32)
     net = WarmStartNet(size=(D, D, D), params=params)
     rho = net.forward(to_bf16_dev(x)).cpu().numpy()
     loss = float(net.backward(f32(tgt)))
     got = net.grads()
-    t64 = tgt.astype(np.float64)
-    for q, tol_rho, tol_loss, tol_g in ((bf16_round, 1e-4, 1e-4, 1e-2), (None, 5e-3, 3e-2, 0.3)):
-        r_ref, _ = U.forward(oparams, x, q)
-        l_ref, g_ref = U.loss_and_grads(oparams, x, t64, q)
-        errs = {}
-        for k in g_ref:
-            for j in (0, 1):
-                errs[(k, j)] = np.linalg.norm(got[k][j] - g_ref[k][j]) / np.linalg.norm(g_ref[k][j])
-        print("bf16 storage" if q else "float64", f"rho {np.max(np.abs(rho - r_ref)):.2e}",
-              f"loss {abs(loss - l_ref) / l_ref:.2e}", {f"{k}.{'wb'[j]}": f"{e:.1e}" for (k, j), e in errs.items()})
-        assert np.max(np.abs(rho - r_ref)) <= tol_rho
-        assert abs(loss - l_ref) <= tol_loss * l_ref
-        assert max(errs.values()) <= tol_g
+    r_ref, _ = U.forward(oparams, x, q)
+    l_ref, g_ref = U.loss_and_grads(oparams, x, tgt.astype(np.float64), q)
+    errs = {f"{k}.{'wb'[j]}": np.linalg.norm(got[k][j] - g_ref[k][j]) / np.linalg.norm(g_ref[k][j])
+            for k in g_ref for j in (0, 1)}
+    print("bf16 products" if q else "float64", f"rho {np.max(np.abs(rho - r_ref)):.2e}",
+          f"loss {abs(loss - l_ref) / l_ref:.2e}", {k: f"{e:.1e}" for k, e in errs.items()})
+    return np.max(np.abs(rho - r_ref)), abs(loss - l_ref) / l_ref, errs
+
+
+def test_network_against_oracle_with_bfloat16_products():
+    """The whole network against the oracle's bfloat16-operand mode (every product of a
+    convolution takes bfloat16 operands, sums exact): the GPU network is that network up
+    to float32 summation order, so every parameter gradient agrees to 1e-2 even where it is
+    a near-cancelling sum (random targets, 8^3, batch 2)."""
+    drho, dloss, errs = _net_vs_oracle(2, 8, "random", bf16_round)
+    assert drho <= 1e-4 and dloss <= 1e-4
+    assert max(errs.values()) <= 1e-2, errs
+
+
+def test_network_against_float64_oracle():
+    """The whole network against the all-float64 oracle. With every voxel's target above
+    the network's output the gradients do not cancel, so the bfloat16 operands move them by
+    well under 2e-2 (about 5e-3 measured on the oracle's own two modes at this size), while
+    a wrong tap, transposed weight or misrouted skip connection moves them by O(1)."""
+    drho, dloss, errs = _net_vs_oracle(2, 32, "ones", None)
+    assert drho <= 5e-3 and dloss <= 1e-3
+    assert max(errs.values()) <= 2e-2, errs
 
 
 def _random_batch(rng, N, D):
