@@ -534,7 +534,7 @@ int yz_forward(tm_ctx* ctx, const ConvSpec& cs, int zo, cudaStream_t s, bool* yi
 
 // direct z sum from the source planes [zi0, zi0 + nzi) fused with the inverse y
 // transform of every design plane
-int zy_adjoint(tm_ctx* ctx, const ConvSpec& cs, int zi0, int nzi, cudaStream_t s) {
+int zy_adjoint(tm_ctx* ctx, const ConvSpec& cs, int zi0, int nzi, cudaStream_t s, bool yfwd_inside) {
   const int Ly = ctx->L[1];
   const long long P = ctx->P;
   ZYArgs z{};
@@ -578,6 +578,10 @@ int zy_adjoint(tm_ctx* ctx, const ConvSpec& cs, int zi0, int nzi, cudaStream_t s
     // the adjoint reads its first tensor slice before it waits for the preceding kernel:
     // after a rebuild it must start only once the scaling kernel has finished
     if (rebuilt) z.pdl = 0;
+  }
+  if (yfwd_inside) {  // the source plane as x spectra: rows y < ny of plane zi0 of A slot ain[0]
+    z.gsrc = ctx->A + cs.ain[0] * ((long long)ctx->nz * ctx->ny * P) + (long long)zi0 * ctx->ny * P;
+    z.n_src = ctx->ny;
   }
   Timed t(ctx, KIND_ZYA, s);
   const int r = launch_zy_adj(Ly, z, s);
@@ -1123,7 +1127,6 @@ int adjoint_planes(tm_ctx* ctx, const float* rho, float* dJdrho, const int* F, c
       ca.u[i] = ca.v[i] = kUnit[i];
     }
   }
-  if ((r = ypass(ctx, false, ca.nin, ca.ain, ca.bin, ctx->tz0, np, s))) return r;
   // fused only in its single-spectrum, single-component form; with several spectra or
   // tensor components the separate passes measured faster
   bool simple = ca.nin == 1 && ca.nout == 1 && np == 1;
@@ -1134,8 +1137,14 @@ int adjoint_planes(tm_ctx* ctx, const float* rho, float* dJdrho, const int* F, c
     for (int c = 0; c < 6; c++) nc += c6[c] != 0.0f;
     simple = nc == 1;
   }
+  // on the warp-specialized path the fused adjoint runs the source's y transform itself;
+  // it then reads the source rows from A while it writes the design planes into A, so its
+  // output goes to another slot (the target plane may be a design plane)
+  const bool yfwd_inside = ctx->fuse_yz && simple && zy_adj_ws_length(ctx->L[1]) && ctx->ny <= ctx->L[1] / 2;
+  if (yfwd_inside) ca.aout[0] = (ca.ain[0] + 1) % kSlotsA;
+  if (!yfwd_inside && (r = ypass(ctx, false, ca.nin, ca.ain, ca.bin, ctx->tz0, np, s))) return r;
   if (ctx->fuse_yz && simple) {
-    if ((r = zy_adjoint(ctx, ca, ctx->tz0, np, s))) return r;
+    if ((r = zy_adjoint(ctx, ca, ctx->tz0, np, s, yfwd_inside))) return r;
   } else {
     if ((r = zdirect(ctx, ca, ctx->tz0, np, 0, ctx->nzd, s))) return r;
     if ((r = ypass(ctx, true, ca.nout, ca.aout, ca.bout, 0, ctx->nzd, s))) return r;

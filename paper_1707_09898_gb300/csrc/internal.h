@@ -181,6 +181,10 @@ struct ZYArgs {
   // warp-specialized path (one tensor component c): Ts = coef[0][0][c] * Tz[c], [nzin_total][Ly/2+1][P]
   const float* Ts;
   int nzin_total;                           // z offsets held by Ts
+  // if set (warp-specialized path only): the source plane as x spectra, rows [n_src][P]; the
+  // kernel runs its forward y transform itself and src is not read
+  const float2* gsrc;
+  int n_src;
   unsigned* status;                         // device word: bit 0 set when a copy wait timed out
   unsigned* zero_word;                      // if set, zeroed by the warp-specialized kernel (launch_zy_adj returns 1)
   int pdl;                                  // launch with programmatic dependent launch
@@ -213,6 +217,9 @@ struct YZArgs {
   int pdl;                                  // launch with programmatic dependent launch
 };
 int launch_zy_adj(int L, const ZYArgs& a, cudaStream_t s);
+// whether launch_zy_adj takes the warp-specialized path for length L (one source plane, one
+// spectrum and tensor component, Ts given), the path that can run the source's y transform
+bool zy_adj_ws_length(int L);
 int launch_yz_fwd(int L, const YZArgs& a, cudaStream_t s);
 
 int launch_xfwd(int L, const XFwdArgs& a, int ncomp, cudaStream_t s);

@@ -279,9 +279,7 @@ __global__ void __launch_bounds__(2 * kNT, 1) k_xfwd_ws(XFwdArgs a) {
           }
           v[q] = mk(ipow_t<P3>(va[q], a.p), ipow_t<P3>(vb[q], a.p));
         }
-#pragma unroll
-        for (int q = RH; q < R0; q++) v[q] = zero<float>();
-        Dft<float, R0, false>::run(v);
+        dft32_half_input<false>(v);  // x = j + q M0 >= L/2 is padding
         if (j != 0) {  // q >= R0/2: applied by the other group
 #pragma unroll
           for (int q = 1; q < R0 / 2; q++) v[q] = cmul(v[q], tw0[q * M0 + j]);
@@ -308,7 +306,7 @@ __global__ void __launch_bounds__(2 * kNT, 1) k_xfwd_ws(XFwdArgs a) {
 #pragma unroll
             for (int q = 1; q < R1; q++) v[q] = cmul(v[q], tw[q * g]);
           }
-          Dft<float, R1, false>::run(v);
+          DftF<R1, false>::run(v);
 #pragma unroll
           for (int q = 0; q < R1; q++) tile[unit_idx<R1, 1, true>(g, g * R1, q, line)] = v[q];
         }

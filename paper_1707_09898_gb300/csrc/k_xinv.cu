@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(2 * kNT, 1) k_xinv_ws(XInvArgs a) {
           cx<float> v[R1];
 #pragma unroll
           for (int q = 0; q < R1; q++) v[q] = tile[unit_idx<R1, 1, true>(g, g * R1, q, line)];
-          Dft<float, R1, true>::run(v);
+          DftF<R1, true>::run(v);
           if (it == 1) {
 #pragma unroll
             for (int q = 1; q < R1; q++) v[q] = cmulc(v[q], tw[q * g]);
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(2 * kNT, 1) k_xinv_ws(XInvArgs a) {
 #pragma unroll
           for (int q = 1; q < R0 / 2; q++) v[q] = cmulc(v[q], tw0[q * M0 + j]);
         }
-        Dft<float, R0, true>::run(v);
+        dft_low_half<R0, true>(v);  // x = j + q M0 < L/2: the first half of the outputs
         const int rw = (blockIdx.x + (r - 1) * gridDim.x) * ROWS + 2 * line;
         const bool va = rw < a.rows, vb = rw + 1 < a.rows;
         float* g = a.G + (long long)rw * a.nx + j;

@@ -534,55 +534,85 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a, const __grid_con
 // The target plane after the forward: for column block cb (blockIdx.x), the segment
 // partials of the blocks that held its items, added in block order, then its inverse y
 // transform (the inverse of the two DIF stages) into rows y < n_in of A. Each block takes
-// FL of the column block's TB lines (blockIdx.y).
-constexpr int kFinishLines = 2;
+// FL of the column block's TB lines (blockIdx.y). The segments of a column block are read
+// kFinishSegs at a time with all their loads in flight (the sums are latency-bound: a few
+// megabytes from L2 spread over the column blocks).
+constexpr int kFinishLines = 2, kFinishThreads = 512, kFinishSegs = 12, kFinishMaxBlocks = 1024;
+// tile slot of (pos, line) in the finishing kernel: positions XOR-swizzled by pos / 16 so that
+// the threads of a stage (consecutive groups g at one q, or consecutive j) hit distinct banks
+__device__ __forceinline__ int fin_idx(int pos, int l) { return (pos ^ ((pos >> 4) & 15)) * kFinishLines + l; }
 template <int L>
-__global__ void __launch_bounds__(128) k_yz_finish(YZArgs a, int B) {
+__global__ void __launch_bounds__(kFinishThreads) k_yz_finish(YZArgs a, int B) {
   using S0 = StageShape<L, 0>;
   using S1 = StageShape<L, 1>;
-  constexpr int R0 = S0::R, M0 = S0::M, R1 = S1::R, FL = kFinishLines, NE = L * FL / 128;
+  constexpr int R0 = S0::R, M0 = S0::M, R1 = S1::R, FL = kFinishLines, NT = kFinishThreads, NE = L * FL / NT;
+  static_assert(NE * NT == L * FL, "elements per thread");
   __shared__ cx<float> tw[L];
   __shared__ cx<float> tile[L * FL];
-  load_twiddles<float, 128>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
-  pdl_wait();  // the segment partials come from the forward kernel
+  __shared__ int segidx[kFinishMaxBlocks];
+  load_twiddles<float, NT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
   const int cb = blockIdx.x, l0 = blockIdx.y * FL;
   const long long T = (long long)(a.P / TB) * a.nzin;
   const long long x0 = (long long)cb * a.nzin, x1 = x0 + a.nzin - 1;  // first and last item of cb
   const int b_lo = (int)(((x0 + 1) * B - 1) / T), b_hi = (int)(((x1 + 1) * B - 1) / T);
-  const cx<float>* segs = reinterpret_cast<const cx<float>*>(a.seg);
+  const int nseg = b_hi - b_lo + 1;
+  // segment of block b holding column block cb: its first (0) or its second (1)
+  for (int k = threadIdx.x; k < nseg; k += NT) {
+    const int b = b_lo + k;
+    segidx[k] = 2 * b + ((int)((T * b / B) / a.nzin) == cb ? 0 : 1);
+  }
+  pdl_wait();  // the segment partials come from the forward kernel
+  __syncthreads();
+  const cx<float>* segs = reinterpret_cast<const cx<float>*>(a.seg) + l0;
+  int off[NE];
+#pragma unroll
+  for (int k = 0; k < NE; k++) {
+    const int e = threadIdx.x + NT * k;
+    off[k] = (e / FL) * TB + e % FL;
+  }
   cx<float> acc[NE];
 #pragma unroll
   for (int k = 0; k < NE; k++) acc[k] = zero<float>();
-  for (int b = b_lo; b <= b_hi; b++) {  // a segment's loads are all in flight together
-    const int sgb = (int)((T * b / B) / a.nzin) == cb ? 0 : 1;
-    const cx<float>* sp = segs + (long long)(b * 2 + sgb) * L * TB + l0;
-    cx<float> v[NE];
+  for (int s0 = 0; s0 < nseg; s0 += kFinishSegs) {
+    cx<float> v[kFinishSegs][NE];
 #pragma unroll
-    for (int k = 0; k < NE; k++) {
-      const int e = threadIdx.x + 128 * k;
-      v[k] = sp[(e / FL) * TB + e % FL];
+    for (int s = 0; s < kFinishSegs; s++) {
+      if (s0 + s < nseg) {
+        const cx<float>* sp = segs + (long long)segidx[s0 + s] * L * TB;
+#pragma unroll
+        for (int k = 0; k < NE; k++) {
+          const float2 t = __ldcg(reinterpret_cast<const float2*>(sp + off[k]));
+          v[s][k] = mk(t.x, t.y);
+        }
+      }
     }
 #pragma unroll
-    for (int k = 0; k < NE; k++) acc[k] = acc[k] + v[k];
+    for (int s = 0; s < kFinishSegs; s++)
+      if (s0 + s < nseg)
+#pragma unroll
+        for (int k = 0; k < NE; k++) acc[k] = acc[k] + v[s][k];
   }
 #pragma unroll
-  for (int k = 0; k < NE; k++) tile[threadIdx.x + 128 * k] = acc[k];
+  for (int k = 0; k < NE; k++) {
+    const int e = threadIdx.x + NT * k;
+    tile[fin_idx(e / FL, e % FL)] = acc[k];
+  }
   __syncthreads();
   if (threadIdx.x < (L / R1) * FL) {  // first inverse stage: groups g, positions g R1 + q
     const int g = threadIdx.x / FL, l = threadIdx.x % FL;
     cx<float> v[R1];
 #pragma unroll
-    for (int q = 0; q < R1; q++) v[q] = tile[(g * R1 + q) * FL + l];
+    for (int q = 0; q < R1; q++) v[q] = tile[fin_idx(g * R1 + q, l)];
     Dft<float, R1, true>::run(v);
 #pragma unroll
-    for (int q = 0; q < R1; q++) tile[(g * R1 + q) * FL + l] = v[q];
+    for (int q = 0; q < R1; q++) tile[fin_idx(g * R1 + q, l)] = v[q];
   }
   __syncthreads();
   if (threadIdx.x < M0 * FL) {  // last inverse stage (plan stage 0): rows y = j + q M0 < n_in
     const int j = threadIdx.x / FL, l = threadIdx.x % FL;
     cx<float> v[R0];
 #pragma unroll
-    for (int q = 0; q < R0; q++) v[q] = tile[(j + q * M0) * FL + l];
+    for (int q = 0; q < R0; q++) v[q] = tile[fin_idx(j + q * M0, l)];
     apply_twiddles<float, L, 0, true>(v, j, tw);
     Dft<float, R0, true>::run(v);
     cx<float>* o = reinterpret_cast<cx<float>*>(a.yrows) + cb * TB + l0 + l;
@@ -642,12 +672,42 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a, const __grid_con
     for (int r = 0; r <= n; r++) {
       if (r < n) {
         if (cur.cb != cb_held) {
+          if (a.gsrc) {
+            // the forward y transform of the source's column block, here: rows y < n_src of
+            // the x-transformed source plane through the first DIF stage into this round's
+            // tile (the store warps work on the other one), the second stage into registers
+            cx<float>* scr = tiles + (r & 1) * L * TB;
+            {
+              const int line = t % TB, j = t / TB;
+              const cx<float>* g0 = reinterpret_cast<const cx<float>*>(a.gsrc) + (long long)j * a.P + cur.cb * TB + line;
+              cx<float> v[R0];
 #pragma unroll
-          for (int it = 0; it < 2; it++) {
-            const int u = it * kNT + t, line = u % TB, g = u / TB;
-            const cx<float>* s = src + (long long)(g * R1) * a.P + cur.cb * TB + line;
+              for (int q = 0; q < R0 / 2; q++) v[q] = j + q * M0 < a.n_src ? g0[(long long)q * M0 * a.P] : zero<float>();
+              dft32_half_input<false>(v);
+              if (j != 0) {
 #pragma unroll
-            for (int q = 0; q < R1; q++) sv[it][q] = s[q * a.P];
+                for (int q = 1; q < R0; q++) v[q] = cmul(v[q], tw[j * q]);
+              }
+#pragma unroll
+              for (int q = 0; q < R0; q++) scr[(j + q * M0) * TB + line] = v[q];
+            }
+            bar_named(kBarGroup, kNT);
+#pragma unroll
+            for (int it = 0; it < 2; it++) {
+              const int u = it * kNT + t, line = u % TB, g = u / TB;
+#pragma unroll
+              for (int q = 0; q < R1; q++) sv[it][q] = scr[(g * R1 + q) * TB + line];
+              DftF<R1, false>::run(sv[it]);
+            }
+            bar_named(kBarGroup, kNT);  // the tile is free for this round's first stage
+          } else {
+#pragma unroll
+            for (int it = 0; it < 2; it++) {
+              const int u = it * kNT + t, line = u % TB, g = u / TB;
+              const cx<float>* s = src + (long long)(g * R1) * a.P + cur.cb * TB + line;
+#pragma unroll
+              for (int q = 0; q < R1; q++) sv[it][q] = s[q * a.P];
+            }
           }
           cb_held = cur.cb;
         }
@@ -855,12 +915,20 @@ int run_zy_adj(const ZYArgs& a, cudaStream_t s) {
   if (a.nin == 1 && a.nout == 1 && a.nzin == 1 && c >= 0) {
     if constexpr (yz_ws_plan<L>()) {
       CUtensorMap ms;
-      if (a.Ts && a.nzin_total > 0 && slice_map(&ms, a.Ts, (long long)a.nzin_total * (L / 2 + 1), a.P, slice_box_rows<L>()))
+      if (a.Ts && a.nzin_total > 0 && a.n_src <= L / 2 &&
+          slice_map(&ms, a.Ts, (long long)a.nzin_total * (L / 2 + 1), a.P, slice_box_rows<L>()))
         return a.n_out == L / 2 ? launch_adj_ws_c<L, true>(a, c, ms, s) : launch_adj_ws_c<L, false>(a, c, ms, s);
     }
+    if (a.gsrc) return -1;  // the source's y transform is only done on the warp-specialized path
     return launch_adj<L, true>(a, c, s);
   }
+  if (a.gsrc) return -1;
   return launch_adj<L, false>(a, -1, s);
+}
+
+template <int L>
+constexpr bool ws_length() {
+  return yz_ws_plan<L>();
 }
 
 template <int L>
@@ -911,8 +979,8 @@ int launch_fwd_ws(const YZArgs& a, const CUtensorMap& mslice, cudaStream_t s) {
   if (launch_k(k_yz_fwd_ws<L, C, FULL>, dim3(blocks), dim3(NTF), sm, s, a.pdl != 0, a, mslice) != cudaSuccess)
     return -1;
   // the segment partials of each column block, then the target plane's y inverse
-  return launch_k(k_yz_finish<L>, dim3(a.P / TB, TB / kFinishLines), dim3(128), 0, s, a.pdl != 0, a, blocks) ==
-                 cudaSuccess
+  return launch_k(k_yz_finish<L>, dim3(a.P / TB, TB / kFinishLines), dim3(kFinishThreads), 0, s, a.pdl != 0, a,
+                  blocks) == cudaSuccess
              ? 1  // 1: the target plane's y inverse is done
              : -1;
 }
@@ -934,7 +1002,7 @@ int launch_fwd_single(const YZArgs& a, int c, int nch, cudaStream_t s) {
     // needs the segment buffers, the scaled tensor component, and at most two column
     // blocks per block (blocks >= P / TB)
     CUtensorMap ms;
-    if (a.n_in <= L / 2 && a.seg && a.yrows && a.Ts && a.P / TB <= sm_count() &&
+    if (a.n_in <= L / 2 && a.seg && a.yrows && a.Ts && a.P / TB <= sm_count() && sm_count() <= kFinishMaxBlocks &&
         slice_map(&ms, a.Ts, (long long)a.nz_total * (L / 2 + 1), a.P, slice_box_rows<L>()))
       return a.n_in == L / 2 ? launch_fwd_ws_c<L, true>(a, c, ms, s) : launch_fwd_ws_c<L, false>(a, c, ms, s);
   }
@@ -965,6 +1033,17 @@ int launch_zy_adj(int L, const ZYArgs& a, cudaStream_t s) {
 #undef TM_CASE
   }
   return -2;
+}
+
+bool zy_adj_ws_length(int L) {
+  switch (L) {
+#define TM_CASE(LL) \
+  case LL:          \
+    return ws_length<LL>();
+    TM_FOR_EACH_L(TM_CASE)
+#undef TM_CASE
+  }
+  return false;
 }
 
 int launch_yz_fwd(int L, const YZArgs& a, cudaStream_t s) {
