@@ -313,8 +313,11 @@ def alg_bytes(wl, L, direct=True, fused=True, step_fused=False):
     fuse_a = direct and fused and npl == 1 and single
     if fuse_f:
         out["yz_forward"] = s8 * fin * nzd * ny * K + tf * Tzc + s8 * fout * npl * Ly * K
+    # with L = 512 the fused adjoint transforms the source along y itself: it reads the source
+    # rows (x spectra, ny rows) instead of a y-transformed source plane (Ly rows)
+    yfwd_in_adjoint = fuse_a and Ly == 512 and ny <= Ly // 2
     if fuse_a:
-        out["zy_adjoint"] = s8 * ain * npl * Ly * K + ta * Tzc + s8 * aout * nzd * ny * K
+        out["zy_adjoint"] = s8 * ain * npl * (ny if yfwd_in_adjoint else Ly) * K + ta * Tzc + s8 * aout * nzd * ny * K
     # separate y passes: forward of the design planes (unless fused) and of the adjoint
     # source planes; inverse of the target planes and of the design planes (unless fused)
     yf = [s8 * ain * npl * K * (ny + Ly)] + ([] if fuse_f else [s8 * fin * nzd * K * (ny + Ly)])

@@ -525,9 +525,16 @@ int yz_forward(tm_ctx* ctx, const ConvSpec& cs, int zo, cudaStream_t s, bool* yi
   y.status = ctx->dstat;
   y.yrows = ctx->A + cs.aout[0] * ((long long)ctx->nz * ctx->ny * P) + (long long)zo * ctx->ny * P;
   y.pdl = ctx->pdl;
-  Timed t(ctx, KIND_YZF, s);
-  const int r = launch_yz_fwd(Ly, y, s);
-  if (r < 0) CKL(r);
+  int r;
+  {
+    Timed t(ctx, KIND_YZF, s);
+    r = launch_yz_fwd(Ly, y, s);
+    if (r < 0) CKL(r);
+  }
+  if (r == 1) {  // the target plane: partial sums added, inverse y transform
+    Timed t(ctx, KIND_YINV, s);
+    CKL(launch_yz_finish(Ly, y, s));
+  }
   *yinv_done = r == 1;
   return TM_OK;
 }

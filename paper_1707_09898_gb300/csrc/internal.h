@@ -221,6 +221,9 @@ int launch_zy_adj(int L, const ZYArgs& a, cudaStream_t s);
 // spectrum and tensor component, Ts given), the path that can run the source's y transform
 bool zy_adj_ws_length(int L);
 int launch_yz_fwd(int L, const YZArgs& a, cudaStream_t s);
+// after launch_yz_fwd returned 1: the segment partials of each column block added in block
+// order, and the target plane's inverse y transform into a.yrows
+int launch_yz_finish(int L, const YZArgs& a, cudaStream_t s);
 
 int launch_xfwd(int L, const XFwdArgs& a, int ncomp, cudaStream_t s);
 int launch_xinv(int L, const XInvArgs& a, cudaStream_t s);

@@ -976,12 +976,8 @@ int launch_fwd_ws(const YZArgs& a, const CUtensorMap& mslice, cudaStream_t s) {
   }
   const long long items = (long long)(a.P / TB) * a.nzin;
   const int blocks = (int)(items < sm_count() ? items : sm_count());  // one resident block per SM
-  if (launch_k(k_yz_fwd_ws<L, C, FULL>, dim3(blocks), dim3(NTF), sm, s, a.pdl != 0, a, mslice) != cudaSuccess)
-    return -1;
-  // the segment partials of each column block, then the target plane's y inverse
-  return launch_k(k_yz_finish<L>, dim3(a.P / TB, TB / kFinishLines), dim3(kFinishThreads), 0, s, a.pdl != 0, a,
-                  blocks) == cudaSuccess
-             ? 1  // 1: the target plane's y inverse is done
+  return launch_k(k_yz_fwd_ws<L, C, FULL>, dim3(blocks), dim3(NTF), sm, s, a.pdl != 0, a, mslice) == cudaSuccess
+             ? 1  // 1: segment partials written; launch_yz_finish completes the target plane
              : -1;
 }
 template <int L, bool FULL>
@@ -1029,6 +1025,30 @@ int launch_zy_adj(int L, const ZYArgs& a, cudaStream_t s) {
 #define TM_CASE(LL) \
   case LL:          \
     return run_zy_adj<LL>(a, s);
+    TM_FOR_EACH_L(TM_CASE)
+#undef TM_CASE
+  }
+  return -2;
+}
+
+template <int L>
+int run_yz_finish(const YZArgs& a, cudaStream_t s) {
+  if constexpr (yz_ws_plan<L>()) {
+    const long long items = (long long)(a.P / TB) * a.nzin;
+    const int blocks = (int)(items < sm_count() ? items : sm_count());  // the forward's grid
+    return launch_k(k_yz_finish<L>, dim3(a.P / TB, TB / kFinishLines), dim3(kFinishThreads), 0, s, a.pdl != 0, a,
+                    blocks) == cudaSuccess
+               ? 0
+               : -1;
+  }
+  return -1;
+}
+
+int launch_yz_finish(int L, const YZArgs& a, cudaStream_t s) {
+  switch (L) {
+#define TM_CASE(LL) \
+  case LL:          \
+    return run_yz_finish<LL>(a, s);
     TM_FOR_EACH_L(TM_CASE)
 #undef TM_CASE
   }

@@ -31,7 +31,7 @@ def test_main_kernels(model):
     ab, _ = model
     assert ab["x_forward"] == 4 * CELLS + SPEC                    # rho in, one spectrum out
     assert ab["yz_forward"] == SPEC + TZ + PLANE                  # spectra, zz tensor, target plane
-    assert ab["zy_adjoint"] == PLANE + TZ + SPEC                  # source plane, tensor, design planes
+    assert ab["zy_adjoint"] == 8 * N * K + TZ + SPEC              # source rows, tensor, design planes
     assert ab["x_inverse"] == SPEC + 8 * CELLS                    # spectra + rho in, G out
 
 
