@@ -9,10 +9,12 @@
  * is a cudaStream_t. Activations are channels-last [N][D][H][W][C] bfloat16
  * with C a multiple of 16; activation gradients are float32 in the same
  * layout. Weights: float32 master [27][Cin][Cout] with tap =
- * (dz+1)*9 + (dy+1)*3 + (dx+1); bfloat16 copies Wf [27][Cout][Cin] (forward)
- * and Wb [27][Cin][Cout] (backward data). Convolutions are 3x3x3, stride 1,
- * zero padding 1. Return 0, or -1 (bad argument), -4 (CUDA error), -5 (work
- * buffer too small).
+ * (dz+1)*9 + (dy+1)*3 + (dx+1); bfloat16 copies Wf (forward) and Wb (backward
+ * data), each 27*Cin*Cout values packed by tmn_pack_conv_weights in the operand
+ * layout of the tensor-core kernels (opaque to callers: make them with
+ * tmn_pack_conv_weights or tmn_adamw). Convolutions are 3x3x3, stride 1, zero
+ * padding 1. Return 0, or -1 (bad argument), -4 (CUDA error), -5 (work buffer
+ * too small).
  */
 #ifndef TOPOMAG_NET_H
 #define TOPOMAG_NET_H
@@ -23,7 +25,9 @@
 extern "C" {
 #endif
 
-/* out = relu?(conv(in, W) + bias), bfloat16; Cin % 16 == 0, Cout in {16, 32, 64}. */
+/* out = relu?(conv(in, W) + bias), bfloat16; Cin % 16 == 0, Cout in {16, 32, 64}. An implicit
+ * GEMM on the fifth-generation tensor cores: 128 voxels x Cout per block, the float32
+ * accumulator in tensor memory, bfloat16 operands. */
 int tmn_conv3d_forward(const void* in, const void* Wf, const float* bias, void* out, int N, int D, int H, int W,
                        int Cin, int Cout, int relu, void* stream);
 
@@ -31,12 +35,21 @@ int tmn_conv3d_forward(const void* in, const void* Wf, const float* bias, void* 
 int tmn_conv3d_backward_data(const float* dout, const void* Wb, float* din, int N, int D, int H, int W, int Cin,
                              int Cout, int accumulate, void* stream);
 
-/* dW[27][Cin][Cout] and db[Cout] (overwritten) from in (bfloat16) and dout (float32; rounded
- * to bfloat16 for dW, as for the data gradient, float32 for db); tensor cores, float32
- * sums in a fixed order. Cin % 16 == 0, Cout in {16, 32, 64}. work: float32 scratch of
- * work_floats >= 27*Cin*Cout elements (more allows more blocks). */
+/* dW[27][Cin][Cout] and db[Cout] (overwritten) from in (bfloat16) and dout (float32, rounded
+ * to bfloat16 where it is a product operand, as for the data gradient; float32 for db). An
+ * implicit GEMM on the fifth-generation tensor cores with rows (tap, ci), columns co and the
+ * voxels as the reduction; float32 partial sums per block of voxels, added in a fixed order.
+ * Cin % 16 == 0, Cout in {16, 32, 64}. work: float32 scratch of work_floats >=
+ * tmn_conv3d_backward_weight_work(N*D*H*W, Cin, Cout) elements (it holds the bfloat16 copy
+ * of dout and the partials; more allows more blocks); -5 if smaller. */
 int tmn_conv3d_backward_weight(const void* in, const float* dout, float* dW, float* db, float* work,
                                long long work_floats, int N, int D, int H, int W, int Cin, int Cout, void* stream);
+long long tmn_conv3d_backward_weight_work(long long nvox, int Cin, int Cout);
+
+/* Error word of the tensor-core kernels since the last call (bit 0: a bounded wait for a
+ * copy or an MMA ran out, the results of that launch are invalid), then cleared.
+ * Synchronous. */
+int tmn_status(unsigned* out);
 
 /* g[i] = 0 where act[i] <= 0 (ReLU backward through the stored activation). */
 int tmn_relu_backward(float* g, const void* act, long long n, void* stream);

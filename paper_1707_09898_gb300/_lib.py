@@ -60,6 +60,8 @@ _SIGS = {
     "tmn_conv3d_forward": (ctypes.c_int, [vp, vp, vp, vp] + [ctypes.c_int] * 7 + [vp]),
     "tmn_conv3d_backward_data": (ctypes.c_int, [vp, vp, vp] + [ctypes.c_int] * 7 + [vp]),
     "tmn_conv3d_backward_weight": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_longlong] + [ctypes.c_int] * 6 + [vp]),
+    "tmn_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
+    "tmn_conv3d_backward_weight_work": (ctypes.c_longlong, [ctypes.c_longlong, ctypes.c_int, ctypes.c_int]),
     "tmn_relu_backward": (ctypes.c_int, [vp, vp, ctypes.c_longlong, vp]),
     "tmn_pool": (ctypes.c_int, [vp, vp] + [ctypes.c_int] * 5 + [vp]),
     "tmn_pool_backward": (ctypes.c_int, [vp, vp] + [ctypes.c_int] * 6 + [vp]),

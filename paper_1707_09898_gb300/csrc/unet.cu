@@ -6,15 +6,17 @@
 // Layouts: activations channels-last [N][D][H][W][C], C a multiple of 16 (padded
 // channels are zero); bfloat16 activations, float32 activation gradients.
 // Weights: float32 master [27][Cin][Cout] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1));
-// bfloat16 copies Wf [27][Cout][Cin] (forward) and Wb [27][Cin][Cout] (backward).
+// bfloat16 copies Wf (forward) and Wb (backward data) packed in the operand layout of
+// the tensor-core kernels (see pack_f / pack_b below).
 // 3x3x3 convolutions (stride 1, zero padding 1) forward and backward-data are
-// implicit GEMMs on the tensor cores (mma m16n8k16, bfloat16 in, float32
-// accumulate); so are the weight gradients (a GEMM over voxels per tap, the output
-// gradient rounded to bfloat16 as in the data gradient).
+// implicit GEMMs on the fifth-generation tensor cores (tcgen05.mma, bfloat16 in,
+// float32 accumulators in tensor memory); the weight gradients are GEMMs over voxels
+// per tap on mma.sync (the output gradient rounded to bfloat16 as in the data gradient).
 #include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "../../include/topomag_net.h"
+#include "unet_tc.cuh"
 
 namespace {
 
@@ -25,13 +27,6 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 struct Vox {
   int n, z, y, x;
@@ -47,215 +42,376 @@ __device__ __forceinline__ Vox vox_of(long long v, int D, int H, int W) {
   return r;
 }
 
-constexpr int MT = 2;        // 16-voxel m tiles per warp
-constexpr int WARPS = 4;     // warps per block
-constexpr int VB = 16 * MT * WARPS;  // voxels per block
+// Packed bfloat16 weights for the tensor-core kernels: per (tap, 16-channel chunk kc of
+// the reduced dimension) a block of N x 16 values in the MMA's B layout,
+// [k-group (2)][N/8][8 rows][8 elements], rows = output channels of the GEMM.
+// Forward (N = cout, reduced = ci), backward data (N = cin, reduced = co).
+__host__ __device__ __forceinline__ long long pack_f(int tap, int ci, int co, int cin, int cout) {
+  const int kc = ci >> 4, kk = ci & 15;
+  return ((long long)tap * (cin >> 4) + kc) * (16LL * cout) + (kk >> 3) * 8LL * cout + (co >> 3) * 64 + (co & 7) * 8 +
+         (kk & 7);
+}
+__host__ __device__ __forceinline__ long long pack_b(int tap, int ci, int co, int cin, int cout) {
+  const int kc = co >> 4, kk = co & 15;
+  return ((long long)tap * (cout >> 4) + kc) * (16LL * cin) + (kk >> 3) * 8LL * cin + (ci >> 3) * 64 + (ci & 7) * 8 +
+         (kk & 7);
+}
 
-// Forward (MODE 0): out[v][co] = act(sum_{tap,ci} in[v + off][ci] Wf[tap][co][ci] + b[co])
-// Backward data (MODE 1): din[v][ci] = sum_{tap,co} dout[v - off][co] Wb[tap][ci][co]
-// KC = input channels of the GEMM (Cin fwd, Cout bwd); NO = output channels (<= 64).
+// Error word of the tensor-core kernels: bit 0 set when a bounded wait ran out (tmn_status).
+__device__ unsigned g_net_status;
+
+// Implicit-GEMM convolution on tcgen05: a block of 128 threads owns 128 consecutive voxels
+// (the M = 128 rows of the accumulator, one tensor-memory lane per voxel) and all NO output
+// channels (N). The reduction runs over (tap, 16-channel chunk) steps, K = 16 each: every
+// thread gathers its voxel's 16 shifted input channels into the A tile (zero outside the
+// grid), thread 0 copies the step's packed weight block into the B tile (bulk copy,
+// mbarrier) and issues the MMA once the step's operands are in place; S stages of A and B
+// keep the next steps' loads in flight while the tensor core works. The epilogue reads
+// the accumulator from tensor memory (each warp its 32 lanes).
+//   MODE 0 (forward):       out[v][co] = act(sum in[v + off][ci] W[tap][ci][co] + b[co]), bfloat16
+//   MODE 1 (backward data): din[v][ci] (+)= sum dout[v - off][co] W[tap][ci][co], float32
+// KC: channels of the gathered input (cin forward, cout backward).
+constexpr int kTcStages = 4;
+template <int NO>
+__host__ __device__ constexpr unsigned tmem_cols() {
+  return NO <= 32 ? 32u : (NO <= 64 ? 64u : 128u);
+}
+template <int NO>
+constexpr size_t conv_tc_smem() {
+  return (size_t)kTcStages * (128 * 32 + NO * 32) + (2 * kTcStages + 1) * 8 + 16;
+}
 template <int MODE, int NO>
-__global__ void __launch_bounds__(WARPS * 32) k_conv_mma(const void* src, const bf16* Wt, const float* bias, void* dst,
-                                                         int N, int D, int H, int W, int KC, int relu) {
-  constexpr int NT = NO / 8;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const long long nvox = (long long)N * D * H * W;
-  const long long v0 = (long long)blockIdx.x * VB + warp * 16 * MT;
-  Vox rv[MT][2];
-  bool rok[MT][2];
-#pragma unroll
-  for (int m = 0; m < MT; m++)
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const long long v = v0 + m * 16 + g + 8 * h;
-      rok[m][h] = v < nvox;
-      rv[m][h] = vox_of(rok[m][h] ? v : 0, D, H, W);
+__global__ void __launch_bounds__(128) k_conv_tc(const void* src, const bf16* Wc, const float* bias, void* dst,
+                                                 int Nb, int D, int H, int W, int KC, int flag) {
+  using namespace tmk;
+  constexpr int S = kTcStages, AB = 128 * 32, BB = NO * 32;
+  constexpr unsigned NCOLS = tmem_cols<NO>();
+  constexpr unsigned IDESC = idesc_bf16(128, NO);
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* As = smem;                  // [S][2 k-groups][16 row groups][8][16 B]
+  unsigned char* Bs = smem + S * AB;         // [S][2][NO/8][8][16 B]
+  unsigned long long* tma_bar = reinterpret_cast<unsigned long long*>(Bs + S * BB);
+  unsigned long long* mma_bar = tma_bar + S;
+  unsigned* tslot = reinterpret_cast<unsigned*>(mma_bar + S);
+  const int t = threadIdx.x, warp = t >> 5;
+  if (t == 0) {
+    for (int b = 0; b < S; b++) {
+      mbar_init(tma_bar + b, 1);
+      mbar_init(mma_bar + b, 1);
     }
-  float acc[MT][NT][4];
-#pragma unroll
-  for (int m = 0; m < MT; m++)
-#pragma unroll
-    for (int j = 0; j < NT; j++)
-#pragma unroll
-      for (int q = 0; q < 4; q++) acc[m][j][q] = 0.0f;
+    mbar_init_fence();
+  }
+  if (warp == 0) {
+    tmem_alloc(tslot, NCOLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned taddr = *tslot;
 
-  for (int tap = 0; tap < 27; tap++) {
+  const long long nvox = (long long)Nb * D * H * W;
+  const long long v = (long long)blockIdx.x * 128 + t;
+  const bool valid = v < nvox;
+  int vx = 0, vy = 0, vz = 0, vn = 0;
+  if (valid) {
+    long long q = v;
+    vx = (int)(q % W);
+    q /= W;
+    vy = (int)(q % H);
+    q /= H;
+    vz = (int)(q % D);
+    vn = (int)(q / D);
+  }
+  const int nk = KC >> 4, nsteps = 27 * nk;
+  // bounded waits: the first one that runs out flags g_net_status and this thread skips its
+  // later waits, so a broken launch ends in milliseconds instead of spinning on every step
+  bool dead = false;
+  auto wait = [&](unsigned long long* mb, unsigned parity) {
+    if (!dead) dead = !mbar_wait_limit(mb, parity, 1 << 16, &g_net_status);
+  };
+  // this thread's row (m = t) in the A tile: row group t / 8, row t % 8
+  const int arow = (t >> 3) * 128 + (t & 7) * 16;
+  auto load_step = [&](int s, int b) {
+    const int tap = s / nk, kc = s - tap * nk;
     int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
     if (MODE == 1) {
       dz = -dz;
       dy = -dy;
       dx = -dx;
     }
-    long long base[MT][2];
-#pragma unroll
-    for (int m = 0; m < MT; m++)
-#pragma unroll
-      for (int h = 0; h < 2; h++) {
-        const Vox& q = rv[m][h];
-        const int z = q.z + dz, y = q.y + dy, x = q.x + dx;
-        const bool in = rok[m][h] && z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W;
-        base[m][h] = in ? ((((long long)q.n * D + z) * H + y) * W + x) * KC : -1;
+    const int z = vz + dz, y = vy + dy, x = vx + dx;
+    const bool ok = valid && z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W;
+    const long long u = ok ? (((long long)vn * D + z) * H + y) * W + x : 0;
+    unsigned char* a = As + b * AB + arow;
+    if constexpr (MODE == 0) {
+      const bf16* p = reinterpret_cast<const bf16*>(src) + u * KC + kc * 16;
+      cp_async16(a, p, ok ? 16u : 0u);             // channels 0..7: k-group 0
+      cp_async16(a + 2048, p + 8, ok ? 16u : 0u);  // channels 8..15: k-group 1
+    } else {
+      uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+      if (ok) {
+        const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(src) + u * KC + kc * 16);
+        const float4 f0 = p[0], f1 = p[1], f2 = p[2], f3 = p[3];
+        lo = make_uint4(pack2(f0.x, f0.y), pack2(f0.z, f0.w), pack2(f1.x, f1.y), pack2(f1.z, f1.w));
+        hi = make_uint4(pack2(f2.x, f2.y), pack2(f2.z, f2.w), pack2(f3.x, f3.y), pack2(f3.z, f3.w));
       }
-    for (int k0 = 0; k0 < KC; k0 += 16) {
-      uint32_t a[MT][4];
+      *reinterpret_cast<uint4*>(a) = lo;
+      *reinterpret_cast<uint4*>(a + 2048) = hi;
+    }
+    if (t == 0) {
+      mbar_expect_tx(tma_bar + b, BB);
+      bulk_load(Bs + b * BB, Wc + ((long long)tap * nk + kc) * NO * 16, BB, tma_bar + b);
+    }
+  };
+  for (int s = 0; s < S - 1; s++) {  // always S - 1 groups, so that the wait below counts right
+    if (s < nsteps) load_step(s, s);
+    cp_async_commit();
+  }
+  for (int s = 0; s < nsteps; s++) {
+    const int b = s % S;
+    const int sn = s + S - 1;  // its loads go into the buffer the MMA of step s - 1 read
+    if (sn < nsteps) {
+      const int bn = sn % S;
+      if (s >= 1) wait(mma_bar + bn, ((s - 1) / S) & 1);
+      load_step(sn, bn);
+    }
+    cp_async_commit();
+    cp_async_wait<S - 1>();  // this thread's copies of step s have landed
+    fence_proxy_async_smem();  // its A rows, written through the generic proxy, for the tensor core
+    __syncthreads();
+    if (t == 0) {
+      wait(tma_bar + b, (s / S) & 1);  // the weight block
+      tc_fence_after();
+      const uint64_t ad = smem_desc(As + b * AB, 2048, 128);
+      const uint64_t bd = smem_desc(Bs + b * BB, NO * 16, 128);
+      tc_mma(taddr, ad, bd, IDESC, s > 0);
+      tc_commit(mma_bar + b);
+    }
+  }
+  // the last commit arrives once every MMA has completed
+  wait(mma_bar + (nsteps - 1) % S, ((nsteps - 1) / S) & 1);
+  cp_async_wait<0>();
+  tc_fence_after();
+  const unsigned trow = taddr + ((unsigned)(warp * 32) << 16);
 #pragma unroll
-      for (int m = 0; m < MT; m++)
+  for (int c0 = 0; c0 < NO; c0 += 16) {
+    float r[16];
+    tc_ld16(trow + c0, r);
+    tc_wait_ld();
+    if (!valid) continue;
+    if constexpr (MODE == 0) {
+      uint32_t pk[8];
 #pragma unroll
-        for (int r = 0; r < 4; r++) {
-          const int h = r & 1, col = k0 + 2 * t + 8 * (r >> 1);
-          const long long b = base[m][h];
-          if (b < 0) {
-            a[m][r] = 0u;
-          } else if (MODE == 0) {
-            a[m][r] = *reinterpret_cast<const uint32_t*>(reinterpret_cast<const bf16*>(src) + b + col);
-          } else {
-            const float2 f = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(src) + b + col);
-            a[m][r] = pack2(f.x, f.y);
-          }
+      for (int i = 0; i < 8; i++) {
+        float o0 = r[2 * i], o1 = r[2 * i + 1];
+        if (bias) {
+          o0 += bias[c0 + 2 * i];
+          o1 += bias[c0 + 2 * i + 1];
         }
-#pragma unroll
-      for (int j = 0; j < NT; j++) {
-        // Wt[tap][n][k] with k (the reduced channel) contiguous
-        const bf16* wr = Wt + ((long long)tap * NO + j * 8 + g) * KC + k0 + 2 * t;
-        uint32_t b[2];
-        b[0] = *reinterpret_cast<const uint32_t*>(wr);
-        b[1] = *reinterpret_cast<const uint32_t*>(wr + 8);
-#pragma unroll
-        for (int m = 0; m < MT; m++) mma16816(acc[m][j], a[m], b);
-      }
-    }
-  }
-  // epilogue: rows g (c0, c1) and g + 8 (c2, c3), columns j*8 + 2t, +1
-#pragma unroll
-  for (int m = 0; m < MT; m++)
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      if (!rok[m][h]) continue;
-      const long long v = v0 + m * 16 + g + 8 * h;
-#pragma unroll
-      for (int j = 0; j < NT; j++) {
-        const int col = j * 8 + 2 * t;
-        float o0 = acc[m][j][2 * h], o1 = acc[m][j][2 * h + 1];
-        if (MODE == 0) {
-          if (bias) {
-            o0 += bias[col];
-            o1 += bias[col + 1];
-          }
-          if (relu) {
-            o0 = fmaxf(o0, 0.0f);
-            o1 = fmaxf(o1, 0.0f);
-          }
-          *reinterpret_cast<uint32_t*>(reinterpret_cast<bf16*>(dst) + v * NO + col) = pack2(o0, o1);
-        } else {
-          float* d = reinterpret_cast<float*>(dst) + v * NO + col;
-          if (relu) {  // accumulate into an existing gradient
-            d[0] += o0;
-            d[1] += o1;
-          } else {
-            d[0] = o0;
-            d[1] = o1;
-          }
+        if (flag) {
+          o0 = fmaxf(o0, 0.0f);
+          o1 = fmaxf(o1, 0.0f);
         }
+        pk[i] = pack2(o0, o1);
+      }
+      uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(dst) + v * NO + c0);
+      o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    } else {
+      float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(dst) + v * NO + c0);
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        float4 w = make_float4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+        if (flag) {  // accumulate into an existing gradient
+          const float4 e = o[i];
+          w.x += e.x;
+          w.y += e.y;
+          w.z += e.z;
+          w.w += e.w;
+        }
+        o[i] = w;
       }
     }
-}
-
-// dW[tap][ci][co] partial over a voxel range on the tensor cores: for one tap and one
-// 16-channel tile of ci, dW_tile = sum_v in[v + off][ci] dout[v][co] is a 16 x Cout x
-// (voxels) GEMM. Each step stages 64 voxels (shifted input rows, bfloat16; dout rows
-// rounded to bfloat16) in shared memory; warp w takes voxels 16w..16w+15 as the k
-// dimension of one m16n8k16 per 8 columns of co. The four warps' float32 sums are added
-// in a fixed order into one partial per block.
-constexpr int WVD = 64;  // voxels per staging step
-template <int NT>
-__global__ void __launch_bounds__(128) k_conv_dw_mma(const bf16* in, const float* dout, float* part, int N, int D,
-                                                     int H, int W, int Cin, int Cout, int chunks_per_block) {
-  constexpr int CO = NT * 8;
-  __shared__ __align__(16) bf16 sa[WVD][16 + 8];
-  __shared__ __align__(16) bf16 sb[WVD][CO + 8];
-  __shared__ long long srow[WVD];
-  __shared__ float red[4][16][CO];
-  const int tap = blockIdx.y, mt = blockIdx.z;
-  const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const long long nvox = (long long)N * D * H * W;
-  float acc[NT][4];
-#pragma unroll
-  for (int j = 0; j < NT; j++)
-#pragma unroll
-    for (int q = 0; q < 4; q++) acc[j][q] = 0.0f;
-  const long long vstart = (long long)blockIdx.x * chunks_per_block * WVD;
-  for (int cidx = 0; cidx < chunks_per_block; cidx++) {
-    const long long vb = vstart + (long long)cidx * WVD;
-    if (vb >= nvox) break;
-    __syncthreads();
-    if (threadIdx.x < WVD) {  // source row of each staged voxel (-1: outside the grid)
-      const long long v = vb + threadIdx.x;
-      long long src = -1;
-      if (v < nvox) {
-        const Vox q = vox_of(v, D, H, W);
-        const int z = q.z + dz, y = q.y + dy, x = q.x + dx;
-        if (z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W) src = (((long long)q.n * D + z) * H + y) * W + x;
-      }
-      srow[threadIdx.x] = src;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < WVD * 16; i += 128) {
-      const int r = i >> 4, ci = i & 15;
-      const long long src = srow[r];
-      sa[r][ci] = src >= 0 ? in[src * Cin + mt * 16 + ci] : __float2bfloat16(0.0f);
-    }
-    for (int i = threadIdx.x; i < WVD * CO; i += 128) {
-      const int r = i / CO, co = i - r * CO;
-      const long long v = vb + r;
-      sb[r][co] = __float2bfloat16(v < nvox ? dout[v * Cout + co] : 0.0f);
-    }
-    __syncthreads();
-    const int k0 = warp * 16;
-    uint32_t af[4];
-    af[0] = (uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t][g]) | ((uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t + 1][g]) << 16);
-    af[1] = (uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t][g + 8]) |
-            ((uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t + 1][g + 8]) << 16);
-    af[2] = (uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t + 8][g]) |
-            ((uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t + 9][g]) << 16);
-    af[3] = (uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t + 8][g + 8]) |
-            ((uint32_t)__bfloat16_as_ushort(sa[k0 + 2 * t + 9][g + 8]) << 16);
-#pragma unroll
-    for (int j = 0; j < NT; j++) {
-      const int n = j * 8 + g;
-      uint32_t bfr[2];
-      bfr[0] = (uint32_t)__bfloat16_as_ushort(sb[k0 + 2 * t][n]) | ((uint32_t)__bfloat16_as_ushort(sb[k0 + 2 * t + 1][n]) << 16);
-      bfr[1] = (uint32_t)__bfloat16_as_ushort(sb[k0 + 2 * t + 8][n]) |
-               ((uint32_t)__bfloat16_as_ushort(sb[k0 + 2 * t + 9][n]) << 16);
-      mma16816(acc[j], af, bfr);
-    }
   }
-  // rows g (c0, c1) and g + 8 (c2, c3) of the tile, columns j*8 + 2t, +1
-#pragma unroll
-  for (int j = 0; j < NT; j++) {
-    red[warp][g][j * 8 + 2 * t] = acc[j][0];
-    red[warp][g][j * 8 + 2 * t + 1] = acc[j][1];
-    red[warp][g + 8][j * 8 + 2 * t] = acc[j][2];
-    red[warp][g + 8][j * 8 + 2 * t + 1] = acc[j][3];
-  }
+  tc_fence_before();
   __syncthreads();
-  for (int i = threadIdx.x; i < 16 * CO; i += 128) {
-    const int r = i / CO, co = i - r * CO;
-    const float v = ((red[0][r][co] + red[1][r][co]) + red[2][r][co]) + red[3][r][co];
-    part[((long long)blockIdx.x * 27 + tap) * Cin * Cout + (long long)(mt * 16 + r) * Cout + co] = v;
-  }
+  if (warp == 0) tmem_dealloc(taddr, NCOLS);
 }
 
-// sum of the block partials in a fixed order; also the bias gradient
-__global__ void k_dw_reduce(const float* part, int nblk, long long n, float* dW) {
+template <int MODE, int NO>
+int launch_conv_tc(const void* src, const bf16* Wc, const float* bias, void* dst, int Nb, int D, int H, int W, int KC,
+                   int flag, cudaStream_t s) {
+  constexpr size_t sm = conv_tc_smem<NO>();
+  static bool init = false;
+  if (!init) {
+    if (cudaFuncSetAttribute(k_conv_tc<MODE, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+      return -4;
+    init = true;
+  }
+  const long long nvox = (long long)Nb * D * H * W;
+  const int blocks = (int)((nvox + 127) / 128);
+  if (blocks > 0) k_conv_tc<MODE, NO><<<blocks, 128, sm, s>>>(src, Wc, bias, dst, Nb, D, H, W, KC, flag);
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : -4;
+}
+
+// Weight gradient on tcgen05: dW[tap][ci][co] = sum_v in[v + off(tap)][ci] q(dout[v][co]),
+// a GEMM with rows (tap, ci), columns co and the voxels as the reduction. A block owns one
+// row tile of 128 = 8 taps x 16 input channels (tile = (tap group, channel chunk)) and a
+// range of voxels, 16 per MMA (K = 16); its float32 accumulator (128 x NO) lives in tensor
+// memory and is written out as one partial, and k_dw_reduce_tc adds the partials in block
+// order. Both operands are MN-major, so the channels-last rows go into shared memory as
+// they are: A gets each (tap, voxel)'s 16 shifted input channels (two 16-byte pieces), B
+// each voxel's NO output-gradient channels, taken from a bfloat16 copy made beforehand
+// (rounded to nearest even, the operand precision of every product).
+template <int NO>
+constexpr size_t dw_tc_smem() {
+  return (size_t)kTcStages * (128 * 32 + NO * 32) + (2 * kTcStages + 1) * 8 + 16;
+}
+template <int NO>
+__global__ void __launch_bounds__(128) k_conv_dw_tc(const bf16* in, const bf16* g16, float* part, int Nb, int D,
+                                                    int H, int W, int Cin, long long chunks_per_block) {
+  using namespace tmk;
+  constexpr int S = kTcStages, AB = 128 * 32, BB = NO * 32, PG = NO / 8;
+  constexpr unsigned NCOLS = tmem_cols<NO>();
+  constexpr unsigned IDESC = idesc_bf16(128, NO, true);
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* As = smem;           // [S][k-group (2)][16 row groups][8 k-rows][16 B]
+  unsigned char* Bs = smem + S * AB;  // [S][2][PG][8][16 B]
+  unsigned long long* mma_bar = reinterpret_cast<unsigned long long*>(Bs + S * BB);
+  unsigned* tslot = reinterpret_cast<unsigned*>(mma_bar + S);
+  const int t = threadIdx.x, warp = t >> 5;
+  if (t == 0) {
+    for (int b = 0; b < S; b++) mbar_init(mma_bar + b, 1);
+    mbar_init_fence();
+  }
+  if (warp == 0) {
+    tmem_alloc(tslot, NCOLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned taddr = *tslot;
+  bool dead = false;
+  auto wait = [&](unsigned long long* mb, unsigned parity) {
+    if (!dead) dead = !mbar_wait_limit(mb, parity, 1 << 16, &g_net_status);
+  };
+  const long long nvox = (long long)Nb * D * H * W;
+  const int tile = blockIdx.y, ncc = Cin >> 4;
+  const int tg = tile / ncc, cc = tile - tg * ncc;
+  // A: this thread's (tap, voxel) = (8 tg + t / 16, t % 16) of each chunk
+  const int tap = 8 * tg + (t >> 4), ka = t & 15;
+  const bool tap_ok = tap < 27;
+  const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+  const int aoff = (t >> 4) * 2 * 128 + (ka >> 3) * 2048 + (ka & 7) * 16;
+  // B: this thread's piece (voxel kb, 8 channels pg) of each chunk, if t < 16 PG
+  const int kb = t / PG, pg = t - kb * PG;
+  const int boff = pg * 128 + (kb >> 3) * (PG * 128) + (kb & 7) * 16;
+  const long long c0 = (long long)blockIdx.x * chunks_per_block;
+  const long long nch = (nvox + 15) / 16;
+  const long long c1 = c0 + chunks_per_block < nch ? c0 + chunks_per_block : nch;
+  const int nsteps = c1 > c0 ? (int)(c1 - c0) : 0;
+  auto load_step = [&](int s, int b) {
+    const long long v0 = (c0 + s) * 16;
+    {
+      const long long v = v0 + ka;
+      bool ok = tap_ok && v < nvox;
+      long long u = 0;
+      if (ok) {
+        long long q = v;
+        const int x = (int)(q % W) + dx;
+        q /= W;
+        const int y = (int)(q % H) + dy;
+        q /= H;
+        const int z = (int)(q % D) + dz;
+        const long long n = q / D;
+        ok = z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W;
+        u = ok ? ((n * D + z) * H + y) * W + x : 0;
+      }
+      const bf16* src = in + u * Cin + cc * 16;
+      unsigned char* a = As + b * AB + aoff;
+      cp_async16(a, src, ok ? 16u : 0u);            // channels 0..7: row group 2 (t / 16)
+      cp_async16(a + 128, src + 8, ok ? 16u : 0u);  // channels 8..15: the next row group
+    }
+    if (t < 16 * PG) {
+      const long long v = v0 + kb;
+      const bool ok = v < nvox;
+      cp_async16(Bs + b * BB + boff, g16 + (ok ? v : 0) * NO + pg * 8, ok ? 16u : 0u);
+    }
+  };
+  for (int s = 0; s < S - 1; s++) {  // always S - 1 groups, so that the wait below counts right
+    if (s < nsteps) load_step(s, s);
+    cp_async_commit();
+  }
+  for (int s = 0; s < nsteps; s++) {
+    const int b = s % S;
+    const int sn = s + S - 1;
+    if (sn < nsteps) {
+      const int bn = sn % S;
+      if (s >= 1) wait(mma_bar + bn, ((s - 1) / S) & 1);
+      load_step(sn, bn);
+    }
+    cp_async_commit();
+    cp_async_wait<S - 1>();
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (t == 0) {
+      tc_fence_after();
+      const uint64_t ad = smem_desc(As + b * AB, 2048, 128);
+      const uint64_t bd = smem_desc(Bs + b * BB, PG * 128, 128);
+      tc_mma(taddr, ad, bd, IDESC, s > 0);
+      tc_commit(mma_bar + b);
+    }
+  }
+  if (nsteps > 0) wait(mma_bar + (nsteps - 1) % S, ((nsteps - 1) / S) & 1);
+  cp_async_wait<0>();
+  tc_fence_after();
+  // row t of the tile: tap 8 tg + t / 16, channel 16 cc + t % 16
+  float* pr = part + (((long long)blockIdx.x * gridDim.y + tile) * 128 + t) * NO;
+  const unsigned trow = taddr + ((unsigned)(warp * 32) << 16);
+#pragma unroll
+  for (int q0 = 0; q0 < NO; q0 += 16) {
+    float r[16];
+    tc_ld16(trow + q0, r);
+    tc_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; i++) r[i] = nsteps > 0 ? r[i] : 0.0f;
+    float4* o = reinterpret_cast<float4*>(pr + q0);
+#pragma unroll
+    for (int i = 0; i < 4; i++) o[i] = make_float4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(taddr, NCOLS);
+}
+
+// dW[tap][ci][co] = sum over the voxel blocks p (in order) of part[p][tile][row][co]
+__global__ void k_dw_reduce_tc(const float* part, int nblk, int ntiles, int Cin, int Cout, float* dW) {
+  const long long n = 27LL * Cin * Cout;
+  const int ncc = Cin >> 4;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int tap = (int)(i / ((long long)Cin * Cout));
+    const int r = (int)(i - (long long)tap * Cin * Cout), ci = r / Cout, co = r - ci * Cout;
+    const int tile = (tap >> 3) * ncc + (ci >> 4), row = (tap & 7) * 16 + (ci & 15);
     float s = 0.0f;
-    for (int b = 0; b < nblk; b++) s += part[(long long)b * n + i];
+    for (int b = 0; b < nblk; b++) s += part[(((long long)b * ntiles + tile) * 128 + row) * Cout + co];
     dW[i] = s;
   }
 }
+
+// bfloat16 copy of a float32 array (round to nearest even), two values per thread step
+__global__ void k_to_bf16(const float* x, bf16* y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; 2 * i < n; i += (long long)gridDim.x * blockDim.x) {
+    if (2 * i + 1 < n) {
+      *reinterpret_cast<uint32_t*>(y + 2 * i) = pack2(x[2 * i], x[2 * i + 1]);
+    } else {
+      y[2 * i] = __float2bfloat16(x[2 * i]);
+    }
+  }
+}
+
+// the bias gradient: float32 sum over the voxels of the unrounded output gradient
 __global__ void k_db(const float* dout, long long nvox, int C, float* db) {
   const int c = blockIdx.x;
   __shared__ float red[256];
@@ -393,10 +549,10 @@ __global__ void k_adamw(float* w, const float* g, float* m, float* v, long long 
     wi -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * wi);
     w[i] = wi;
     if (wf) {  // i = (tap, ci, co)
-      const long long tap = i / ((long long)cin * cout);
-      const int r = (int)(i - tap * cin * cout), ci = r / cout, co = r - ci * cout;
-      wf[(tap * cout + co) * cin + ci] = __float2bfloat16(wi);
-      wb[(tap * cin + ci) * cout + co] = __float2bfloat16(wi);
+      const int tap = (int)(i / ((long long)cin * cout));
+      const int r = (int)(i - (long long)tap * cin * cout), ci = r / cout, co = r - ci * cout;
+      wf[pack_f(tap, ci, co, cin, cout)] = __float2bfloat16(wi);
+      wb[pack_b(tap, ci, co, cin, cout)] = __float2bfloat16(wi);
     }
   }
 }
@@ -405,10 +561,10 @@ __global__ void k_adamw(float* w, const float* g, float* m, float* v, long long 
 __global__ void k_pack_w(const float* w, bf16* wf, bf16* wb, int cin, int cout) {
   const long long n = 27LL * cin * cout;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const long long tap = i / ((long long)cin * cout);
-    const int r = (int)(i - tap * cin * cout), ci = r / cout, co = r - ci * cout;
-    wf[(tap * cout + co) * cin + ci] = __float2bfloat16(w[i]);
-    wb[(tap * cin + ci) * cout + co] = __float2bfloat16(w[i]);
+    const int tap = (int)(i / ((long long)cin * cout));
+    const int r = (int)(i - (long long)tap * cin * cout), ci = r / cout, co = r - ci * cout;
+    wf[pack_f(tap, ci, co, cin, cout)] = __float2bfloat16(w[i]);
+    wb[pack_b(tap, ci, co, cin, cout)] = __float2bfloat16(w[i]);
   }
 }
 
@@ -443,31 +599,40 @@ extern "C" {
 
 int tmn_conv3d_forward(const void* in, const void* Wf, const float* bias, void* out, int N, int D, int H, int W,
                        int Cin, int Cout, int relu, void* stream) {
-  if (!in || !Wf || !out || Cin % 16 || (Cout != 16 && Cout != 32 && Cout != 64)) return -1;
-  const long long nvox = (long long)N * D * H * W;
-  const int blocks = (int)((nvox + VB - 1) / VB);
+  if (!in || !Wf || !out || Cin % 16 || Cin < 16 || (Cout != 16 && Cout != 32 && Cout != 64)) return -1;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const bf16* w = reinterpret_cast<const bf16*>(Wf);
-  if (Cout == 16) k_conv_mma<0, 16><<<blocks, WARPS * 32, 0, s>>>(in, w, bias, out, N, D, H, W, Cin, relu);
-  if (Cout == 32) k_conv_mma<0, 32><<<blocks, WARPS * 32, 0, s>>>(in, w, bias, out, N, D, H, W, Cin, relu);
-  if (Cout == 64) k_conv_mma<0, 64><<<blocks, WARPS * 32, 0, s>>>(in, w, bias, out, N, D, H, W, Cin, relu);
-  return ok();
+  if (Cout == 16) return launch_conv_tc<0, 16>(in, w, bias, out, N, D, H, W, Cin, relu, s);
+  if (Cout == 32) return launch_conv_tc<0, 32>(in, w, bias, out, N, D, H, W, Cin, relu, s);
+  return launch_conv_tc<0, 64>(in, w, bias, out, N, D, H, W, Cin, relu, s);
 }
 
 int tmn_conv3d_backward_data(const float* dout, const void* Wb, float* din, int N, int D, int H, int W, int Cin,
                              int Cout, int accumulate, void* stream) {
-  if (!dout || !Wb || !din || Cout % 16 || (Cin != 16 && Cin != 32 && Cin != 48 && Cin != 64 && Cin != 96)) return -1;
-  const long long nvox = (long long)N * D * H * W;
-  const int blocks = (int)((nvox + VB - 1) / VB);
+  if (!dout || !Wb || !din || Cout % 16 || Cout < 16 || (Cin != 16 && Cin != 32 && Cin != 48 && Cin != 64 && Cin != 96))
+    return -1;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const bf16* w = reinterpret_cast<const bf16*>(Wb);
-  // GEMM over k = (tap, co) with Wb[tap][ci][co]: N-side width Cin
-  if (Cin == 16) k_conv_mma<1, 16><<<blocks, WARPS * 32, 0, s>>>(dout, w, nullptr, din, N, D, H, W, Cout, accumulate);
-  if (Cin == 32) k_conv_mma<1, 32><<<blocks, WARPS * 32, 0, s>>>(dout, w, nullptr, din, N, D, H, W, Cout, accumulate);
-  if (Cin == 48) k_conv_mma<1, 48><<<blocks, WARPS * 32, 0, s>>>(dout, w, nullptr, din, N, D, H, W, Cout, accumulate);
-  if (Cin == 64) k_conv_mma<1, 64><<<blocks, WARPS * 32, 0, s>>>(dout, w, nullptr, din, N, D, H, W, Cout, accumulate);
-  if (Cin == 96) k_conv_mma<1, 96><<<blocks, WARPS * 32, 0, s>>>(dout, w, nullptr, din, N, D, H, W, Cout, accumulate);
-  return ok();
+  // GEMM over k = (tap, co) with the output channels ci as the N side
+  if (Cin == 16) return launch_conv_tc<1, 16>(dout, w, nullptr, din, N, D, H, W, Cout, accumulate, s);
+  if (Cin == 32) return launch_conv_tc<1, 32>(dout, w, nullptr, din, N, D, H, W, Cout, accumulate, s);
+  if (Cin == 48) return launch_conv_tc<1, 48>(dout, w, nullptr, din, N, D, H, W, Cout, accumulate, s);
+  if (Cin == 64) return launch_conv_tc<1, 64>(dout, w, nullptr, din, N, D, H, W, Cout, accumulate, s);
+  return launch_conv_tc<1, 96>(dout, w, nullptr, din, N, D, H, W, Cout, accumulate, s);
+}
+
+int tmn_status(unsigned* out) {
+  if (!out) return -1;
+  unsigned z = 0;
+  if (cudaMemcpyFromSymbol(out, g_net_status, sizeof(unsigned)) != cudaSuccess) return -4;
+  if (cudaMemcpyToSymbol(g_net_status, &z, sizeof(unsigned)) != cudaSuccess) return -4;
+  return 0;
+}
+
+long long tmn_conv3d_backward_weight_work(long long nvox, int Cin, int Cout) {
+  if (nvox < 1 || Cin < 16 || Cin % 16 || Cout < 16 || Cout % 16) return -1;
+  const long long copy = (nvox * Cout + 1) / 2;         // floats holding the bfloat16 copy of dout
+  return (copy + 3) / 4 * 4 + 4LL * (Cin / 16) * 128 * Cout;  // partials from a 16-byte boundary, one set
 }
 
 int tmn_conv3d_backward_weight(const void* in, const float* dout, float* dW, float* db, float* work,
@@ -475,20 +640,43 @@ int tmn_conv3d_backward_weight(const void* in, const float* dout, float* dW, flo
   if (!in || !dout || !dW || !db || !work || Cin % 16 || Cin < 16 || (Cout != 16 && Cout != 32 && Cout != 64))
     return -1;
   const long long nvox = (long long)N * D * H * W;
-  const long long chunks = (nvox + WVD - 1) / WVD;
-  const long long per_blk = 27LL * Cin * Cout;
-  int nblk = (int)(work_floats / per_blk);
-  if (nblk > 64) nblk = 64;
-  if (nblk < 1) return -5;
-  const int cpb = (int)((chunks + nblk - 1) / nblk);
-  nblk = (int)((chunks + cpb - 1) / cpb);
+  if (nvox < 1) return -1;
+  if (work_floats < tmn_conv3d_backward_weight_work(nvox, Cin, Cout)) return -5;
+  const long long pofs = ((nvox * Cout + 1) / 2 + 3) / 4 * 4;
+  const int tiles = 4 * (Cin / 16);
+  const long long per_blk = (long long)tiles * 128 * Cout;
+  // voxel blocks: about two blocks per SM over all tiles, no more than the work buffer holds
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
+  }
+  const long long chunks = (nvox + 15) / 16;
+  long long nblk = (work_floats - pofs) / per_blk;
+  const long long want = (2LL * nsm + tiles - 1) / tiles;
+  if (nblk > want) nblk = want;
+  if (nblk > chunks) nblk = chunks;
+  const long long cpb = (chunks + nblk - 1) / nblk;
+  nblk = (chunks + cpb - 1) / cpb;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const dim3 grid(nblk, 27, Cin / 16);
+  bf16* g16 = reinterpret_cast<bf16*>(work);
+  float* part = work + pofs;
+  k_to_bf16<<<grid_of(nvox * Cout / 2 + 1), 256, 0, s>>>(dout, g16, nvox * Cout);
+  const dim3 grid((unsigned)nblk, (unsigned)tiles);
   const bf16* x = reinterpret_cast<const bf16*>(in);
-  if (Cout == 16) k_conv_dw_mma<2><<<grid, 128, 0, s>>>(x, dout, work, N, D, H, W, Cin, Cout, cpb);
-  if (Cout == 32) k_conv_dw_mma<4><<<grid, 128, 0, s>>>(x, dout, work, N, D, H, W, Cin, Cout, cpb);
-  if (Cout == 64) k_conv_dw_mma<8><<<grid, 128, 0, s>>>(x, dout, work, N, D, H, W, Cin, Cout, cpb);
-  k_dw_reduce<<<grid_of(per_blk), 256, 0, s>>>(work, nblk, per_blk, dW);
+  int r = 0;
+  auto run = [&](auto kernel, size_t sm) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+      r = -4;
+    else
+      kernel<<<grid, 128, sm, s>>>(x, g16, part, N, D, H, W, Cin, cpb);
+  };
+  if (Cout == 16) run(k_conv_dw_tc<16>, dw_tc_smem<16>());
+  if (Cout == 32) run(k_conv_dw_tc<32>, dw_tc_smem<32>());
+  if (Cout == 64) run(k_conv_dw_tc<64>, dw_tc_smem<64>());
+  if (r) return r;
+  k_dw_reduce_tc<<<grid_of(27LL * Cin * Cout), 256, 0, s>>>(part, (int)nblk, tiles, Cin, Cout, dW);
   k_db<<<Cout, 256, 0, s>>>(dout, nvox, Cout, db);
   return ok();
 }

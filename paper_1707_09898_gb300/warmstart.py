@@ -30,6 +30,7 @@ from . import _lib
 
 LAYERS = (("e1a", 16, 16), ("e1b", 16, 16), ("e2a", 16, 32), ("e2b", 32, 32), ("b1", 32, 64), ("b2", 64, 64),
           ("d2a", 96, 32), ("d2b", 32, 32), ("d1a", 48, 16), ("d1b", 16, 16))
+LEVEL = {"e1a": 1, "e1b": 1, "e2a": 2, "e2b": 2, "b1": 4, "b2": 4, "d2a": 2, "d2b": 2, "d1a": 1, "d1b": 1}
 C_IN = 16     # padded input channels (3 used)
 C_USED = 3
 BF16, F32, U8 = torch.bfloat16, torch.float32, torch.uint8
@@ -157,7 +158,11 @@ class WarmStartNet:
                   "e1a": a(g1, 16, F32), "d2b": a(g2, 32, F32), "d2a": a(g2, 32, F32), "u2": a(g2, 96, F32),
                   "e2": a(g2, 32, F32), "e2a": a(g2, 32, F32), "p1": a(g2, 16, F32), "b2": a(g3, 64, F32),
                   "b1": a(g3, 64, F32), "p2": a(g3, 32, F32)}
-        self.work = torch.empty(64 * 27 * 96 * 32, dtype=F32, device=self.dev)
+        # weight-gradient scratch: the bfloat16 copy of the largest output gradient plus the
+        # per-block partial sums of about two blocks per SM (2 * 160 * 128 * Cout floats)
+        nwork = max(self.L.tmn_conv3d_backward_weight_work(N * (D // LEVEL[n]) * (H // LEVEL[n]) * (W // LEVEL[n]),
+                                                           ci, co) for n, ci, co in LAYERS)
+        self.work = torch.empty(nwork + 2 * 160 * 128 * 64, dtype=F32, device=self.dev)
         self.hwork = torch.empty(256 * 18, dtype=F32, device=self.dev)
         self._N = N
 
@@ -447,7 +452,7 @@ def conv_profile(net, N=4, reps=10):
     net.forward(x)
     net.backward(torch.zeros((N, D, H, W), dtype=F32, device=net.dev))
     L, s = net.L, _stream(net.dev)
-    dims = {"e1a": 1, "e1b": 1, "e2a": 2, "e2b": 2, "b1": 4, "b2": 4, "d2a": 2, "d2b": 2, "d1a": 1, "d1b": 1}
+    dims = LEVEL
     inp = {"e1a": "x", "e1b": "e1a", "e2a": "p1", "e2b": "e2a", "b1": "p2", "b2": "b1", "d2a": "u2", "d2b": "d2a",
            "d1a": "u1", "d1b": "d1a"}
     out = []

@@ -66,9 +66,20 @@ def f32(a):
     return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(DEV)
 
 
-def wf_wb(W):
-    """Wf [27][cout][cin] and Wb [27][cin][cout] bfloat16 copies of W [27][cin][cout]."""
-    return to_bf16_dev(W.transpose(0, 2, 1)), to_bf16_dev(W)
+def wf_wb(L, W):
+    """Packed bfloat16 weight copies (forward, backward data) of W [27][cin][cout], made by
+    the library's packing kernel."""
+    cin, cout = W.shape[1], W.shape[2]
+    wf = torch.empty(27 * cin * cout, dtype=torch.bfloat16, device=DEV)
+    wb = torch.empty_like(wf)
+    assert L.tmn_pack_conv_weights(p(f32(W)), p(wf), p(wb), cin, cout, S()) == 0
+    return wf, wb
+
+
+def net_status(L):
+    st = ctypes.c_uint(1)
+    assert L.tmn_status(ctypes.byref(st)) == 0
+    return st.value
 
 
 DIMS = (2, 5, 6, 7)  # N, D, H, W: 420 voxels
@@ -82,7 +93,7 @@ def test_conv_forward(L, cin, cout):
     b = rng.normal(0, 0.1, size=cout).astype(np.float32).astype(np.float64)
     out = torch.empty(DIMS + (cout,), dtype=torch.bfloat16, device=DEV)
     for relu in (0, 1):
-        Wf, _ = wf_wb(W)
+        Wf, _ = wf_wb(L, W)
         assert L.tmn_conv3d_forward(p(to_bf16_dev(x)), p(Wf), p(f32(b)), p(out), *DIMS, cin, cout, relu, S()) == 0
         got = out.float().cpu().numpy()
         ref = U.conv(x, W, b)
@@ -90,6 +101,7 @@ def test_conv_forward(L, cin, cout):
             ref = np.maximum(ref, 0)
         bound = U.conv(np.abs(x), np.abs(W), np.abs(b))
         assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-5 * bound)
+    assert net_status(L) == 0
 
 
 @pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (32, 64), (48, 16), (96, 32), (64, 64)])
@@ -99,7 +111,7 @@ def test_conv_backward_data_and_weight(L, cin, cout):
     W = bf16_round(rng.normal(0, 0.1, size=(27, cin, cout)))
     g = bf16_round(rng.normal(size=DIMS + (cout,)))  # the data gradient rounds dout to bfloat16
     dx_ref, dW_ref, db_ref = U.conv_backward(x, W, g)
-    _, Wb = wf_wb(W)
+    _, Wb = wf_wb(L, W)
     gd = f32(g)
     din = torch.full(DIMS + (cin,), 0.5, dtype=torch.float32, device=DEV)
     assert L.tmn_conv3d_backward_data(p(gd), p(Wb), p(din), *DIMS, cin, cout, 0, S()) == 0
@@ -107,6 +119,7 @@ def test_conv_backward_data_and_weight(L, cin, cout):
     assert np.all(np.abs(din.cpu().numpy() - dx_ref) <= 1e-5 * bound + 1e-30)
     assert L.tmn_conv3d_backward_data(p(gd), p(Wb), p(din), *DIMS, cin, cout, 1, S()) == 0  # accumulate
     assert np.all(np.abs(din.cpu().numpy() - 2 * dx_ref) <= 2e-5 * bound + 1e-30)
+    assert net_status(L) == 0
     # weight gradient: float32 sums of bfloat16 products (dout rounded to bfloat16, as the
     # kernel does; the bias gradient sums the float32 values)
     g32 = bf16_round(rng.normal(size=DIMS + (cout,)))
@@ -114,13 +127,17 @@ def test_conv_backward_data_and_weight(L, cin, cout):
     _, dWb, dbb = U.conv_backward(np.abs(x), W, np.abs(g32))
     dW = torch.empty(27, cin, cout, device=DEV)
     db = torch.empty(cout, device=DEV)
-    for blocks in (1, 5, 64):  # one partial per block, reduced in a fixed order
-        work = torch.empty(blocks * 27 * cin * cout, device=DEV)
+    nvox = int(np.prod(DIMS))
+    base = L.tmn_conv3d_backward_weight_work(nvox, cin, cout)
+    per_blk = 4 * (cin // 16) * 128 * cout
+    for blocks in (1, 2, 9, 27):  # one partial set per block of voxels (27: one 16-voxel chunk each)
+        work = torch.empty(base + (blocks - 1) * per_blk, device=DEV)
         assert L.tmn_conv3d_backward_weight(p(to_bf16_dev(x)), p(f32(g32)), p(dW), p(db), p(work), work.numel(),
                                             *DIMS, cin, cout, S()) == 0
         assert np.all(np.abs(dW.cpu().numpy() - dW_ref) <= 1e-5 * dWb + 1e-30)
         assert np.all(np.abs(db.cpu().numpy() - db_ref) <= 1e-5 * dbb + 1e-30)
-    work = torch.empty(27 * cin * cout - 1, device=DEV)
+    assert net_status(L) == 0
+    work = torch.empty(base - 1, device=DEV)
     assert L.tmn_conv3d_backward_weight(p(to_bf16_dev(x)), p(f32(g32)), p(dW), p(db), p(work), work.numel(), *DIMS,
                                         cin, cout, S()) == -5
 
@@ -209,12 +226,32 @@ def test_adamw_and_weight_copies(L):
         ref, m, v = U.adamw(ref, g.astype(np.float64), m, v, step, 1e-2, 0.9, 0.999, 1e-8, 1e-2)
         got = wd.cpu().numpy()
         assert np.max(np.abs(got - ref)) <= 1e-5 * np.abs(ref).max()
-    # the bfloat16 copies are the round-to-nearest-even images of the masters, in both layouts
+    # the bfloat16 copies are the round-to-nearest-even images of the masters, in both packed layouts
     rb = bf16_round(got)
-    assert np.array_equal(wb.float().cpu().numpy(), rb)
-    assert np.array_equal(wf.float().cpu().numpy(), rb.transpose(0, 2, 1))
+    pf, pb = packed_layouts(rb)
+    assert np.array_equal(wf.float().cpu().numpy().ravel(), pf)
+    assert np.array_equal(wb.float().cpu().numpy().ravel(), pb)
     assert L.tmn_pack_conv_weights(p(f32(w)), p(wf), p(wb), cin, cout, S()) == 0
-    assert np.array_equal(wb.float().cpu().numpy(), bf16_round(w))
+    pf, pb = packed_layouts(bf16_round(w))
+    assert np.array_equal(wf.float().cpu().numpy().ravel(), pf)
+    assert np.array_equal(wb.float().cpu().numpy().ravel(), pb)
+
+
+def packed_layouts(W):
+    """The tensor-core operand layouts of W [27][cin][cout], written out: per tap and 16-wide
+    chunk of the reduced channels, [k-group (2)][GEMM row / 8][8 rows][8 reduced channels];
+    forward rows = co (reduced ci), backward-data rows = ci (reduced co)."""
+    _, cin, cout = W.shape
+    tap, ci, co = np.meshgrid(np.arange(27), np.arange(cin), np.arange(cout), indexing="ij")
+    f = ((tap * (cin // 16) + ci // 16) * 16 * cout + ((ci % 16) // 8) * 8 * cout + (co // 8) * 64 + (co % 8) * 8
+         + ci % 8)
+    b = ((tap * (cout // 16) + co // 16) * 16 * cin + ((co % 16) // 8) * 8 * cin + (ci // 8) * 64 + (ci % 8) * 8
+         + co % 8)
+    pf, pb = np.zeros(W.size), np.zeros(W.size)
+    pf[f.ravel()] = W.ravel()
+    pb[b.ravel()] = W.ravel()
+    assert len(set(f.ravel())) == W.size and len(set(b.ravel())) == W.size  # both are permutations
+    return pf, pb
 
 
 def test_spec_input(L):
