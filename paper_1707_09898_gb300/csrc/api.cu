@@ -1,6 +1,7 @@
 // C ABI of libtopomag: context, workspace and the pass sequences of the
 // stray-field operator D, its adjoint, the fused objective/gradient and the
 // projected update. Every array argument is a caller-owned device pointer.
+#include <nvtx3/nvToolsExt.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -129,16 +130,23 @@ bool injected(const char* name) {
   return true;
 }
 // Entry points called from inside another one (tm_evaluate_step -> tm_evaluate) do not
-// count: only calls made by the caller of the library do.
+// count: only calls made by the caller of the library do. Each entry point is also an
+// NVTX range named after it (free when no profiler is attached).
 thread_local int tl_depth = 0;
 struct DepthGuard {
-  DepthGuard() { tl_depth++; }
-  ~DepthGuard() { tl_depth--; }
+  explicit DepthGuard(const char* name) {
+    tl_depth++;
+    nvtxRangePushA(name);
+  }
+  ~DepthGuard() {
+    nvtxRangePop();
+    tl_depth--;
+  }
 };
 #define INJECT(ctx, name)                                                                       \
   if (tl_depth == 0 && injected(name))                                                          \
     return fail(ctx, TM_ERR_INJECTED, "%s: failure injected by tm_inject_fault", name);         \
-  DepthGuard depth_guard_
+  DepthGuard depth_guard_(name)
 
 // Reads the device status word (synchronising `s`); a set bit 0 means that a bounded
 // wait ran out in some kernel since the word was last cleared.

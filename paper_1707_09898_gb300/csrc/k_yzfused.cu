@@ -359,16 +359,20 @@ __device__ __forceinline__ cx<float> ws_apply(float f, cx<float> v) {  // (-i f)
 }
 
 // The stage-0 twiddle of position j + q M0 (= g R1 + q' with j = q', q = g) is W^(j q),
-// applied after the first DIF stage or before the last DIT stage. The two groups share
-// that work: the stage-0 warps take q < R0/2, the last-stage warps (their second unit,
-// g >= R0/2) the rest.
-template <int L, bool INV>
+// applied after the first DIF stage or before the last DIT stage, by either group: in the
+// forward all of it by the accumulate warps (their stage-0 partners set the pace: moving
+// the work the other way cost 8 us per launch), in the adjoint shared, q < R0/2 by the
+// store warps and the rest by the load warps (their second unit, g >= R0/2); the other
+// splits measured no faster there.
+// TW: 0 = q < R0/2 here (the rest by the other group), 1 = all, 2 = none
+template <int L, bool INV, int TW>
 __device__ __forceinline__ void twiddles_lo(cx<float>* v, int j, const cx<float>* tw) {
   constexpr int R0 = StageShape<L, 0>::R;
-  if (j == 0) return;
+  if (TW == 2 || j == 0) return;
 #pragma unroll
-  for (int q = 1; q < R0 / 2; q++) v[q] = INV ? cmulc(v[q], tw[j * q]) : cmul(v[q], tw[j * q]);
+  for (int q = 1; q < (TW == 1 ? R0 : R0 / 2); q++) v[q] = INV ? cmulc(v[q], tw[j * q]) : cmul(v[q], tw[j * q]);
 }
+constexpr int kFwdTw = 2, kAdjTw = 0;
 template <int L, bool INV>
 __device__ __forceinline__ void twiddles_hi(cx<float>* v, int g, const cx<float>* tw) {
   constexpr int R1 = StageShape<L, 1>::R;
@@ -475,7 +479,7 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a, const __grid_con
         }
         cur = nxt;
         dft32_half_input<false>(v);
-        twiddles_lo<L, false>(v, j, tw);  // q >= R0/2: applied by the accumulate warps
+        twiddles_lo<L, false, kFwdTw>(v, j, tw);  // none here: the accumulate warps apply them
         cx<float>* tile = tiles + (r & 1) * L * TB;
 #pragma unroll
         for (int q = 0; q < R0; q++) tile[(j + q * M0) * TB + line] = v[q];
@@ -503,7 +507,7 @@ __global__ void __launch_bounds__(NTF, 1) k_yz_fwd_ws(YZArgs a, const __grid_con
           cx<float> v[R1];
 #pragma unroll
           for (int q = 0; q < R1; q++) v[q] = tile[(g * R1 + q) * TB + line];
-          if (it == 1) twiddles_hi<L, false>(v, g, tw);  // stage-0 twiddles of g >= R0/2
+          if (kFwdTw == 2 || (kFwdTw == 0 && it == 1)) twiddles_hi<L, false>(v, g, tw);  // stage-0 twiddles
           DftF<R1, false>::run(v);
           const float* tlo = stt + g * TB + line;
           const float* thi = stt + (L - g) * TB + line;
@@ -724,7 +728,7 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a, const __grid_con
 #pragma unroll
           for (int q = 0; q < R1; q++) v[q] = ws_apply<C>(ws_tensor<L, C>(tlo, thi, g, q, neg), sv[it][q]);
           DftF<R1, true>::run(v);
-          if (it == 1) twiddles_hi<L, true>(v, g, tw);  // stage-0 twiddles of g >= R0/2
+          if (kAdjTw == 2 || (kAdjTw == 0 && it == 1)) twiddles_hi<L, true>(v, g, tw);  // stage-0 twiddles
 #pragma unroll
           for (int q = 0; q < R1; q++) tile[(g * R1 + q) * TB + line] = v[q];
         }
@@ -750,7 +754,7 @@ __global__ void __launch_bounds__(NTF, 1) k_zy_adj_ws(ZYArgs a, const __grid_con
         cx<float> v[R0];
 #pragma unroll
         for (int q = 0; q < R0; q++) v[q] = tile[(j + q * M0) * TB + line];
-        twiddles_lo<L, true>(v, j, tw);  // q >= R0/2: applied by the load warps
+        twiddles_lo<L, true, kAdjTw>(v, j, tw);  // else q >= R0/2: applied by the load warps
         cx<float>* o = out0 + cur.z * a.out_zstride + cur.cb * TB + line;
         if constexpr (FULL) {  // rows y = j + q M0 < L/2: the first half of the outputs
           dft_low_half<R0, true>(v);

@@ -142,6 +142,38 @@ def test_conv_backward_data_and_weight(L, cin, cout):
                                         cin, cout, S()) == -5
 
 
+# rows of W = 8 .. 64 voxels take the halo-tile kernels (TMA-staged rows shared by the 27
+# taps); D and H ragged against their 2-plane x (128 / W)-row tiles
+HALO = [((1, 3, 17, 8), 16, 16), ((2, 3, 9, 16), 32, 64), ((1, 5, 7, 32), 96, 32), ((1, 3, 3, 64), 48, 16),
+        ((1, 2, 4, 64), 16, 32), ((2, 1, 2, 16), 64, 64)]
+
+
+@pytest.mark.parametrize("dims,cin,cout", HALO)
+def test_conv_halo_forward_and_backward_data(L, dims, cin, cout):
+    rng = np.random.default_rng(int(np.prod(dims)) + cin * 100 + cout)
+    x = bf16_round(rng.normal(size=dims + (cin,)))
+    W = bf16_round(rng.normal(0, 0.1, size=(27, cin, cout)))
+    b = rng.normal(0, 0.1, size=cout).astype(np.float32).astype(np.float64)
+    Wf, Wb = wf_wb(L, W)
+    out = torch.empty(dims + (cout,), dtype=torch.bfloat16, device=DEV)
+    for relu in (0, 1):
+        assert L.tmn_conv3d_forward(p(to_bf16_dev(x)), p(Wf), p(f32(b)), p(out), *dims, cin, cout, relu, S()) == 0
+        ref = U.conv(x, W, b)
+        if relu:
+            ref = np.maximum(ref, 0)
+        bound = U.conv(np.abs(x), np.abs(W), np.abs(b))
+        assert np.all(np.abs(out.float().cpu().numpy() - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-5 * bound)
+    g = bf16_round(rng.normal(size=dims + (cout,)))
+    dx_ref = U.conv_backward(x, W, g)[0]
+    bound = U.conv_backward(np.abs(x), np.abs(W), np.abs(g))[0]
+    din = torch.full(dims + (cin,), 0.5, dtype=torch.float32, device=DEV)
+    assert L.tmn_conv3d_backward_data(p(f32(g)), p(Wb), p(din), *dims, cin, cout, 0, S()) == 0
+    assert np.all(np.abs(din.cpu().numpy() - dx_ref) <= 1e-5 * bound + 1e-30)
+    assert L.tmn_conv3d_backward_data(p(f32(g)), p(Wb), p(din), *dims, cin, cout, 1, S()) == 0  # accumulate
+    assert np.all(np.abs(din.cpu().numpy() - 2 * dx_ref) <= 2e-5 * bound + 1e-30)
+    assert net_status(L) == 0
+
+
 def test_argument_checks(L):
     t = torch.empty(16, device=DEV)
     assert L.tmn_conv3d_forward(p(t), p(t), None, p(t), 1, 1, 1, 1, 16, 24, 0, S()) == -1  # Cout 24
