@@ -505,27 +505,29 @@ int launch_conv(const void* src, const bf16* Wc, const float* bias, void* dst, i
 // Weight gradient on tcgen05: dW[tap][ci][co] = sum_v in[v + off(tap)][ci] q(dout[v][co]),
 // a GEMM with rows (tap, ci), columns co and the voxels as the reduction. A block owns one
 // row tile of 128 = 8 taps x 16 input channels (tile = (tap group, channel chunk)) and a
-// range of voxels, 16 per MMA (K = 16); its float32 accumulator (128 x NO) lives in tensor
-// memory and is written out as one partial, and k_dw_reduce_tc adds the partials in block
-// order. Both operands are MN-major, so the channels-last rows go into shared memory as
+// range of voxels, 16 per MMA (K = 16), kDwChunks MMAs per pipeline stage; its float32
+// accumulator (128 x NO) lives in tensor memory and is written out as one partial, and
+// k_dw_reduce_tc adds the partials in block order. Both operands are MN-major, so the channels-last rows go into shared memory as
 // they are: A gets each (tap, voxel)'s 16 shifted input channels (two 16-byte pieces), B
 // each voxel's NO output-gradient channels, taken from a bfloat16 copy made beforehand
 // (rounded to nearest even, the operand precision of every product).
+constexpr int kDwStages = 3, kDwChunks = 4;  // pipeline stages; 16-voxel chunks (MMAs) per stage
+constexpr int kDwBlocksPerSm = 4;            // voxel blocks per SM, over all row tiles
 template <int NO>
 constexpr size_t dw_tc_smem() {
-  return (size_t)kTcStages * (128 * 32 + NO * 32) + (2 * kTcStages + 1) * 8 + 16;
+  return (size_t)kDwStages * kDwChunks * (128 * 32 + NO * 32) + (2 * kDwStages + 1) * 8 + 16;
 }
 template <int NO>
 __global__ void __launch_bounds__(128) k_conv_dw_tc(const bf16* in, const bf16* g16, float* part, int Nb, int D,
                                                     int H, int W, int Cin, long long chunks_per_block) {
   using namespace tmk;
-  constexpr int S = kTcStages, AB = 128 * 32, BB = NO * 32, PG = NO / 8;
+  constexpr int S = kDwStages, KS = kDwChunks, AB = 128 * 32, BB = NO * 32, PG = NO / 8;
   constexpr unsigned NCOLS = tmem_cols<NO>();
   constexpr unsigned IDESC = idesc_bf16(128, NO, true);
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* As = smem;           // [S][k-group (2)][16 row groups][8 k-rows][16 B]
-  unsigned char* Bs = smem + S * AB;  // [S][2][PG][8][16 B]
-  unsigned long long* mma_bar = reinterpret_cast<unsigned long long*>(Bs + S * BB);
+  unsigned char* As = smem;                // [S][KS][k-group (2)][16 row groups][8 k-rows][16 B]
+  unsigned char* Bs = smem + S * KS * AB;  // [S][KS][2][PG][8][16 B]
+  unsigned long long* mma_bar = reinterpret_cast<unsigned long long*>(Bs + S * KS * BB);
   unsigned* tslot = reinterpret_cast<unsigned*>(mma_bar + S);
   const int t = threadIdx.x, warp = t >> 5;
   if (t == 0) {
@@ -558,33 +560,53 @@ __global__ void __launch_bounds__(128) k_conv_dw_tc(const bf16* in, const bf16* 
   const long long c0 = (long long)blockIdx.x * chunks_per_block;
   const long long nch = (nvox + 15) / 16;
   const long long c1 = c0 + chunks_per_block < nch ? c0 + chunks_per_block : nch;
-  const int nsteps = c1 > c0 ? (int)(c1 - c0) : 0;
+  const int nsteps = c1 > c0 ? (int)((c1 - c0 + KS - 1) / KS) : 0;
+  // this thread's A voxel v = 16 ch + ka as a cursor (x, y, z, n) that the steps advance by
+  // 16 voxels in order (no divisions in the loop)
+  int cx = 0, cy = 0, cz = 0;
+  long long cn = 0;
+  {
+    long long q = c0 * 16 + ka;
+    cx = (int)(q % W);
+    q /= W;
+    cy = (int)(q % H);
+    q /= H;
+    cz = (int)(q % D);
+    cn = q / D;
+  }
+  // step s: chunks c0 + s KS + k (k < KS) of the block's range; chunks past it read zeros
   auto load_step = [&](int s, int b) {
-    const long long v0 = (c0 + s) * 16;
-    {
-      const long long v = v0 + ka;
-      bool ok = tap_ok && v < nvox;
-      long long u = 0;
-      if (ok) {
-        long long q = v;
-        const int x = (int)(q % W) + dx;
-        q /= W;
-        const int y = (int)(q % H) + dy;
-        q /= H;
-        const int z = (int)(q % D) + dz;
-        const long long n = q / D;
-        ok = z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W;
-        u = ok ? ((n * D + z) * H + y) * W + x : 0;
+#pragma unroll
+    for (int k = 0; k < KS; k++) {
+      const long long ch = c0 + (long long)s * KS + k;
+      const long long v0 = ch * 16;
+      const bool in_range = ch < c1;
+      {
+        const long long v = v0 + ka;
+        const int x = cx + dx, y = cy + dy, z = cz + dz;
+        const bool ok = in_range && tap_ok && v < nvox && z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W;
+        const long long u = ok ? ((cn * D + z) * H + y) * W + x : 0;
+        cx += 16;  // the cursor moves to this thread's voxel of the next chunk
+        while (cx >= W) {
+          cx -= W;
+          if (++cy == H) {
+            cy = 0;
+            if (++cz == D) {
+              cz = 0;
+              ++cn;
+            }
+          }
+        }
+        const bf16* src = in + u * Cin + cc * 16;
+        unsigned char* a = As + (b * KS + k) * AB + aoff;
+        cp_async16(a, src, ok ? 16u : 0u);            // channels 0..7: row group 2 (t / 16)
+        cp_async16(a + 128, src + 8, ok ? 16u : 0u);  // channels 8..15: the next row group
       }
-      const bf16* src = in + u * Cin + cc * 16;
-      unsigned char* a = As + b * AB + aoff;
-      cp_async16(a, src, ok ? 16u : 0u);            // channels 0..7: row group 2 (t / 16)
-      cp_async16(a + 128, src + 8, ok ? 16u : 0u);  // channels 8..15: the next row group
-    }
-    if (t < 16 * PG) {
-      const long long v = v0 + kb;
-      const bool ok = v < nvox;
-      cp_async16(Bs + b * BB + boff, g16 + (ok ? v : 0) * NO + pg * 8, ok ? 16u : 0u);
+      if (t < 16 * PG) {
+        const long long v = v0 + kb;
+        const bool ok = in_range && v < nvox;
+        cp_async16(Bs + (b * KS + k) * BB + boff, g16 + (ok ? v : 0) * NO + pg * 8, ok ? 16u : 0u);
+      }
     }
   };
   for (int s = 0; s < S - 1; s++) {  // always S - 1 groups, so that the wait below counts right
@@ -605,9 +627,12 @@ __global__ void __launch_bounds__(128) k_conv_dw_tc(const bf16* in, const bf16* 
     __syncthreads();
     if (t == 0) {
       tc_fence_after();
-      const uint64_t ad = smem_desc(As + b * AB, 2048, 128);
-      const uint64_t bd = smem_desc(Bs + b * BB, PG * 128, 128);
-      tc_mma(taddr, ad, bd, IDESC, s > 0);
+#pragma unroll
+      for (int k = 0; k < KS; k++) {
+        const uint64_t ad = smem_desc(As + (b * KS + k) * AB, 2048, 128);
+        const uint64_t bd = smem_desc(Bs + (b * KS + k) * BB, PG * 128, 128);
+        tc_mma(taddr, ad, bd, IDESC, s > 0 || k > 0);
+      }
       tc_commit(mma_bar + b);
     }
   }
@@ -892,8 +917,8 @@ int tmn_conv3d_backward_weight(const void* in, const float* dout, float* dW, flo
   const long long pofs = ((nvox * Cout + 1) / 2 + 3) / 4 * 4;
   const int tiles = 4 * (Cin / 16);
   const long long per_blk = (long long)tiles * 128 * Cout;
-  // voxel blocks: about eight blocks per SM over all tiles (each block's loop is bound by the
-  // latency of its gathers, so more of them in flight), no more than the work buffer holds
+  // voxel blocks: about four blocks per SM over all tiles (each block's loop is bound by the
+  // latency of its gathers, so several of them in flight), no more than the work buffer holds
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
@@ -902,10 +927,11 @@ int tmn_conv3d_backward_weight(const void* in, const float* dout, float* dW, flo
   }
   const long long chunks = (nvox + 15) / 16;
   long long nblk = (work_floats - pofs) / per_blk;
-  const long long want = (8LL * nsm + tiles - 1) / tiles;
+  const long long want = ((long long)kDwBlocksPerSm * nsm + tiles - 1) / tiles;
   if (nblk > want) nblk = want;
   if (nblk > chunks) nblk = chunks;
-  const long long cpb = (chunks + nblk - 1) / nblk;
+  long long cpb = (chunks + nblk - 1) / nblk;
+  if (cpb > kDwChunks) cpb = (cpb + kDwChunks - 1) / kDwChunks * kDwChunks;  // whole pipeline stages
   nblk = (chunks + cpb - 1) / cpb;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   bf16* g16 = reinterpret_cast<bf16*>(work);

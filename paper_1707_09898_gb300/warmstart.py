@@ -159,7 +159,7 @@ class WarmStartNet:
                   "e2": a(g2, 32, F32), "e2a": a(g2, 32, F32), "p1": a(g2, 16, F32), "b2": a(g3, 64, F32),
                   "b1": a(g3, 64, F32), "p2": a(g3, 32, F32)}
         # weight-gradient scratch: the bfloat16 copy of the largest output gradient plus the
-        # per-block partial sums of about eight blocks per SM (8 * 160 * 128 * Cout floats)
+        # per-block partial sums of up to eight blocks per SM (8 * 160 * 128 * Cout floats)
         nwork = max(self.L.tmn_conv3d_backward_weight_work(N * (D // LEVEL[n]) * (H // LEVEL[n]) * (W // LEVEL[n]),
                                                            ci, co) for n, ci, co in LAYERS)
         self.work = torch.empty(nwork + 8 * 160 * 128 * 64, dtype=F32, device=self.dev)
