@@ -340,11 +340,37 @@ __global__ void __launch_bounds__(128) k_conv_halo(const void* src, const bf16* 
       mbar_expect_tx(tma_bar, 27 * BB);
       for (int tap = 0; tap < 27; tap++) bulk_load(Bs + tap * BB, Wc + ((long long)tap * nk + kc) * NO * 16, BB, tma_bar);
     }
-    {
-      // (half, row, x) items, x fastest: the 8 channels of one voxel (bfloat16, or float32
-      // rounded to bfloat16 in MODE 1) are read once and stored into the copies that hold
-      // them (copy c has the value of x + c - 1 at position x); the loads of kBatch items
-      // are in flight together
+    if constexpr (MODE == 0) {
+      // (half, row, x) items, x fastest: the unshifted copy (dx = 0) by 16-byte asynchronous
+      // copies, all of them in flight at once (zero fill outside the grid); then the copies
+      // for dx = -1 and +1 from it in shared memory (position x of copy c holds x + c - 1;
+      // x + c - 1 outside the row is outside the grid, so zero)
+      constexpr int ITEMS = 2 * ROWS * W;
+      const bf16* in = reinterpret_cast<const bf16*>(src) + kc * 16;
+      for (int i = t; i < ITEMS; i += 128) {
+        const int x = i % W, r = (i / W) % ROWS, h = i / (W * ROWS);
+        const int z = z0 - 1 + r / (RY + 2), y = y0 - 1 + r % (RY + 2);
+        const bool ok = z >= 0 && z < D && y >= 0 && y < H;
+        const long long e = ok ? ((((long long)n * D + z) * H + y) * W + x) * KC + h * 8 : 0;
+        cp_async16(As + (2 + h) * BOX + (r * W + x) * 16, in + e, ok ? 16u : 0u);
+      }
+      cp_async_commit();
+      cp_async_wait<0>();
+      __syncthreads();
+      for (int i = t; i < ITEMS; i += 128) {
+        const int x = i % W, rest = i / W, h = rest / ROWS;  // rest = h ROWS + r
+        const int o = (rest - h * ROWS) * W;                 // r W
+        const uint4 v = *reinterpret_cast<const uint4*>(As + (2 + h) * BOX + (o + x) * 16);
+        // copy 0 at x + 1 and copy 2 at x - 1 hold this voxel; their row ends are zero
+        if (x + 1 < W) *reinterpret_cast<uint4*>(As + h * BOX + (o + x + 1) * 16) = v;
+        if (x >= 1) *reinterpret_cast<uint4*>(As + (4 + h) * BOX + (o + x - 1) * 16) = v;
+        if (x == 0) *reinterpret_cast<uint4*>(As + h * BOX + o * 16) = make_uint4(0u, 0u, 0u, 0u);
+        if (x == W - 1) *reinterpret_cast<uint4*>(As + (4 + h) * BOX + (o + W - 1) * 16) = make_uint4(0u, 0u, 0u, 0u);
+      }
+    } else {
+      // (half, row, x) items, x fastest: the 8 float32 values of one voxel are read once,
+      // rounded to bfloat16 and stored into the copies that hold them (copy c has the value
+      // of x + c - 1 at position x); the loads of kBatch items are in flight together
       constexpr int XW = W + 2, ITEMS = 2 * ROWS * XW, kBatch = 8;
       constexpr int NV = MODE == 0 ? 1 : 2;  // 16-byte loads per item (MODE 1: 8 float32 values)
       for (int i0 = 0; i0 < ITEMS; i0 += 128 * kBatch) {
