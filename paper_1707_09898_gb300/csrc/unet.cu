@@ -266,10 +266,11 @@ int launch_conv_tc(const void* src, const bf16* Wc, const float* bias, void* dst
 // [channel half][z][y][x][8 channels]: the A operand of tap (dz, dy, dx) for tile m is copy
 // dx from row (m + dz + 1, dy + 1) on (16-byte voxel rows, row groups 128 bytes apart, the
 // two channel halves one box apart), so all 27 taps read the same staged rows instead of
-// gathering them again. The threads read each staged voxel's 8 channels once (MODE 1: the
-// float32 output gradient, rounded to bfloat16) and store them into the three copies: a
-// third of the reads of copying every copy from memory, and faster than TMA boxes of these
-// 16-byte rows (measured 86 us against 77 us for one copy per box on a 64^3 x 2 layer).
+// gathering them again. Each staged voxel's 8 channels are read from memory once: MODE 0
+// copies the unshifted rows asynchronously (all copies in flight) and builds the two
+// shifted copies from them in shared memory; MODE 1 loads the float32 output gradient,
+// rounds it to bfloat16 and stores it into the three copies. (TMA boxes of these 16-byte
+// rows measured slower: 86 us against 77 us on a 64^3 x 2 layer.)
 // The chunk's 27 packed weight blocks arrive by bulk copies (mbarrier completion). Thread 0
 // issues 27 x TZ MMAs per chunk (K = 16 each); the epilogue is that of k_conv_tc. Same
 // arithmetic as k_conv_tc: the same products, float32 sums in the tensor core's order.
