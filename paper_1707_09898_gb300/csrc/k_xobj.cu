@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(OW * 32) k_xobj(XInvArgs a, int L) {
     for (int w = 0; w < OW; w++) s += red[w];
     a.Jpart[jc * gridDim.x + blockIdx.x] = s;
   }
+  if (!a.Jcount) return;  // partials only: a later kernel sums them
   __shared__ unsigned int last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -252,7 +253,7 @@ __device__ __forceinline__ void r8_stage(const cx<float>* src, cx<float>* dst, c
       v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
     }
   }
-  Dft<float, 8, INV>::run(v);
+  DftF<8, INV>::run(v);
   const int base = (j / Ns) * (8 * Ns) + k;
 #pragma unroll
   for (int r = 0; r < 8; r++) dst[base + r * Ns] = v[r];
@@ -371,9 +372,12 @@ __global__ void __launch_bounds__(NT8) k_xobj512(XInvArgs a) {
     double s = 0.0;
     for (int w = 0; w < NT8 / 32; w++) s += red[w];
     a.Jpart[jc * gridDim.x + blockIdx.x] = s;
-    __threadfence();
-    last = atomicAdd(a.Jcount, 1u) == gridDim.x * gridDim.y - 1 ? 1u : 0u;
+    if (a.Jcount) {
+      __threadfence();
+      last = atomicAdd(a.Jcount, 1u) == gridDim.x * gridDim.y - 1 ? 1u : 0u;
+    }
   }
+  if (!a.Jcount) return;  // partials only: a later kernel sums them
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -409,7 +413,7 @@ int launch_xobj(int L, const XInvArgs& a, cudaStream_t s) {
     const int rows = a.rows - a.row_base;
     const int blocks = (rows + 2 * NG8 - 1) / (2 * NG8);
     if (blocks <= 0 || a.ncomp == 0) return 0;
-    if (!a.Jcount || !a.adj_out) return -1;
+    if (!a.adj_out || (!a.Jcount && a.Jout)) return -1;
     return launch_k(k_xobj512, dim3(blocks, a.ncomp), dim3(NT8), sm8, s, a.pdl != 0, a) == cudaSuccess ? 0 : -1;
   }
   const size_t sm = xobj_smem(L);
@@ -422,8 +426,14 @@ int launch_xobj(int L, const XInvArgs& a, cudaStream_t s) {
   }
   const int rows = a.rows - a.row_base;
   const int blocks = (rows + 2 * NG - 1) / (2 * NG);
-  if (blocks <= 0 || a.ncomp == 0 || !a.Jcount || !a.adj_out) return blocks <= 0 || a.ncomp == 0 ? 0 : -1;
+  if (blocks <= 0 || a.ncomp == 0) return 0;
+  if (!a.adj_out || (!a.Jcount && a.Jout)) return -1;
   return launch_k(k_xobj, dim3(blocks, a.ncomp), dim3(OW * 32), sm, s, a.pdl != 0, a, L) == cudaSuccess ? 0 : -1;
+}
+
+int xobj_blocks(int L, int rows) {
+  const int rpb = L == 512 ? 2 * NG8 : 2 * NG;
+  return rows > 0 ? (rows + rpb - 1) / rpb : 0;
 }
 
 int xobj_rows_per_block() { return 2 * (NG < NG8 ? NG : NG8); }  // the fewest rows any block holds

@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_yz_finish(YZArgs a, int B) {
     cx<float> v[R1];
 #pragma unroll
     for (int q = 0; q < R1; q++) v[q] = tile[fin_idx(g * R1 + q, l)];
-    Dft<float, R1, true>::run(v);
+    DftF<R1, true>::run(v);
 #pragma unroll
     for (int q = 0; q < R1; q++) tile[fin_idx(g * R1 + q, l)] = v[q];
   }
@@ -618,12 +618,21 @@ __global__ void __launch_bounds__(kFinishThreads) k_yz_finish(YZArgs a, int B) {
 #pragma unroll
     for (int q = 0; q < R0; q++) v[q] = tile[fin_idx(j + q * M0, l)];
     apply_twiddles<float, L, 0, true>(v, j, tw);
-    Dft<float, R0, true>::run(v);
     cx<float>* o = reinterpret_cast<cx<float>*>(a.yrows) + cb * TB + l0 + l;
+    if (a.n_in <= L / 2) {  // the kept rows y = j + q M0 < n_in have q < R0/2
+      dft_low_half<R0, true>(v);
 #pragma unroll
-    for (int q = 0; q < R0; q++) {
-      const int y = j + q * M0;
-      if (y < a.n_in) o[(long long)y * a.P] = v[q];
+      for (int q = 0; q < R0 / 2; q++) {
+        const int y = j + q * M0;
+        if (y < a.n_in) o[(long long)y * a.P] = v[q];
+      }
+    } else {
+      DftF<R0, true>::run(v);
+#pragma unroll
+      for (int q = 0; q < R0; q++) {
+        const int y = j + q * M0;
+        if (y < a.n_in) o[(long long)y * a.P] = v[q];
+      }
     }
   }
 }
