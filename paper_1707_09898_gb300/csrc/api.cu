@@ -53,7 +53,6 @@ struct tm_ctx {
   int2* zcol = nullptr;     // [Ly]
   double* Jpart = nullptr;  // [ceil(nz*ny/rows_per_block)]
   int nJpart = 0;
-  int jsum_n = 0;           // J partials of the last objective pass not summed yet (taken by the chain rule)
   double* Jdev = nullptr;
   unsigned int* gmax = nullptr;
   const float* gmax_of = nullptr;  // the array whose max |.| gmax holds (set by the chain-rule pass)
@@ -667,12 +666,6 @@ int xinv_chain(tm_ctx* ctx, const float* rho, float* G, int ncomp, const int* sl
   x.gmax = ctx->gmax;
   x.tw = ctx->tw;
   x.status = ctx->dstat;
-  if (ctx->jsum_n > 0) {  // the objective pass left its J partials to this pass
-    x.Jsum_part = ctx->Jpart;
-    x.Jsum_n = ctx->jsum_n;
-    x.Jsum_out = ctx->Jdev;
-    ctx->jsum_n = 0;
-  }
   Timed t(ctx, KIND_XINV, s);
   CKL(launch_xinv(ctx->L[0], x, s));
   ctx->gmax_of = G;
@@ -1398,10 +1391,9 @@ int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, vo
         x.w[c] = w[c];
       }
       x.adj_out = ctx->A;
-      x.Jpart = ctx->Jpart;  // partials only: the chain-rule pass sums them, off this path
-      x.Jcount = nullptr;
-      x.Jout = nullptr;
-      ctx->jsum_n = nF * xobj_blocks(ctx->L[0], x.rows - x.row_base);
+      x.Jpart = ctx->Jpart;
+      x.Jcount = ctx->Jcount;  // J summed by the pass's last block
+      x.Jout = ctx->Jdev;
       x.ny = ctx->ny;
       x.tw = ctx->tw;
       x.pdl = ctx->pdl;
@@ -1410,10 +1402,6 @@ int tm_evaluate(tm_ctx* ctx, const float* rho, double* J_host, float* dJdrho, vo
         CKL(launch_xobj(ctx->L[0], x, s));
       }
       if ((r = adjoint_planes(ctx, rho, dJdrho, F, W, nW, s))) return r;
-      if (ctx->jsum_n > 0) {  // no chain-rule pass took the partials
-        CKL(launch_j_finalize(ctx->Jpart, ctx->jsum_n, ctx->Jdev, s));
-        ctx->jsum_n = 0;
-      }
     }
   }
   if (J_host) {

@@ -109,20 +109,7 @@ struct XInvArgs {
   const float2* tw;
   int pdl;                  // launch with programmatic dependent launch
   unsigned* status;         // device word: bit 0 set when a copy wait timed out (CHAIN, L = 512)
-  const double* Jsum_part;  // CHAIN, optional: the objective pass's partials, summed by the last block
-  int Jsum_n;               //   (one warp, fixed order) into *Jsum_out, off the objective's path
-  double* Jsum_out;
 };
-
-// fixed-order sum of n partials by one full warp (lane sums, then a fixed shuffle tree);
-// the result in lane 0
-__device__ __forceinline__ double warp_sum_partials(const double* part, int n) {
-  const int lane = threadIdx.x & 31;
-  double s = 0.0;
-  for (int i = lane; i < n; i += 32) s += __ldcg(part + i);
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  return s;
-}
 
 // y pass over [slot][planes][points][P] arrays, tiles of 16 kx columns; blockIdx.z -> in_slot[], out_slot[].
 struct YArgs {
@@ -257,7 +244,6 @@ int tensor_setup(int nx, int ny, int nz, const double d[3], int Lx, int Ly, int 
 
 // Small kernels -- misc.cu
 int launch_j_finalize(const double* part, int n, double* J, cudaStream_t s);
-int xobj_blocks(int L, int rows);  // blocks (per component) of the objective pass over `rows` rows
 int launch_absmax(const float* G, long long n, unsigned int* gmax, cudaStream_t s);
 int launch_mask_extent(const uint8_t* mask, int nz, long long plane, int* ext, cudaStream_t s);
 int launch_update(float* rho, const float* G, long long n, float alpha, int normalize, const unsigned int* gmax,

@@ -57,10 +57,6 @@ __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
   load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
   load_twiddles0<L>(tw0, reinterpret_cast<const cx<float>*>(a.tw));
   pdl_wait();  // the spectra, rho and the outputs belong to earlier kernels
-  if (a.Jsum_out && blockIdx.x == gridDim.x - 1 && blockIdx.y == 0 && threadIdx.x < 32) {
-    const double J = warp_sum_partials(a.Jsum_part, a.Jsum_n);
-    if (threadIdx.x == 0) *a.Jsum_out = J;
-  }
   const int row0 = a.row_base + blockIdx.x * ROWS;
   const cx<float>* in0 = reinterpret_cast<const cx<float>*>(a.in);
 
@@ -295,12 +291,6 @@ __global__ void __launch_bounds__(2 * kNT, 1) k_xinv_ws(XInvArgs a) {
     mbar_init_fence();
   }
   pdl_wait();  // the spectra, rho and G belong to earlier kernels
-  // the objective's J: the last block (it has the fewest tiles) sums the partials with the
-  // first warp of its second group
-  if (a.Jsum_out && blockIdx.x == gridDim.x - 1 && threadIdx.x >= kNT && threadIdx.x < kNT + 32) {
-    const double J = warp_sum_partials(a.Jsum_part, a.Jsum_n);
-    if (threadIdx.x == kNT) *a.Jsum_out = J;
-  }
   __syncthreads();
   const int ntiles = (a.rows + ROWS - 1) / ROWS;
   const int nr = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;

@@ -201,7 +201,6 @@ __global__ void __launch_bounds__(OW * 32) k_xobj(XInvArgs a, int L) {
     for (int w = 0; w < OW; w++) s += red[w];
     a.Jpart[jc * gridDim.x + blockIdx.x] = s;
   }
-  if (!a.Jcount) return;  // partials only: a later kernel sums them
   __shared__ unsigned int last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -372,12 +371,9 @@ __global__ void __launch_bounds__(NT8) k_xobj512(XInvArgs a) {
     double s = 0.0;
     for (int w = 0; w < NT8 / 32; w++) s += red[w];
     a.Jpart[jc * gridDim.x + blockIdx.x] = s;
-    if (a.Jcount) {
-      __threadfence();
-      last = atomicAdd(a.Jcount, 1u) == gridDim.x * gridDim.y - 1 ? 1u : 0u;
-    }
+    __threadfence();
+    last = atomicAdd(a.Jcount, 1u) == gridDim.x * gridDim.y - 1 ? 1u : 0u;
   }
-  if (!a.Jcount) return;  // partials only: a later kernel sums them
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -413,7 +409,7 @@ int launch_xobj(int L, const XInvArgs& a, cudaStream_t s) {
     const int rows = a.rows - a.row_base;
     const int blocks = (rows + 2 * NG8 - 1) / (2 * NG8);
     if (blocks <= 0 || a.ncomp == 0) return 0;
-    if (!a.adj_out || (!a.Jcount && a.Jout)) return -1;
+    if (!a.Jcount || !a.adj_out) return -1;
     return launch_k(k_xobj512, dim3(blocks, a.ncomp), dim3(NT8), sm8, s, a.pdl != 0, a) == cudaSuccess ? 0 : -1;
   }
   const size_t sm = xobj_smem(L);
@@ -426,14 +422,8 @@ int launch_xobj(int L, const XInvArgs& a, cudaStream_t s) {
   }
   const int rows = a.rows - a.row_base;
   const int blocks = (rows + 2 * NG - 1) / (2 * NG);
-  if (blocks <= 0 || a.ncomp == 0) return 0;
-  if (!a.adj_out || (!a.Jcount && a.Jout)) return -1;
+  if (blocks <= 0 || a.ncomp == 0 || !a.Jcount || !a.adj_out) return blocks <= 0 || a.ncomp == 0 ? 0 : -1;
   return launch_k(k_xobj, dim3(blocks, a.ncomp), dim3(OW * 32), sm, s, a.pdl != 0, a, L) == cudaSuccess ? 0 : -1;
-}
-
-int xobj_blocks(int L, int rows) {
-  const int rpb = L == 512 ? 2 * NG8 : 2 * NG;
-  return rows > 0 ? (rows + rpb - 1) / rpb : 0;
 }
 
 int xobj_rows_per_block() { return 2 * (NG < NG8 ? NG : NG8); }  // the fewest rows any block holds
