@@ -26,12 +26,17 @@ extern "C" {
 #endif
 
 /* out = relu?(conv(in, W) + bias), bfloat16; Cin % 16 == 0, Cout in {16, 32, 64}. An implicit
- * GEMM on the fifth-generation tensor cores: 128 voxels x Cout per block, the float32
- * accumulator in tensor memory, bfloat16 operands. */
+ * GEMM on the fifth-generation tensor cores: M = 128 voxels, N = Cout, the float32
+ * accumulator in tensor memory, bfloat16 operands. For W in {8, 16, 32, 64} (and `in` 16-byte
+ * aligned) a block stages its halo rows once and every tap reads them; other grids gather
+ * each voxel's shifted channels per tap. Same products and float32 sums either way. */
 int tmn_conv3d_forward(const void* in, const void* Wf, const float* bias, void* out, int N, int D, int H, int W,
                        int Cin, int Cout, int relu, void* stream);
 
-/* din (+)= conv^T(dout, W), float32; Cout % 16 == 0, Cin in {16, 32, 48, 64, 96}. */
+/* din (+)= conv^T(dout, W), float32; Cout % 16 == 0, Cin in {16, 32, 48, 64, 96}. dout is
+ * rounded to bfloat16 as a product operand; the same tensor-core kernels as the forward
+ * (halo tiles for W in {8, 16, 32, 64}), N = Cin. accumulate: add to din instead of
+ * overwriting it. */
 int tmn_conv3d_backward_data(const float* dout, const void* Wb, float* din, int N, int D, int H, int W, int Cin,
                              int Cout, int accumulate, void* stream);
 

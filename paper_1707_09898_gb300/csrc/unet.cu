@@ -8,10 +8,12 @@
 // Weights: float32 master [27][Cin][Cout] (tap = (dz+1)*9 + (dy+1)*3 + (dx+1));
 // bfloat16 copies Wf (forward) and Wb (backward data) packed in the operand layout of
 // the tensor-core kernels (see pack_f / pack_b below).
-// 3x3x3 convolutions (stride 1, zero padding 1) forward and backward-data are
-// implicit GEMMs on the fifth-generation tensor cores (tcgen05.mma, bfloat16 in,
-// float32 accumulators in tensor memory); the weight gradients are GEMMs over voxels
-// per tap on mma.sync (the output gradient rounded to bfloat16 as in the data gradient).
+// 3x3x3 convolutions (stride 1, zero padding 1), forward, data gradient and weight
+// gradient, are implicit GEMMs on the fifth-generation tensor cores (tcgen05.mma,
+// bfloat16 operands, float32 accumulators in tensor memory): k_conv_halo (rows of 8..64
+// voxels: halo rows staged once per block), k_conv_tc (any grid: per-voxel gathers) and
+// k_conv_dw_tc (weight gradient, the output gradient rounded to bfloat16 as in the data
+// gradient).
 #include <cuda_bf16.h>
 #include <stdint.h>
 
