@@ -285,6 +285,45 @@ __device__ __forceinline__ void static_for(F&& f) {
   }
 }
 constexpr int kPartSplit = 13;  // taps [0, 13) and [13, 27) go to two accumulators
+// Stage the rows (z0 - 1 + r / RP, y0 - 1 + r % RP), r < ROWS, of batch item n, channels
+// [c0, c0 + 16), into three copies shifted by dx = -1, 0, +1 in the K-major core-matrix
+// layout [copy][channel half][r][x][8 channels] (copy c holds x + c - 1 at position x; zero
+// outside the grid), in two parts so that other loads can be in flight in between:
+// stage_halo_issue copies the unshifted rows by 16-byte asynchronous copies (all in flight);
+// stage_halo_finish waits for them (block barrier) and builds the shifted copies in shared
+// memory. The caller still fences the generic-proxy stores for the tensor core.
+template <int W, int RP, int ROWS>
+__device__ __forceinline__ void stage_halo_issue(unsigned char* As, const bf16* in, int n, int z0, int y0, int D,
+                                                 int H, int KC, int c0) {
+  using namespace tmk;
+  constexpr int BOX = 16 * W * ROWS, ITEMS = 2 * ROWS * W;
+  for (int i = threadIdx.x; i < ITEMS; i += blockDim.x) {
+    const int x = i % W, r = (i / W) % ROWS, h = i / (W * ROWS);
+    const int z = z0 - 1 + r / RP, y = y0 - 1 + r % RP;
+    const bool ok = z >= 0 && z < D && y >= 0 && y < H;
+    const long long e = ok ? ((((long long)n * D + z) * H + y) * W + x) * KC + c0 + h * 8 : c0;
+    cp_async16(As + (2 + h) * BOX + (r * W + x) * 16, in + e, ok ? 16u : 0u);
+  }
+  cp_async_commit();
+}
+template <int W, int ROWS>
+__device__ __forceinline__ void stage_halo_finish(unsigned char* As) {
+  using namespace tmk;
+  constexpr int BOX = 16 * W * ROWS, ITEMS = 2 * ROWS * W;
+  cp_async_wait<0>();
+  __syncthreads();
+  for (int i = threadIdx.x; i < ITEMS; i += blockDim.x) {
+    const int x = i % W, rest = i / W, h = rest / ROWS;  // rest = h ROWS + r
+    const int o = (rest - h * ROWS) * W;                 // r W
+    const uint4 v = *reinterpret_cast<const uint4*>(As + (2 + h) * BOX + (o + x) * 16);
+    // copy 0 at x + 1 and copy 2 at x - 1 hold this voxel; their row ends are zero
+    if (x + 1 < W) *reinterpret_cast<uint4*>(As + h * BOX + (o + x + 1) * 16) = v;
+    if (x >= 1) *reinterpret_cast<uint4*>(As + (4 + h) * BOX + (o + x - 1) * 16) = v;
+    if (x == 0) *reinterpret_cast<uint4*>(As + h * BOX + o * 16) = make_uint4(0u, 0u, 0u, 0u);
+    if (x == W - 1) *reinterpret_cast<uint4*>(As + (4 + h) * BOX + (o + W - 1) * 16) = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
 template <int W>
 struct Halo {
   static constexpr int RY = 128 / W, TZ = 2, ROWS = (TZ + 2) * (RY + 2);
@@ -344,32 +383,8 @@ __global__ void __launch_bounds__(128) k_conv_halo(const void* src, const bf16* 
       for (int tap = 0; tap < 27; tap++) bulk_load(Bs + tap * BB, Wc + ((long long)tap * nk + kc) * NO * 16, BB, tma_bar);
     }
     if constexpr (MODE == 0) {
-      // (half, row, x) items, x fastest: the unshifted copy (dx = 0) by 16-byte asynchronous
-      // copies, all of them in flight at once (zero fill outside the grid); then the copies
-      // for dx = -1 and +1 from it in shared memory (position x of copy c holds x + c - 1;
-      // x + c - 1 outside the row is outside the grid, so zero)
-      constexpr int ITEMS = 2 * ROWS * W;
-      const bf16* in = reinterpret_cast<const bf16*>(src) + kc * 16;
-      for (int i = t; i < ITEMS; i += 128) {
-        const int x = i % W, r = (i / W) % ROWS, h = i / (W * ROWS);
-        const int z = z0 - 1 + r / (RY + 2), y = y0 - 1 + r % (RY + 2);
-        const bool ok = z >= 0 && z < D && y >= 0 && y < H;
-        const long long e = ok ? ((((long long)n * D + z) * H + y) * W + x) * KC + h * 8 : 0;
-        cp_async16(As + (2 + h) * BOX + (r * W + x) * 16, in + e, ok ? 16u : 0u);
-      }
-      cp_async_commit();
-      cp_async_wait<0>();
-      __syncthreads();
-      for (int i = t; i < ITEMS; i += 128) {
-        const int x = i % W, rest = i / W, h = rest / ROWS;  // rest = h ROWS + r
-        const int o = (rest - h * ROWS) * W;                 // r W
-        const uint4 v = *reinterpret_cast<const uint4*>(As + (2 + h) * BOX + (o + x) * 16);
-        // copy 0 at x + 1 and copy 2 at x - 1 hold this voxel; their row ends are zero
-        if (x + 1 < W) *reinterpret_cast<uint4*>(As + h * BOX + (o + x + 1) * 16) = v;
-        if (x >= 1) *reinterpret_cast<uint4*>(As + (4 + h) * BOX + (o + x - 1) * 16) = v;
-        if (x == 0) *reinterpret_cast<uint4*>(As + h * BOX + o * 16) = make_uint4(0u, 0u, 0u, 0u);
-        if (x == W - 1) *reinterpret_cast<uint4*>(As + (4 + h) * BOX + (o + W - 1) * 16) = make_uint4(0u, 0u, 0u, 0u);
-      }
+      stage_halo_issue<W, RY + 2, ROWS>(As, reinterpret_cast<const bf16*>(src), n, z0, y0, D, H, KC, kc * 16);
+      stage_halo_finish<W, ROWS>(As);
     } else {
       // (half, row, x) items, x fastest: the 8 float32 values of one voxel are read once,
       // rounded to bfloat16 and stored into the copies that hold them (copy c has the value
@@ -687,6 +702,151 @@ __global__ void __launch_bounds__(128) k_conv_dw_tc(const bf16* in, const bf16* 
   if (warp == 0) tmem_dealloc(taddr, NCOLS);
 }
 
+// Weight gradient for rows of 8..64 voxels (128 % W == 0): dW[tap][ci][co] =
+// sum_v in[v + off(tap)][ci] q(dout[v][co]) as MMAs with M = co (padded to 128), N = the
+// 16 input channels of a chunk for the three dx taps at once (48), K = 16 voxels. A
+// persistent block takes tiles of one plane x 128 / W rows (128 voxels): it stages the three
+// planes of rows around the tile once, in the forward's three dx-shifted copies, whose
+// channel halves and dx copies lie one box apart -- the uniform stride the N side needs --
+// and the tile's output gradient, rounded to bfloat16, as [8 co][voxel] rows. Each of the
+// nine (dz, dy) pairs then has one accumulator of 48 tensor-memory columns (432 in all),
+// fed by 8 MMAs per tile from four issuing threads. After the block's tiles of a channel
+// chunk its accumulators go out as one float32 partial per block; k_dw_reduce_halo adds the
+// partials in block order. Same products as k_conv_dw_tc, float32 sums in another order.
+template <int W>
+struct DwHalo {
+  static constexpr int RY = 128 / W, NV = 128, ROWS = 3 * (RY + 2);
+  static constexpr int BOX = 16 * W * ROWS, ABYTES = 6 * BOX, GBYTES = 16 * NV * 16;
+};
+template <int W>
+constexpr size_t dw_halo_smem() {
+  return 128 + (size_t)DwHalo<W>::ABYTES + DwHalo<W>::GBYTES + 2 * 8 + 16;
+}
+template <int W, int NO>
+__global__ void __launch_bounds__(128, 1) k_conv_dw_halo(const bf16* in, const float* dout, float* part, int Nb,
+                                                         int D, int H, int Cin) {
+  using namespace tmk;
+  using HT = DwHalo<W>;
+  constexpr int RY = HT::RY, NV = HT::NV, ROWS = HT::ROWS, BOX = HT::BOX;
+  constexpr unsigned NCOLS = 512, IDESC = idesc_bf16(128, 48, true);
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* As = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);  // [copy][half][plane][y][x][16 B]
+  unsigned char* Gs = As + HT::ABYTES;                                         // [16 co groups][NV][16 B]
+  unsigned long long* mma_bar = reinterpret_cast<unsigned long long*>(Gs + HT::GBYTES);
+  unsigned* tslot = reinterpret_cast<unsigned*>(mma_bar + 1);
+  const int t = threadIdx.x, warp = t >> 5;
+  for (int i = t; i < (16 - NO / 8) * NV; i += 128)  // co >= NO: zero rows of A, never written again
+    *reinterpret_cast<uint4*>(Gs + (NO / 8) * NV * 16 + i * 16) = make_uint4(0u, 0u, 0u, 0u);
+  if (t == 0) {
+    mbar_init(mma_bar, 4);  // one commit per issuer
+    mbar_init_fence();
+  }
+  if (warp == 0) {
+    tmem_alloc(tslot, NCOLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned taddr = *tslot;
+  bool dead = false;
+  auto wait = [&](unsigned long long* mb, unsigned parity) {
+    if (!dead) dead = !mbar_wait_limit(mb, parity, 1 << 16, &g_net_status);
+  };
+  const int nyt = (H + RY - 1) / RY;
+  const long long ntiles = (long long)Nb * D * nyt;
+  const int nk = Cin >> 4;
+  unsigned phase = 0;  // completed phases of mma_bar
+  for (int kc = 0; kc < nk; kc++) {
+    bool first = true;  // the block's first tile of this chunk starts the accumulators
+    for (long long q = blockIdx.x; q < ntiles; q += gridDim.x) {
+      const int yt = (int)(q % nyt);
+      const long long rq = q / nyt;
+      const int z = (int)(rq % D), n = (int)(rq / D), y0 = yt * RY;
+      if (!first) {  // the previous tile's MMAs have read the staged rows
+        wait(mma_bar, phase & 1);
+        phase++;
+      }
+      if (t == 0 && kc == 0 && first) fence_proxy_async_global();  // in and dout came by ordinary stores
+      stage_halo_issue<W, RY + 2, ROWS>(As, in, n, z, y0, D, H, Cin, kc * 16);  // in flight meanwhile
+      // the tile's output gradient: voxel v = ty W + x, co group cg; zero outside the grid
+      {
+        constexpr int GI = NV * (NO / 8);
+        for (int i = t; i < GI; i += 128) {
+          const int v = i % NV, cg = i / NV, y = y0 + v / W;
+          uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+          if (y < H) {
+            const float4* g = reinterpret_cast<const float4*>(
+                dout + ((((long long)n * D + z) * H + y) * W + v % W) * NO + cg * 8);
+            const float4 f0 = g[0], f1 = g[1];
+            pk = make_uint4(pack2(f0.x, f0.y), pack2(f0.z, f0.w), pack2(f1.x, f1.y), pack2(f1.z, f1.w));
+          }
+          *reinterpret_cast<uint4*>(Gs + cg * NV * 16 + v * 16) = pk;
+        }
+      }
+      stage_halo_finish<W, ROWS>(As);
+      fence_proxy_async_smem();  // the staged rows, written through the generic proxy, for the tensor core
+      __syncthreads();
+      if ((t & 31) == 0) {
+        // issuer w: the (dz, dy) pairs w, w + 4, w + 8 (nine over four issuers)
+        tc_fence_after();
+        const uint64_t a0 = smem_desc(Gs, 128, NV * 16);  // K groups (8 voxels) 128 B, M groups (8 co) NV 16 B
+        const uint64_t b0 = smem_desc(As, 128, BOX);      // K groups 128 B, N groups (half, then dx) one box
+        for (int p = warp; p < 9; p += 4) {
+          const int dz = p / 3 - 1, dy = p % 3 - 1;
+#pragma unroll
+          for (int ks = 0; ks < NV / 16; ks++) {
+            const int v0 = ks * 16, ty = v0 / W, x0 = v0 % W;
+            const unsigned boff = (unsigned)((((dz + 1) * (RY + 2) + ty + dy + 1) * W + x0) * 16) >> 4;
+            tc_mma(taddr + p * 48, a0 + (unsigned)(v0 * 16 >> 4), b0 + boff, IDESC, !(first && ks == 0));
+          }
+        }
+        tc_commit(mma_bar);
+      }
+      first = false;
+    }
+    if (!first) {
+      wait(mma_bar, phase & 1);
+      phase++;
+    }
+    tc_fence_after();
+    // the chunk's partial: lane co of warp co / 32 holds D[co][dx 16 + ci] of pair p
+    float* pb = part + (long long)blockIdx.x * 27 * Cin * NO;
+    if (warp * 32 < NO) {
+      const int co = t;
+#pragma unroll 1
+      for (int p = 0; p < 9; p++) {
+#pragma unroll
+        for (int dxi = 0; dxi < 3; dxi++) {
+          float r[16];
+          tc_ld16(taddr + ((unsigned)(warp * 32) << 16) + p * 48 + dxi * 16, r);
+          tc_wait_ld();
+          const int tap = p * 3 + dxi;  // (dz + 1) 9 + (dy + 1) 3 + (dx + 1)
+          if (co < NO) {
+#pragma unroll
+            for (int i = 0; i < 16; i++) pb[((long long)tap * Cin + kc * 16 + i) * NO + co] = first ? 0.0f : r[i];
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // the accumulators are read before the next chunk's MMAs overwrite them
+    tc_fence_after();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(taddr, NCOLS);
+}
+
+// dW = sum over the blocks p (in order) of part[p][tap][ci][co]
+__global__ void k_dw_reduce_halo(const float* part, int nblk, long long n, float* dW) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int b = 0; b < nblk; b++) s += part[(long long)b * n + i];
+    dW[i] = s;
+  }
+}
+
 // dW[tap][ci][co] = sum over the voxel blocks p (in order) of part[p][tile][row][co]
 __global__ void k_dw_reduce_tc(const float* part, int nblk, int ntiles, int Cin, int Cout, float* dW) {
   const long long n = 27LL * Cin * Cout;
@@ -943,17 +1103,48 @@ int tmn_conv3d_backward_weight(const void* in, const float* dout, float* dW, flo
   const long long nvox = (long long)N * D * H * W;
   if (nvox < 1) return -1;
   if (work_floats < tmn_conv3d_backward_weight_work(nvox, Cin, Cout)) return -5;
-  const long long pofs = ((nvox * Cout + 1) / 2 + 3) / 4 * 4;
-  const int tiles = 4 * (Cin / 16);
-  const long long per_blk = (long long)tiles * 128 * Cout;
-  // voxel blocks: about four blocks per SM over all tiles (each block's loop is bound by the
-  // latency of its gathers, so several of them in flight), no more than the work buffer holds
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
   }
+  if ((W == 8 || W == 16 || W == 32 || W == 64) && (reinterpret_cast<uintptr_t>(in) & 15) == 0) {
+    // halo tiles: one persistent block per SM, as many as the work buffer holds partials for
+    const long long per = 27LL * Cin * Cout, ntl = (long long)N * D * ((H + 128 / W - 1) / (128 / W));
+    long long nblk = work_floats / per;
+    if (nblk > nsm) nblk = nsm;
+    if (nblk > ntl) nblk = ntl;
+    const bf16* x = reinterpret_cast<const bf16*>(in);
+    int r = 0;
+    auto run = [&](auto kernel, size_t sm) {
+      if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        r = -4;
+      else
+        kernel<<<(unsigned)nblk, 128, sm, s>>>(x, dout, work, N, D, H, Cin);
+    };
+#define TMN_DW_HALO(WW)                                                             \
+  if (W == WW) {                                                                    \
+    if (Cout == 16) run(k_conv_dw_halo<WW, 16>, dw_halo_smem<WW>());                \
+    if (Cout == 32) run(k_conv_dw_halo<WW, 32>, dw_halo_smem<WW>());                \
+    if (Cout == 64) run(k_conv_dw_halo<WW, 64>, dw_halo_smem<WW>());                \
+  }
+    TMN_DW_HALO(8)
+    TMN_DW_HALO(16)
+    TMN_DW_HALO(32)
+    TMN_DW_HALO(64)
+#undef TMN_DW_HALO
+    if (r) return r;
+    k_dw_reduce_halo<<<grid_of(per), 256, 0, s>>>(work, (int)nblk, per, dW);
+    k_db<<<Cout, 256, 0, s>>>(dout, nvox, Cout, db);
+    return ok();
+  }
+  const long long pofs = ((nvox * Cout + 1) / 2 + 3) / 4 * 4;
+  const int tiles = 4 * (Cin / 16);
+  const long long per_blk = (long long)tiles * 128 * Cout;
+  // voxel blocks: about four blocks per SM over all tiles (each block's loop is bound by the
+  // latency of its gathers, so several of them in flight), no more than the work buffer holds
   const long long chunks = (nvox + 15) / 16;
   long long nblk = (work_floats - pofs) / per_blk;
   const long long want = ((long long)kDwBlocksPerSm * nsm + tiles - 1) / tiles;
@@ -962,7 +1153,6 @@ int tmn_conv3d_backward_weight(const void* in, const float* dout, float* dW, flo
   long long cpb = (chunks + nblk - 1) / nblk;
   if (cpb > kDwChunks) cpb = (cpb + kDwChunks - 1) / kDwChunks * kDwChunks;  // whole pipeline stages
   nblk = (chunks + cpb - 1) / cpb;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   bf16* g16 = reinterpret_cast<bf16*>(work);
   float* part = work + pofs;
   k_to_bf16<<<grid_of(nvox * Cout / 2 + 1), 256, 0, s>>>(dout, g16, nvox * Cout);

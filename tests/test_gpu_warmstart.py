@@ -142,8 +142,9 @@ def test_conv_backward_data_and_weight(L, cin, cout):
                                         cin, cout, S()) == -5
 
 
-# rows of W = 8 .. 64 voxels take the halo-tile kernels (TMA-staged rows shared by the 27
-# taps); D and H ragged against their 2-plane x (128 / W)-row tiles
+# rows of W = 8 .. 64 voxels take the halo-tile kernels (rows staged once per block, shared by
+# the 27 taps; the weight gradient's tiles are one plane x 128 / W rows); D and H ragged
+# against the tiles
 HALO = [((1, 3, 17, 8), 16, 16), ((2, 3, 9, 16), 32, 64), ((1, 5, 7, 32), 96, 32), ((1, 3, 3, 64), 48, 16),
         ((1, 2, 4, 64), 16, 32), ((2, 1, 2, 16), 64, 64)]
 
@@ -171,6 +172,19 @@ def test_conv_halo_forward_and_backward_data(L, dims, cin, cout):
     assert np.all(np.abs(din.cpu().numpy() - dx_ref) <= 1e-5 * bound + 1e-30)
     assert L.tmn_conv3d_backward_data(p(f32(g)), p(Wb), p(din), *dims, cin, cout, 1, S()) == 0  # accumulate
     assert np.all(np.abs(din.cpu().numpy() - 2 * dx_ref) <= 2e-5 * bound + 1e-30)
+    # weight gradient by halo tiles: one float32 partial per persistent block, 1, 3 or as many
+    # blocks as the work buffer allows
+    _, dW_ref, db_ref = U.conv_backward(x, W, g)
+    _, dWb, dbb = U.conv_backward(np.abs(x), W, np.abs(g))
+    dW = torch.empty(27, cin, cout, device=DEV)
+    db = torch.empty(cout, device=DEV)
+    base = L.tmn_conv3d_backward_weight_work(int(np.prod(dims)), cin, cout)
+    for nblk in (1, 3, 1000):
+        work = torch.empty(max(base, nblk * 27 * cin * cout), device=DEV)
+        assert L.tmn_conv3d_backward_weight(p(to_bf16_dev(x)), p(f32(g)), p(dW), p(db), p(work), work.numel(),
+                                            *dims, cin, cout, S()) == 0
+        assert np.all(np.abs(dW.cpu().numpy() - dW_ref) <= 1e-5 * dWb + 1e-30)
+        assert np.all(np.abs(db.cpu().numpy() - db_ref) <= 1e-5 * dbb + 1e-30)
     assert net_status(L) == 0
 
 
