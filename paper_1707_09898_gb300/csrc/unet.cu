@@ -873,18 +873,38 @@ __global__ void k_to_bf16(const float* x, bf16* y, long long n) {
 }
 
 // the bias gradient: float32 sum over the voxels of the unrounded output gradient
-__global__ void k_db(const float* dout, long long nvox, int C, float* db) {
-  const int c = blockIdx.x;
+// The bias gradient db[c] = sum over the voxels of dout[v][c] (float32, unrounded), in a
+// fixed order: block b sums its range of voxels for every channel (consecutive threads on
+// consecutive channels, then voxels), k_db_final adds the block partials in block order.
+constexpr int kDbBlocks = 256;
+__global__ void __launch_bounds__(256) k_db_part(const float* dout, long long nvox, int C, float* part) {
   __shared__ float red[256];
+  const int t = threadIdx.x, c = t % C, lane = t / C, lanes = 256 / C;
+  const long long chunk = (nvox + gridDim.x - 1) / gridDim.x;
+  const long long v0 = blockIdx.x * chunk, v1 = v0 + chunk < nvox ? v0 + chunk : nvox;
   float s = 0.0f;
-  for (long long v = threadIdx.x; v < nvox; v += blockDim.x) s += dout[v * C + c];
-  red[threadIdx.x] = s;
+  for (long long v = v0 + lane; v < v1; v += lanes) s += dout[v * C + c];
+  red[t] = s;
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
+  if (t < C) {
+    float a = 0.0f;
+    for (int l = 0; l < lanes; l++) a += red[l * C + t];
+    part[(long long)blockIdx.x * C + t] = a;
   }
-  if (threadIdx.x == 0) db[c] = red[0];
+}
+__global__ void k_db_final(const float* part, int nblk, int C, float* db) {
+  if ((int)threadIdx.x < C) {
+    float a = 0.0f;
+    for (int b = 0; b < nblk; b++) a += part[(long long)b * C + threadIdx.x];
+    db[threadIdx.x] = a;
+  }
+}
+// after the weight gradient's partials are consumed, work holds the bias partials
+int launch_db(const float* dout, long long nvox, int C, float* work, float* db, cudaStream_t s) {
+  const int nb = (int)(nvox < kDbBlocks ? nvox : kDbBlocks);
+  k_db_part<<<nb, 256, 0, s>>>(dout, nvox, C, work);
+  k_db_final<<<1, 64, 0, s>>>(work, nb, C, db);
+  return 0;
 }
 
 // g *= (act > 0): ReLU backward through the stored bfloat16 activation
@@ -1137,7 +1157,7 @@ int tmn_conv3d_backward_weight(const void* in, const float* dout, float* dW, flo
 #undef TMN_DW_HALO
     if (r) return r;
     k_dw_reduce_halo<<<grid_of(per), 256, 0, s>>>(work, (int)nblk, per, dW);
-    k_db<<<Cout, 256, 0, s>>>(dout, nvox, Cout, db);
+    launch_db(dout, nvox, Cout, work, db, s);
     return ok();
   }
   const long long pofs = ((nvox * Cout + 1) / 2 + 3) / 4 * 4;
@@ -1170,7 +1190,7 @@ int tmn_conv3d_backward_weight(const void* in, const float* dout, float* dW, flo
   if (Cout == 64) run(k_conv_dw_tc<64>, dw_tc_smem<64>());
   if (r) return r;
   k_dw_reduce_tc<<<grid_of(27LL * Cin * Cout), 256, 0, s>>>(part, (int)nblk, tiles, Cin, Cout, dW);
-  k_db<<<Cout, 256, 0, s>>>(dout, nvox, Cout, db);
+  launch_db(dout, nvox, Cout, work, db, s);
   return ok();
 }
 
