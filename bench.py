@@ -48,18 +48,18 @@ UNIT = "evals/s"
 # 256^3 step, each from one ncu capture of the kernel as built from the named source file;
 # a figure is reported only while that file is unchanged.
 MEASURED_TRAFFIC = {
-    "x_forward": {"bytes": 282.1e6, "source": "paper_1707_09898_gb300/csrc/k_xfwd.cu",  # with the fused step
+    "x_forward": {"bytes": 282.2e6, "source": "paper_1707_09898_gb300/csrc/k_xfwd.cu",  # with the fused step
                   "source_sha1": "c37b74d2d49959d1d27713fd22a6deb58ea25069"},
-    "yz_forward": {"bytes": 219.2e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
-                   "source_sha1": "b7e384901f42d510dec91296a400d1a5ef801e3e"},
+    "yz_forward": {"bytes": 219.1e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
+                   "source_sha1": "98227a45ccd29cff2420ec2ac14ce9db3d1caf7f"},
     "y_inverse": {"bytes": 11.1e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",  # the finishing kernel
-                  "source_sha1": "b7e384901f42d510dec91296a400d1a5ef801e3e"},
-    "zy_adjoint": {"bytes": 161.0e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
-                   "source_sha1": "b7e384901f42d510dec91296a400d1a5ef801e3e"},
-    "x_inverse": {"bytes": 250.3e6, "source": "paper_1707_09898_gb300/csrc/k_xinv.cu",
+                  "source_sha1": "98227a45ccd29cff2420ec2ac14ce9db3d1caf7f"},
+    "zy_adjoint": {"bytes": 161.1e6, "source": "paper_1707_09898_gb300/csrc/k_yzfused.cu",
+                   "source_sha1": "98227a45ccd29cff2420ec2ac14ce9db3d1caf7f"},
+    "x_inverse": {"bytes": 250.6e6, "source": "paper_1707_09898_gb300/csrc/k_xinv.cu",
                   "source_sha1": "1db0b31247b968b8ac460d25b5bff05d1900e42e"},
     "objective": {"bytes": 0.66e6, "source": "paper_1707_09898_gb300/csrc/k_xobj.cu",
-                  "source_sha1": "9f7626a15c078cc5e39ce7c758676ac6afb9578a"},
+                  "source_sha1": "c3bd93ef1d8d2023b6f5163bbec502652dfa6488"},
 }
 
 
@@ -785,14 +785,22 @@ def run_native(args):
             abn = alg_bytes(wn, Ln, direct=True, fused=q.fused,
                             step_fused=q.one_call and Ln[0] == 512 and wn.m0_kind == "const")
             bn = step_bytes(pn, abn, prof_steps)
-            sweep.append({"workload": wn.name, "cells": list(wn.n_out), "fft": list(Ln),
-                          "value": args.steps / (msn / 1e3), "unit": UNIT, "ms_per_step": msn / args.steps,
-                          "alg_bytes_per_step": bn, "frac_step": bn / (msn / args.steps / 1e3) / 1e9 / hbm,
-                          "roofline": roofline(pn, abn, prof_steps, hbm, peak_kind, False)})
+            entry = {"workload": wn.name, "cells": list(wn.n_out), "fft": list(Ln),
+                     "value": args.steps / (msn / 1e3), "unit": UNIT, "ms_per_step": msn / args.steps,
+                     "alg_bytes_per_step": bn, "frac_step": bn / (msn / args.steps / 1e3) / 1e9 / hbm,
+                     "roofline": roofline(pn, abn, prof_steps, hbm, peak_kind, False)}
             if not args.no_cpu_baseline:
                 gpu_results[n] = q.results_at_rho0()
             q.close()
             torch.cuda.empty_cache()
+            if args.m0 == "const":  # the plain cuFFT pipeline on the same workload, same protocol
+                qc = Prepared(wn, dev, args, impl="cufft")
+                msc_n, _ = time_loop(qc.step, args.steps, args.warmup)
+                entry["cufft"] = {"value": args.steps / (msc_n / 1e3), "unit": UNIT, "ms_per_step": msc_n / args.steps}
+                entry["vs_cufft"] = entry["value"] / entry["cufft"]["value"]
+                qc.close()
+                torch.cuda.empty_cache()
+            sweep.append(entry)
 
     cufft = None
     if extras and args.m0 == "const":
