@@ -18,6 +18,7 @@
 
 #include "fft.cuh"
 #include "internal.h"
+#include "unet_tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -70,6 +71,7 @@ struct TensorCol {
   float sy;
   int need, single;  // bitmask of components; index if exactly one is needed, else -1
   float coef[6];
+  float c1;          // coef[single] (no run-time index into coef)
   __device__ __forceinline__ float at(int kz, int Lz) const {
     const bool lo = kz <= Lz / 2;
     const int kzf = lo ? kz : Lz - kz;
@@ -77,7 +79,7 @@ struct TensorCol {
     const float* t = T + kzf * Tz;
     if (single >= 0) {
       const float sg = single == 3 ? sy : single == 4 ? sz : single == 5 ? sy * sz : 1.0f;
-      return coef[single] * sg * t[single * Tc];
+      return c1 * sg * t[single * Tc];
     }
     float r = 0.0f;
     if (need & 1) r += coef[0] * t[0];
@@ -98,11 +100,21 @@ __device__ __forceinline__ TensorCol make_tcol(const ZArgs& a, int o, int i, int
   t.sy = sy;
   t.need = 0;
 #pragma unroll
-  for (int c = 0; c < 6; c++) {
-    t.coef[c] = a.coef[o][i][c];
-    if (t.coef[c] != 0.0f) t.need |= 1 << c;
+  for (int c = 0; c < 6; c++) {  // (o, i) selected by compile-time indexes: no local copy of a.coef
+    float v = 0.0f;
+#pragma unroll
+    for (int oo = 0; oo < 3; oo++)
+#pragma unroll
+      for (int ii = 0; ii < 3; ii++)
+        if (oo == o && ii == i) v = a.coef[oo][ii][c];
+    t.coef[c] = v;
+    if (v != 0.0f) t.need |= 1 << c;
   }
   t.single = (t.need != 0 && (t.need & (t.need - 1)) == 0) ? __ffs(t.need) - 1 : -1;
+  t.c1 = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 6; c++)
+    if (c == t.single) t.c1 = t.coef[c];
   return t;
 }
 
@@ -222,6 +234,171 @@ __global__ void __launch_bounds__(kNT, 3) k_z1(ZArgs a) {
     dit_stage0_store<float, L, kNT>(tile, tw, [&](int pos, int line, cx<float> v) {
       if (pos >= olo && pos < ohi) out[pos * a.zstride + line] = v;
     });
+  }
+}
+
+// One input, every output in one block, for two-stage plans with R0 = 2 R1 = 2 M0 and
+// n_in, n_out <= L/2 (L = 512 = 32 x 16): the forward transform of the column tile is
+// computed once. Thread (line, j) runs stage-0 unit j (the radix-32 DFT of an input
+// whose upper half is zero, as two 16-point DFTs); thread (line, g) then finishes the
+// last-stage units g and g + R0/2 and keeps their spectra in tensor memory (64 columns of
+// its lane). For each output: the spectra times s_o (the tensor combination), the first
+// inverse stage into the tile, and the last inverse stage, which forms only the rows
+// z < L/2 and writes those in [olo, ohi).
+// Tensor factors of last-stage unit g for output o: frequencies kz = kb + q L/R1 (kb =
+// k_of_group(g)). With one tensor component the folded row of every q is a compile-time
+// offset from one of two bases (kz <= L/2 for q < R1/2, above for q > R1/2, and at q = R1/2
+// unless kb = 0), and the sign under kz -> L - kz is fixed per side.
+template <int L>
+__device__ __forceinline__ void z_factors(const TensorCol& tc, int kb, float* f) {
+  constexpr int R1 = StageShape<L, plan_stages(L) - 1>::R, QS = L / R1;
+  if (tc.single >= 0) {
+    const int c = tc.single;
+    const float* lo = tc.T + c * tc.Tc + kb * tc.Tz;
+    const float* hi = tc.T + c * tc.Tc + (L - kb) * tc.Tz;
+    const float slo = tc.c1 * ((c == 3 || c == 5) ? tc.sy : 1.0f);
+    const float shi = (c == 4 || c == 5) ? -slo : slo;
+#pragma unroll
+    for (int q = 0; q < R1; q++) {
+      const long long off = (long long)q * QS * tc.Tz;
+      if (q < R1 / 2) f[q] = slo * lo[off];
+      else if (q > R1 / 2) f[q] = shi * hi[-off];
+      else f[q] = kb == 0 ? slo * lo[off] : shi * hi[-off];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < R1; q++) f[q] = tc.at(kb + q * QS, L);
+  }
+}
+
+template <int L>
+__host__ __device__ constexpr bool zmulti_plan() {
+  return plan_stages(L) == 2 && StageShape<L, 0>::R == 2 * StageShape<L, 1>::R &&
+         StageShape<L, 0>::M == StageShape<L, 1>::R && StageShape<L, 1>::R == TB;
+}
+constexpr unsigned kZmTmemCols = 128;  // 64 per thread; two warps share each lane quarter
+template <int L>
+__global__ void __launch_bounds__(kNT, 2) k_z1m(ZArgs a) {
+  using S0 = StageShape<L, 0>;
+  using S1 = StageShape<L, 1>;
+  constexpr int R0 = S0::R, M0 = S0::M, R1 = S1::R;
+  static_assert(R0 == 2 * R1 && M0 == R1 && M0 * TB == kNT && (L / R1) * TB == 2 * kNT, "plan");
+  extern __shared__ __align__(16) unsigned char smem[];
+  cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
+  cx<float>* tile = tw + L;
+  __shared__ unsigned tslot;
+  const int t = threadIdx.x, warp = t / 32;
+  load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
+  if (warp == 0) {
+    tmem_alloc(&tslot, kZmTmemCols);
+    tmem_relinquish();
+  }
+  const int chunk = blockIdx.x;
+  const int2 col = a.zcol[blockIdx.y];  // (ky position, ky)
+  const int kyf = col.y <= a.Ly / 2 ? col.y : a.Ly - col.y;
+  const float sy = col.y <= a.Ly / 2 ? 1.0f : -1.0f;
+  const long long colo = (long long)col.x * a.P + chunk * TB;
+  const cx<float>* in = reinterpret_cast<const cx<float>*>(a.buf) + a.in_slot[0] * a.cstride + colo;
+  int ilo = 0, ihi = a.n_in, olo = 0, ohi = a.n_out;
+  if (a.in_ext) {
+    ilo = max(a.ext[0], 0);
+    ihi = min(a.ext[1], a.n_in);
+  }
+  if (a.out_ext) {
+    olo = max(a.ext[0], 0);
+    ohi = min(a.ext[1], a.n_out);
+  }
+  const int line = t % TB, j = t / TB;
+  // the tensor factors of both last-stage units for output o, loaded one phase ahead of
+  // their use (output 0's with the input rows)
+  float f[2][R1];
+  auto load_factors = [&](int o) {
+    const TensorCol tcol = make_tcol(a, o, 0, kyf, sy, chunk * TB + line);
+#pragma unroll
+    for (int it = 0; it < 2; it++) z_factors<L>(tcol, k_of_group<L>(it * (R0 / 2) + j), f[it]);
+  };
+  {  // stage 0: rows z = j + q M0 < L/2 in, positions j + q M0 (q < R0) of the tile out
+    cx<float> v[R0];
+#pragma unroll
+    for (int q = 0; q < R0 / 2; q++) {
+      const int z = j + q * M0;
+      v[q] = (z >= ilo && z < ihi) ? in[z * a.zstride + line] : zero<float>();
+    }
+    load_factors(0);
+    dft32_half_input<false>(v);
+    if (j != 0) {
+#pragma unroll
+      for (int q = 1; q < R0; q++) v[q] = cmul(v[q], tw[j * q]);
+    }
+#pragma unroll
+    for (int q = 0; q < R0; q++) tile[(j + q * M0) * TB + line] = v[q];
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tsp = tslot + ((unsigned)((warp % 4) * 32) << 16) + (unsigned)((warp / 4) * 64);
+  // last forward stage of units g = t / TB and g + R0/2, spectra into tensor memory
+#pragma unroll
+  for (int it = 0; it < 2; it++) {
+    const int g = it * (R0 / 2) + j;
+    cx<float> v[R1];
+#pragma unroll
+    for (int q = 0; q < R1; q++) v[q] = tile[(g * R1 + q) * TB + line];
+    DftF<R1, false>::run(v);
+#pragma unroll
+    for (int c = 0; c < R1 / 8; c++) {
+      float b[16];
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        b[2 * k] = v[8 * c + k].x;
+        b[2 * k + 1] = v[8 * c + k].y;
+      }
+      tc_st16(tsp + 32 * it + 16 * c, b);
+    }
+  }
+  tc_wait_st();
+  for (int o = 0; o < a.nout; o++) {
+    __syncthreads();  // every read of the tile (previous output's last stage, or the spectra) is done
+#pragma unroll
+    for (int it = 0; it < 2; it++) {  // spectra times s_o, first inverse stage
+      const int g = it * (R0 / 2) + j;
+      cx<float> v[R1];
+#pragma unroll
+      for (int c = 0; c < R1 / 8; c++) {
+        float b[16];
+        tc_ld16(tsp + 32 * it + 16 * c, b);
+        tc_wait_ld();
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[8 * c + k] = scale(mk(b[2 * k], b[2 * k + 1]), f[it][8 * c + k]);
+      }
+      DftF<R1, true>::run(v);
+#pragma unroll
+      for (int q = 0; q < R1; q++) tile[(g * R1 + q) * TB + line] = v[q];
+    }
+    if (o + 1 < a.nout) load_factors(o + 1);
+    __syncthreads();
+    {  // last inverse stage: positions j + q M0 in, rows z = j + q M0 < L/2 out
+      cx<float> v[R0];
+#pragma unroll
+      for (int q = 0; q < R0; q++) v[q] = tile[(j + q * M0) * TB + line];
+      if (j != 0) {
+#pragma unroll
+        for (int q = 1; q < R0; q++) v[q] = cmulc(v[q], tw[j * q]);
+      }
+      dft_low_half<R0, true>(v);
+      cx<float>* out = reinterpret_cast<cx<float>*>(a.buf) + a.out_slot[o] * a.cstride + colo;
+#pragma unroll
+      for (int q = 0; q < R0 / 2; q++) {
+        const int z = j + q * M0;
+        if (z >= olo && z < ohi) out[z * a.zstride + line] = v[q];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tslot, kZmTmemCols);
   }
 }
 
@@ -349,6 +526,20 @@ int run_y(const YArgs& a, int ncomp, cudaStream_t s) {
 template <int L>
 int run_z(const ZArgs& a, cudaStream_t s) {
   const size_t sm = tile_smem<L>();
+  if constexpr (zmulti_plan<L>()) {
+    // one input over its whole range, and either every output plane or several outputs
+    // (a single output on a few target planes keeps the other kernel's direct inverse)
+    if (a.nin == 1 && !a.in_ext && (!a.out_ext || a.nout > 1) && a.n_in <= L / 2 && a.n_out <= L / 2) {
+      static bool initm = false;
+      if (!initm) {
+        if (cudaFuncSetAttribute(k_z1m<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+          return -1;
+        initm = true;
+      }
+      k_z1m<L><<<dim3(a.P / TB, a.Ly), kNT, sm, s>>>(a);
+      return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
+    }
+  }
   if (a.nin == 1) {
     static bool init = false;
     if (!init) {

@@ -1,7 +1,8 @@
-// Fifth-generation tensor-core (tcgen05) building blocks for the warm-start network's
-// convolutions on sm_103a: tensor-memory allocation, the single-thread MMA with
-// shared-memory operand descriptors, completion through an mbarrier, and the
-// tensor-memory load of the accumulator for the epilogue.
+// Fifth-generation tensor-core (tcgen05) building blocks on sm_103a: tensor-memory
+// allocation, the single-thread MMA with shared-memory operand descriptors (the
+// warm-start network's convolutions), completion through an mbarrier, and tensor-memory
+// loads and stores (the convolutions' epilogue; the fused y/z kernels keep per-thread
+// running sums there).
 //
 // Operand layout (both A and B "K-major", no swizzle): the matrix is cut into core
 // matrices of 8 rows x 8 bfloat16 (16 bytes per row, 128 bytes per core matrix, rows
@@ -79,6 +80,20 @@ __device__ __forceinline__ void tc_ld16(unsigned taddr, float* r) {
   for (int i = 0; i < 16; i++) r[i] = __uint_as_float(u[i]);
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+// the matching store: lane t of the warp writes r[0 .. 15] to row (lane quarter) + t,
+// columns col .. col + 15; tc_wait_st() waits until this thread's stores have completed
+__device__ __forceinline__ void tc_st16(unsigned taddr, const float* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};\n" ::"r"(taddr),
+      "r"(__float_as_uint(r[0])), "r"(__float_as_uint(r[1])), "r"(__float_as_uint(r[2])), "r"(__float_as_uint(r[3])),
+      "r"(__float_as_uint(r[4])), "r"(__float_as_uint(r[5])), "r"(__float_as_uint(r[6])), "r"(__float_as_uint(r[7])),
+      "r"(__float_as_uint(r[8])), "r"(__float_as_uint(r[9])), "r"(__float_as_uint(r[10])),
+      "r"(__float_as_uint(r[11])), "r"(__float_as_uint(r[12])), "r"(__float_as_uint(r[13])),
+      "r"(__float_as_uint(r[14])), "r"(__float_as_uint(r[15]))
+      : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
 // 16-byte asynchronous copy global -> shared; src_bytes = 0 fills the 16 bytes with zeros
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, unsigned src_bytes) {
