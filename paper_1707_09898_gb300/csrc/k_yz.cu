@@ -277,7 +277,7 @@ __host__ __device__ constexpr bool zmulti_plan() {
          StageShape<L, 0>::M == StageShape<L, 1>::R && StageShape<L, 1>::R == TB;
 }
 constexpr unsigned kZmTmemCols = 128;  // 64 per thread; two warps share each lane quarter
-template <int L>
+template <int L, bool EXT>
 __global__ void __launch_bounds__(kNT, 2) k_z1m(ZArgs a) {
   using S0 = StageShape<L, 0>;
   using S1 = StageShape<L, 1>;
@@ -287,6 +287,7 @@ __global__ void __launch_bounds__(kNT, 2) k_z1m(ZArgs a) {
   cx<float>* tw = reinterpret_cast<cx<float>*>(smem);
   cx<float>* tile = tw + L;
   __shared__ unsigned tslot;
+  __shared__ cx<float> small[kNT / TB][TB];
   const int t = threadIdx.x, warp = t / 32;
   load_twiddles<float, kNT>(tw, reinterpret_cast<const cx<float>*>(a.tw), L);
   if (warp == 0) {
@@ -308,6 +309,10 @@ __global__ void __launch_bounds__(kNT, 2) k_z1m(ZArgs a) {
     olo = max(a.ext[0], 0);
     ohi = min(a.ext[1], a.n_out);
   }
+  ihi = max(ihi, ilo);
+  ohi = max(ohi, olo);
+  // a few planes on either side: direct transforms of those planes instead
+  const bool din = EXT && ihi - ilo <= kDirectPlanes, dout = EXT && ohi - olo <= kDirectPlanes;
   const int line = t % TB, j = t / TB;
   // the tensor factors of both last-stage units for output o, loaded one phase ahead of
   // their use (output 0's with the input rows)
@@ -317,7 +322,10 @@ __global__ void __launch_bounds__(kNT, 2) k_z1m(ZArgs a) {
 #pragma unroll
     for (int it = 0; it < 2; it++) z_factors<L>(tcol, k_of_group<L>(it * (R0 / 2) + j), f[it]);
   };
-  {  // stage 0: rows z = j + q M0 < L/2 in, positions j + q M0 (q < R0) of the tile out
+  if (din) {  // the whole spectrum at its DIF positions
+    load_factors(0);
+    direct_in<L>(tile, tw, in, a.zstride, ilo, ihi, small);
+  } else {  // stage 0: rows z = j + q M0 < L/2 in, positions j + q M0 (q < R0) of the tile out
     cx<float> v[R0];
 #pragma unroll
     for (int q = 0; q < R0 / 2; q++) {
@@ -344,7 +352,7 @@ __global__ void __launch_bounds__(kNT, 2) k_z1m(ZArgs a) {
     cx<float> v[R1];
 #pragma unroll
     for (int q = 0; q < R1; q++) v[q] = tile[(g * R1 + q) * TB + line];
-    DftF<R1, false>::run(v);
+    if (!din) DftF<R1, false>::run(v);
 #pragma unroll
     for (int c = 0; c < R1 / 8; c++) {
       float b[16];
@@ -371,13 +379,16 @@ __global__ void __launch_bounds__(kNT, 2) k_z1m(ZArgs a) {
 #pragma unroll
         for (int k = 0; k < 8; k++) v[8 * c + k] = scale(mk(b[2 * k], b[2 * k + 1]), f[it][8 * c + k]);
       }
-      DftF<R1, true>::run(v);
+      if (!dout) DftF<R1, true>::run(v);
 #pragma unroll
       for (int q = 0; q < R1; q++) tile[(g * R1 + q) * TB + line] = v[q];
     }
     if (o + 1 < a.nout) load_factors(o + 1);
     __syncthreads();
-    {  // last inverse stage: positions j + q M0 in, rows z = j + q M0 < L/2 out
+    if (dout) {  // the few output planes from the whole spectrum
+      direct_out<L>(tile, tw, reinterpret_cast<cx<float>*>(a.buf) + a.out_slot[o] * a.cstride + colo, a.zstride,
+                    olo, ohi, small);
+    } else {  // last inverse stage: positions j + q M0 in, rows z = j + q M0 < L/2 out
       cx<float> v[R0];
 #pragma unroll
       for (int q = 0; q < R0; q++) v[q] = tile[(j + q * M0) * TB + line];
@@ -527,16 +538,17 @@ template <int L>
 int run_z(const ZArgs& a, cudaStream_t s) {
   const size_t sm = tile_smem<L>();
   if constexpr (zmulti_plan<L>()) {
-    // one input over its whole range, and either every output plane or several outputs
-    // (a single output on a few target planes keeps the other kernel's direct inverse)
-    if (a.nin == 1 && !a.in_ext && (!a.out_ext || a.nout > 1) && a.n_in <= L / 2 && a.n_out <= L / 2) {
-      static bool initm = false;
-      if (!initm) {
-        if (cudaFuncSetAttribute(k_z1m<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-          return -1;
-        initm = true;
+    if (a.nin == 1 && a.n_in <= L / 2 && a.n_out <= L / 2) {
+      // EXT: the input or output planes come from the device range a.ext, and a few of them
+      // take the direct transforms
+      const bool ext = a.in_ext || a.out_ext;
+      auto kern = ext ? k_z1m<L, true> : k_z1m<L, false>;
+      static bool initm[2] = {false, false};
+      if (!initm[ext]) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
+        initm[ext] = true;
       }
-      k_z1m<L><<<dim3(a.P / TB, a.Ly), kNT, sm, s>>>(a);
+      kern<<<dim3(a.P / TB, a.Ly), kNT, sm, s>>>(a);
       return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
     }
   }
