@@ -79,6 +79,8 @@ def parse(argv=None):
                     help="prepared path: tm_evaluate + tm_optimize_step per step instead of tm_evaluate_step")
     ap.add_argument("--separate-yz", action="store_true",
                     help="prepared path: y and direct z passes as separate kernels (default: fused)")
+    ap.add_argument("--stray-field-only", action="store_true",
+                    help="time tm_stray_field (full-grid H) on the workload and print only that leg")
     ap.add_argument("--m0", choices=["const", "vmf"], default="const",
                     help="magnetization: constant (0, 0, Ms), or spatially varying (von Mises-Fisher)")
     return ap.parse_args(argv)
@@ -685,6 +687,13 @@ def run_native(args):
     hbm, peak_kind = peaks()
     wl = W.config4(args.n, args.m0)
     p = Prepared(wl, dev, args, impl=args.impl)
+    if args.stray_field_only:  # the general pipeline's full-grid field alone (profiling runs)
+        H = torch.empty((3,) + wl.out_shape, dtype=torch.float32, device=dev)
+        msg, _ = time_loop(lambda: p.m.stray_field(p.rho, out=H), args.steps, args.warmup)
+        print(json.dumps({"stray_field": {"value": args.steps / (msg / 1e3), "unit": "calls/s",
+                                          "ms_per_call": msg / args.steps, "workload": wl.name}}))
+        p.close()
+        return
     nv = NvmlClocks(dev)
     smi = None if nv.ok else SmiClocks(local)
     if smi:
