@@ -26,6 +26,15 @@ namespace tmk {
 
 namespace {
 
+// Two-stage plans with R0 = 2 R1 = 2 M0 = 32 (L = 512 = 32 x 16): the radix-32 stage of an
+// input whose upper half is zero runs as two 16-point DFTs (dft32_half_input), and an
+// inverse whose upper half is cropped forms only its lower half (dft_low_half).
+template <int L>
+__host__ __device__ constexpr bool zmulti_plan() {
+  return plan_stages(L) == 2 && StageShape<L, 0>::R == 2 * StageShape<L, 1>::R &&
+         StageShape<L, 0>::M == StageShape<L, 1>::R && StageShape<L, 1>::R == TB;
+}
+
 template <int L, bool INV>
 __global__ void __launch_bounds__(kNT, 3) k_ypass(YArgs a) {
   constexpr int S = plan_stages(L);
@@ -45,6 +54,67 @@ __global__ void __launch_bounds__(kNT, 3) k_ypass(YArgs a) {
   cx<float>* out = reinterpret_cast<cx<float>*>(a.out) + a.out_slot[blockIdx.z] * a.out_cstride +
                    z * a.out_zstride + chunk * TB;
   __syncthreads();
+  if constexpr (zmulti_plan<L>()) {
+    using S1 = StageShape<L, 1>;
+    constexpr int R0 = StageShape<L, 0>::R, M0 = StageShape<L, 0>::M, R1 = S1::R;
+    const int line = threadIdx.x % TB, j = threadIdx.x / TB;
+    if (!INV && a.n_in <= L / 2) {
+      {  // stage 0: rows y = j + q M0 < n_in (<= L/2) in
+        cx<float> v[R0];
+#pragma unroll
+        for (int q = 0; q < R0 / 2; q++) {
+          const int y = j + q * M0;
+          v[q] = y < a.n_in ? in[y * a.in_pstride + line] : zero<float>();
+        }
+        dft32_half_input<false>(v);
+        if (j != 0) {
+#pragma unroll
+          for (int q = 1; q < R0; q++) v[q] = cmul(v[q], tw[j * q]);
+        }
+#pragma unroll
+        for (int q = 0; q < R0; q++) tile[(j + q * M0) * TB + line] = v[q];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int it = 0; it < 2; it++) {  // last stage: units g, positions g R1 + q out
+        const int g = it * (R0 / 2) + j;
+        cx<float> v[R1];
+#pragma unroll
+        for (int q = 0; q < R1; q++) v[q] = tile[(g * R1 + q) * TB + line];
+        DftF<R1, false>::run(v);
+#pragma unroll
+        for (int q = 0; q < R1; q++) out[(g * R1 + q) * a.out_pstride + line] = v[q];
+      }
+      return;
+    }
+    if (INV && a.n_out <= L / 2) {
+#pragma unroll
+      for (int it = 0; it < 2; it++) {  // first inverse stage: units g, positions g R1 + q in
+        const int g = it * (R0 / 2) + j;
+        cx<float> v[R1];
+#pragma unroll
+        for (int q = 0; q < R1; q++) v[q] = in[(g * R1 + q) * a.in_pstride + line];
+        DftF<R1, true>::run(v);
+#pragma unroll
+        for (int q = 0; q < R1; q++) tile[(g * R1 + q) * TB + line] = v[q];
+      }
+      __syncthreads();
+      cx<float> v[R0];  // last inverse stage: rows y = j + q M0 < n_out (<= L/2) out
+#pragma unroll
+      for (int q = 0; q < R0; q++) v[q] = tile[(j + q * M0) * TB + line];
+      if (j != 0) {
+#pragma unroll
+        for (int q = 1; q < R0; q++) v[q] = cmulc(v[q], tw[j * q]);
+      }
+      dft_low_half<R0, true>(v);
+#pragma unroll
+      for (int q = 0; q < R0 / 2; q++) {
+        const int y = j + q * M0;
+        if (y < a.n_out) out[y * a.out_pstride + line] = v[q];
+      }
+      return;
+    }
+  }
   if (!INV) {
     dif_stage0_load<float, L, kNT>(tile, tw, [&](int pos, int line) {
       return pos < a.n_in ? in[pos * a.in_pstride + line] : zero<float>();
@@ -271,11 +341,6 @@ __device__ __forceinline__ void z_factors(const TensorCol& tc, int kb, float* f)
   }
 }
 
-template <int L>
-__host__ __device__ constexpr bool zmulti_plan() {
-  return plan_stages(L) == 2 && StageShape<L, 0>::R == 2 * StageShape<L, 1>::R &&
-         StageShape<L, 0>::M == StageShape<L, 1>::R && StageShape<L, 1>::R == TB;
-}
 constexpr unsigned kZmTmemCols = 128;  // 64 per thread; two warps share each lane quarter
 template <int L, bool EXT>
 __global__ void __launch_bounds__(kNT, 2) k_z1m(ZArgs a) {
