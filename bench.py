@@ -79,6 +79,8 @@ def parse(argv=None):
                     help="prepared path: tm_evaluate + tm_optimize_step per step instead of tm_evaluate_step")
     ap.add_argument("--separate-yz", action="store_true",
                     help="prepared path: y and direct z passes as separate kernels (default: fused)")
+    ap.add_argument("--fft", type=int, default=0,
+                    help="padded FFT length of every axis of the headline workload (0: the library's default)")
     ap.add_argument("--stray-field-only", action="store_true",
                     help="time tm_stray_field (full-grid H) on the workload and print only that leg")
     ap.add_argument("--m0", choices=["const", "vmf"], default="const",
@@ -495,7 +497,8 @@ class Prepared:
         else:
             Impl = Magnet
         M0 = wl.M0_const() if wl.m0_kind == "const" else torch.from_numpy(wl.M0_field()).to(dev)
-        self.m = Impl(wl.n_out, wl.nzd, wl.cellsize, M0=M0, p=wl.p, device=dev.index or 0)
+        kw = {"fft_lengths": (args.fft,) * 3} if impl != "cufft" and getattr(args, "fft", 0) else {}
+        self.m = Impl(wl.n_out, wl.nzd, wl.cellsize, M0=M0, p=wl.p, device=dev.index or 0, **kw)
         self.rho0 = torch.from_numpy(wl.rho()).to(dev)
         self.rho = self.rho0.clone()
         self.mask = torch.from_numpy(wl.mask()).to(dev)
@@ -788,7 +791,7 @@ def run_native(args):
         sweep = []
         for n in (128, 192):
             wn = W.config4(n, args.m0)
-            q = Prepared(wn, dev, args)
+            q = Prepared(wn, dev, argparse.Namespace(**{**vars(args), "fft": 0}))  # default padding
             msn, ckn, pn, _ = measure(q, args)
             Ln = q.m.fft_lengths()
             abn = alg_bytes(wn, Ln, direct=True, fused=q.fused,

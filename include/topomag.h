@@ -67,11 +67,21 @@ const char* tm_version(void);
 /*
  * Grid (Sec. "Discretization": regular cuboid grid, Eq. (convolution)).
  * n_out[3] = (nx, ny, nz), each in [4, 288]; 1 <= nzd <= nz; cellsize[3] > 0.
- * Each axis is zero padded to L = the smallest supported even 2^a 3^b >= 2 n
- * (open boundaries). Allocates the workspace; discards tensor and M0.
+ * Each axis is zero padded to a length L >= 2 n (open boundaries): the smallest
+ * supported even 2^a 3^b >= 2 n, except that 288 and 384 are replaced by 512, whose
+ * 32 x 16 plan has the fused kernels (any L >= 2 n gives the same linear
+ * convolution). Allocates the workspace; discards tensor and M0.
  * TM_ERR_SIZE if an axis is outside the supported range.
  */
 int tm_set_grid(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[3]);
+
+/*
+ * tm_set_grid with chosen padded lengths: L[a] = 0 takes the default of tm_set_grid,
+ * otherwise L[a] must be one of the supported lengths (even 2^a 3^b from 8 to 576 with
+ * at most two factors 3) and >= 2 n_out[a], else TM_ERR_SIZE and nothing changes.
+ * L may be NULL (all defaults). Counts as tm_set_grid for TM_FAULT_INJECT.
+ */
+int tm_set_grid_lengths(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[3], const int L[3]);
 
 /* The padded FFT lengths (Lx, Ly, Lz) chosen by tm_set_grid. */
 int tm_get_fft_lengths(const tm_ctx* ctx, int L[3]);

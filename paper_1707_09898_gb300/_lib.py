@@ -31,6 +31,7 @@ _SIGS = {
     "tm_last_error": (ctypes.c_char_p, [vp]),
     "tm_version": (ctypes.c_char_p, []),
     "tm_set_grid": (ctypes.c_int, [vp, c_int3, ctypes.c_int, c_double3]),
+    "tm_set_grid_lengths": (ctypes.c_int, [vp, c_int3, ctypes.c_int, c_double3, c_int3]),
     "tm_get_fft_lengths": (ctypes.c_int, [vp, c_int3]),
     "tm_set_penalty": (ctypes.c_int, [vp, ctypes.c_double]),
     "tm_set_M0": (ctypes.c_int, [vp, vp, c_double3, vp]),

@@ -182,6 +182,22 @@ int check_status(tm_ctx* ctx, cudaStream_t s) {
   return TM_OK;
 }
 
+bool supported_L(int L) {
+  switch (L) {
+#define TM_CASE(LL) \
+  case LL:          \
+    return true;
+    TM_FOR_EACH_L(TM_CASE)
+#undef TM_CASE
+  }
+  return false;
+}
+
+// Default padded length of an axis of n cells: the smallest supported L >= 2 n, except that
+// a length strictly between 256 and 512 is replaced by 512. Any L >= 2 n gives the same
+// linear convolution; 512 = 32 x 16 has the fused and warp-specialized kernels, the
+// three-stage lengths 288 and 384 only the general ones (measured at 192^3: 0.246 ms per
+// evaluation with L = 384, 0.174 ms with L = 512).
 int pick_length(int n) {
   static const int ls[] = {
 #define TM_LIST(LL) LL,
@@ -189,7 +205,7 @@ int pick_length(int n) {
 #undef TM_LIST
   };
   for (int L : ls)
-    if (L >= 2 * n) return L;
+    if (L >= 2 * n) return (L > 256 && L < 512) ? 512 : L;
   return 0;
 }
 
@@ -753,6 +769,10 @@ void tm_destroy(tm_ctx* ctx) {
 const char* tm_last_error(const tm_ctx* ctx) { return ctx ? ctx->err : "null context"; }
 
 int tm_set_grid(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[3]) {
+  return tm_set_grid_lengths(ctx, n_out, nzd, cellsize, nullptr);
+}
+
+int tm_set_grid_lengths(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[3], const int L_in[3]) {
   INJECT(ctx, "tm_set_grid");
   if (!ctx || !n_out || !cellsize) return fail(ctx, TM_ERR_ARG, "null argument");
   for (int a = 0; a < 3; a++) {
@@ -761,6 +781,9 @@ int tm_set_grid(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[
     if (!(cellsize[a] > 0.0) || !isfinite(cellsize[a])) return fail(ctx, TM_ERR_ARG, "cellsize[%d] must be > 0", a);
   }
   if (nzd < 1 || nzd > n_out[2]) return fail(ctx, TM_ERR_ARG, "nzd = %d outside [1, nz = %d]", nzd, n_out[2]);
+  for (int a = 0; a < 3; a++)
+    if (L_in && L_in[a] != 0 && (!supported_L(L_in[a]) || L_in[a] < 2 * n_out[a]))
+      return fail(ctx, TM_ERR_SIZE, "L[%d] = %d is not a supported length >= 2 n = %d", a, L_in[a], 2 * n_out[a]);
   CK(cudaSetDevice(ctx->device));
   free_grid(ctx);
   ctx->nx = n_out[0];
@@ -769,7 +792,7 @@ int tm_set_grid(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[
   ctx->nzd = nzd;
   for (int a = 0; a < 3; a++) {
     ctx->d[a] = cellsize[a];
-    ctx->L[a] = pick_length(n_out[a]);
+    ctx->L[a] = (L_in && L_in[a] != 0) ? L_in[a] : pick_length(n_out[a]);
     if (ctx->L[a] == 0) return fail(ctx, TM_ERR_SIZE, "no supported FFT length for n = %d", n_out[a]);
   }
   const int Lx = ctx->L[0], Ly = ctx->L[1], Lz = ctx->L[2];

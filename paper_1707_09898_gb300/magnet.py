@@ -32,7 +32,7 @@ class Magnet:
     """One grid: output box n_out = (nx, ny, nz), design slab z < nzd, cell size in metres."""
 
     def __init__(self, n_out, nzd, cellsize=(1e-3, 1e-3, 1e-3), M0=(0.0, 0.0, 1.0 / (4e-7 * 3.141592653589793)),
-                 p=3.0, device=0, tensor=True):
+                 p=3.0, device=0, tensor=True, fft_lengths=None):
         self.L = _lib.lib()
         self.device = torch.device("cuda", device) if isinstance(device, int) else torch.device(device)
         h = ctypes.c_void_p()
@@ -41,7 +41,11 @@ class Magnet:
         self.n_out = tuple(int(v) for v in n_out)
         self.nzd = int(nzd)
         self.cellsize = tuple(float(v) for v in cellsize)
-        self._ck(self.L.tm_set_grid(self.h, _lib.c_int3(*self.n_out), self.nzd, _lib.c_double3(*self.cellsize)))
+        if fft_lengths is None:
+            self._ck(self.L.tm_set_grid(self.h, _lib.c_int3(*self.n_out), self.nzd, _lib.c_double3(*self.cellsize)))
+        else:  # chosen padded lengths (0: the default for that axis)
+            self._ck(self.L.tm_set_grid_lengths(self.h, _lib.c_int3(*self.n_out), self.nzd,
+                                                _lib.c_double3(*self.cellsize), _lib.c_int3(*fft_lengths)))
         self._ck(self.L.tm_set_penalty(self.h, float(p)))
         self.p = float(p)
         self.set_M0(M0)

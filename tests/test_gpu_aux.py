@@ -112,3 +112,22 @@ def test_log_and_bitwise_resume(tmp_path):
     assert abs(lines[-1]["volume_fraction"] - r.astype(np.float64).mean()) <= 1e-12
     assert lines[-1]["intermediate_fraction"] == np.mean((r > np.float32(0.1)) & (r < np.float32(0.9)))
     assert lines[-1]["grad_max"] == float(a.G.abs().max())
+
+
+def test_chosen_fft_lengths_are_checked():
+    """tm_set_grid_lengths: a length that is not supported or below 2 n is refused and the
+    grid stays as it was; 0 keeps the default of that axis."""
+    from paper_1707_09898_gb300 import Magnet, _lib
+
+    lib = _lib.lib()
+    m = Magnet((20, 24, 10), 6, device=0, tensor=False)
+    assert m.fft_lengths() == (48, 48, 24)  # the smallest supported L >= 2 n
+    cell = _lib.c_double3(1e-3, 1e-3, 1e-3)
+    for L in ((50, 48, 24), (36, 48, 24), (48, 48, 576 * 2)):
+        assert lib.tm_set_grid_lengths(m.h, _lib.c_int3(20, 24, 10), 6, cell, _lib.c_int3(*L)) == -2, L
+        assert m.fft_lengths() == (48, 48, 24)
+    assert lib.tm_set_grid_lengths(m.h, _lib.c_int3(20, 24, 10), 6, cell, _lib.c_int3(64, 0, 32)) == 0
+    assert m.fft_lengths() == (64, 48, 32)
+    # the default for 2 n in (256, 512) is 512
+    m2 = Magnet((130, 150, 192), 8, device=0, tensor=False)
+    assert m2.fft_lengths() == (512, 512, 512)

@@ -8,9 +8,9 @@
 * 128 x 128 x 66 with a von Mises-Fisher M0 and a random 3-component target:
   the autograd gradient against central differences of J in float64 on 64
   cells, and against the oracle gradient.
-* n^3 throughput workloads (n = 128, 192, 256; padded 256^3, 384^3 = (2^7 3)^3 and
-  512^3): J and dJ/drho of the prepared and the one-shot call, and the full-grid
-  field H, against the oracle on the whole grid.
+* n^3 throughput workloads (n = 128, 192, 256; padded 256^3, 512^3 and 512^3, and 192^3
+  also padded to 384^3 = (2^7 3)^3): J and dJ/drho of the prepared and the one-shot call,
+  and the full-grid field H, against the oracle on the whole grid.
 
 Every measured error is also recorded (tests/errlog.py).
 """
@@ -45,11 +45,11 @@ def _build():
     __graft_entry__.build()
 
 
-def magnet(wl):
+def magnet(wl, fft_lengths=None):
     from paper_1707_09898_gb300 import Magnet
 
     M0 = torch.from_numpy(wl.M0_field()).to(DEV) if wl.m0_kind != "const" else wl.M0_const()
-    return Magnet(wl.n_out, wl.nzd, wl.cellsize, M0=M0, p=wl.p, device=0)
+    return Magnet(wl.n_out, wl.nzd, wl.cellsize, M0=M0, p=wl.p, device=0, fft_lengths=fft_lengths)
 
 
 def test_config2_optimization_run():
@@ -149,10 +149,13 @@ def test_config3_autograd_against_central_differences():
         assert abs(G[jz, jy, jx] - fd) <= 1e-3 * abs(fd) + 1e-4 * np.abs(Gr).max()
 
 
-@pytest.mark.parametrize("n", [128, 192, 256])
-def test_throughput_workload_against_oracle(n):
+@pytest.mark.parametrize("n, L", [(128, 0), (192, 0), (192, 384), (256, 0)])
+def test_throughput_workload_against_oracle(n, L):
+    """L = 0: the default padding (256 for 128^3, 512 for 192^3 and 256^3); 192^3 also with
+    L = 384 = 2^7 3 chosen, the three-stage plan with its radix-3 stage at full size."""
     wl = W.config4(n)
-    m = magnet(wl)
+    m = magnet(wl, None if L == 0 else (L, L, L))
+    assert tuple(m.fft_lengths()) == ((L, L, L) if L else {128: (256,) * 3, 192: (512,) * 3, 256: (512,) * 3}[n])
     rho, mask = wl.rho(), wl.mask()
     Htc = tuple(float(v) for v in wl.Ht_const_vec())
     tmask = torch.from_numpy(mask).to(DEV)
@@ -164,7 +167,7 @@ def test_throughput_workload_against_oracle(n):
     H = m.stray_field(torch.from_numpy(rho).to(DEV)).cpu().numpy()
     for call, J, G in (("prepared", J1, G1), ("one-shot", J2, G2)):
         eJ, eG = abs(J - Jr) / abs(Jr), rel_l2(G.cpu().numpy(), Gr)
-        record(f"c4 {n}^3, {call}", H=rel_l2(H, Hr), J=eJ, G=eG)
+        record(f"c4 {n}^3 (L = {m.fft_lengths()[0]}), {call}", H=rel_l2(H, Hr), J=eJ, G=eG)
         assert eJ <= 1e-5
         assert eG <= 1e-4
     assert rel_l2(H, Hr) <= 1e-5
