@@ -43,8 +43,10 @@ __device__ void finish_j(const XInvArgs& a) {
   }
 }
 
-// P3: p = 3 fixed at compile time (chain sink with one contracted slot only).
-template <int L, int SINK, int MINB, bool P3>
+// P3: p = 3 fixed at compile time (chain sink with one contracted slot only). ONE: the
+// chain sink of one slot already contracted with the constant M0; else every slot with
+// its M0 component (MINB: the blocks per SM the registers are sized for).
+template <int L, int SINK, int MINB, bool P3, bool ONE>
 __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
   constexpr int S = plan_stages(L);
   using S0 = StageShape<L, 0>;
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
   const int row0 = a.row_base + blockIdx.x * ROWS;
   const cx<float>* in0 = reinterpret_cast<const cx<float>*>(a.in);
 
-  if constexpr (SINK == SINK_CHAIN && MINB == 2) {
+  if constexpr (SINK == SINK_CHAIN && ONE) {
     // one slot, already contracted with the constant M0: G = p rho^(p-1) D
     constexpr int RH = R / 2 > 0 ? R / 2 : 1;  // x = j + q M < nx <= L/2 needs q < R/2
     __shared__ float wmax[kNT / 32];
@@ -115,6 +117,57 @@ __global__ void __launch_bounds__(kNT, MINB) k_xinv(XInvArgs a) {
       for (int w = 1; w < kNT / 32; w++) gm = fmaxf(gm, wmax[w]);
       if (gm > 0.0f) atomicMax(a.gmax, __float_as_uint(gm));
     }
+    return;
+  } else if constexpr (SINK == SINK_CHAIN && R == 2 * TB && M == TB && ITER == 1) {
+    // every slot with its M0 component, L = 512 = 32 x 16: the last inverse stage forms only
+    // the outputs x = j + q M < L/2 (q < R/2; nx <= L/2), and the sums over the slots stay in
+    // registers for those
+    constexpr int RH = R / 2;
+    const int j = threadIdx.x % M, line = threadIdx.x / M;
+    const int ra = row0 + 2 * line, rb = ra + 1;
+    float acc[RH][2];
+#pragma unroll
+    for (int q = 0; q < RH; q++) acc[q][0] = acc[q][1] = 0.0f;
+    for (int jc = 0; jc < a.ncomp; jc++) {
+      __syncthreads();
+      xhermitian<L>(tile, in0 + a.in_slot[jc] * a.in_cstride, row0, a.rows, a.P);
+      __syncthreads();
+      DitRange<float, L, kNT, 1, S, true>::run(tile, tw);
+      const int c = a.comp[jc];
+      cx<float> v[R];
+#pragma unroll
+      for (int q = 0; q < R; q++) v[q] = tile[tix0<M>(j, q, line)];
+      twiddle0<L, true>(v, j, tw0);
+      dft_low_half<R, true>(v);
+#pragma unroll
+      for (int q = 0; q < RH; q++) {
+        const int x = j + q * M;
+        float ma = 1.0f, mb = 1.0f;  // contracted slot: coefficient 1
+        if (a.M0v && x < a.nx) {
+          if (ra < a.rows) ma = a.M0v[c * a.M0v_cstride + (long long)ra * a.nx + x];
+          if (rb < a.rows) mb = a.M0v[c * a.M0v_cstride + (long long)rb * a.nx + x];
+        }
+        acc[q][0] += ma * v[q].x;
+        acc[q][1] += mb * v[q].y;
+      }
+    }
+    float gm = 0.0f;
+#pragma unroll
+    for (int q = 0; q < RH; q++) {
+      const int x = j + q * M;
+      if (x >= a.nx) continue;
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int row = ra + h;
+        if (row >= a.rows) continue;
+        const long long o = (long long)row * a.nx + x;
+        const float G = dpow(a.rho[o], a.p) * acc[q][h];
+        a.G[o] = G;
+        gm = fmaxf(gm, fabsf(G));
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, off));
+    if ((threadIdx.x & 31) == 0 && gm > 0.0f) atomicMax(a.gmax, __float_as_uint(gm));
     return;
   } else if constexpr (SINK == SINK_CHAIN) {
     float acc[ITER][R][2];
@@ -450,12 +503,12 @@ int run_xinv_ws(const XInvArgs& a, cudaStream_t s) {
   return launch_k(k_xinv_ws<L, P3>, dim3(blocks), dim3(2 * kNT), sm, s, a.pdl != 0, a) == cudaSuccess ? 0 : -1;
 }
 
-template <int L, int SINK, int MINB, bool P3>
+template <int L, int SINK, int MINB, bool P3, bool ONE = false>
 int run_xinv_sink(const XInvArgs& a, cudaStream_t s) {
   const size_t sm = xsmem<L>();
   static bool init = false;
   if (!init) {
-    if (cudaFuncSetAttribute(k_xinv<L, SINK, MINB, P3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+    if (cudaFuncSetAttribute(k_xinv<L, SINK, MINB, P3, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
         cudaSuccess)
       return -1;
     init = true;
@@ -463,7 +516,7 @@ int run_xinv_sink(const XInvArgs& a, cudaStream_t s) {
   const int blocks = (a.rows - a.row_base + ROWS - 1) / ROWS;
   if (blocks <= 0 || a.ncomp == 0) return 0;
   const int gy = SINK == SINK_CHAIN ? 1 : a.ncomp;
-  return launch_k(k_xinv<L, SINK, MINB, P3>, dim3(blocks, gy), dim3(kNT), sm, s, a.pdl != 0, a) == cudaSuccess ? 0
+  return launch_k(k_xinv<L, SINK, MINB, P3, ONE>, dim3(blocks, gy), dim3(kNT), sm, s, a.pdl != 0, a) == cudaSuccess ? 0
                                                                                                         : -1;
 }
 template <int L>
@@ -475,11 +528,16 @@ int run_xinv(const XInvArgs& a, cudaStream_t s) {
       // warp-specialized form when the block's raw rows fit beside the two tiles
       if (a.row_base == 0 && xinv_ws_smem<L>(a.P) <= 227 * 1024 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0)
         return a.p == 3.0f ? run_xinv_ws<L, true>(a, s) : run_xinv_ws<L, false>(a, s);
-      if (a.p == 3.0f) return run_xinv_sink<L, SINK_CHAIN, 2, true>(a, s);
+      if (a.p == 3.0f) return run_xinv_sink<L, SINK_CHAIN, 2, true, true>(a, s);
     }
-    return run_xinv_sink<L, SINK_CHAIN, 2, false>(a, s);
+    return run_xinv_sink<L, SINK_CHAIN, 2, false, true>(a, s);
   }
-  return run_xinv_sink<L, SINK_CHAIN, 1, false>(a, s);
+  // every slot with its M0 component; L = 512: three blocks per SM (at 256^3 with a varying
+  // M0 the pass took 665 us forming all 32 outputs per unit with one block per SM, 327 us
+  // with the low half and two, 304 us with three, despite the spills)
+  if constexpr (StageShape<L, 0>::R == 2 * TB && StageShape<L, 0>::M == TB)
+    return run_xinv_sink<L, SINK_CHAIN, 3, false, false>(a, s);
+  return run_xinv_sink<L, SINK_CHAIN, 1, false, false>(a, s);
 }
 
 }  // namespace

@@ -36,9 +36,27 @@ def blib():
     return _blib
 
 
+def plain_length(n):
+    """Padded length of the plain pipeline: the smallest even 2^a 3^b (b <= 2, >= 8) >= 2 n,
+    which cuFFT transforms directly (no replacement of 288 or 384 by 512)."""
+    L = max(8, 2 * n)
+    while True:
+        r = L
+        while r % 2 == 0:
+            r //= 2
+        b = 0
+        while r % 3 == 0:
+            r //= 3
+            b += 1
+        if L % 2 == 0 and r == 1 and b <= 2:
+            return L
+        L += 1
+
+
 class CufftMagnet:
     def __init__(self, n_out, nzd, cellsize, M0, p=3.0, device=0):
-        self.m = Magnet(n_out, nzd, cellsize, M0=M0, p=p, device=device)
+        self.m = Magnet(n_out, nzd, cellsize, M0=M0, p=p, device=device,
+                        fft_lengths=tuple(plain_length(int(n)) for n in n_out))
         self.device = self.m.device
         self.design_shape, self.out_shape = self.m.design_shape, self.m.out_shape
         L = self.m.fft_lengths()

@@ -357,3 +357,61 @@ def test_length_512_fast_paths(shape):
     H = m.stray_field(rho_t).cpu().numpy()
     Hr = op.forward(O.magnetization(rho, wl.M0_const(), wl.p))
     assert rel_l2(H, Hr) <= 1e-5
+
+
+@pytest.mark.parametrize("planes", [tuple(range(140, 150)), (143, 147)])
+@pytest.mark.parametrize("w", [(0.0, 0.0, 1.0), (1.0, 0.0, 2.0)])
+def test_length_512_z_pass(planes, w):
+    """nz = 150 pads z to 512, the one-input z pass that transforms each column tile once
+    for all outputs: the full field (every plane), the prepared target on 10 planes (the
+    whole-grid route: output and input planes restricted to the device range) and on 2
+    (few planes: the direct transforms of those planes), with one or two weighted field
+    components (one or two outputs per column tile), and the one-shot call."""
+    wl = W.small((24, 20, 150), 140, seed=81, w=w, ht_kind="normal")
+    m = magnet(wl)
+    assert m.fft_lengths()[2] == 512
+    mask = np.zeros(wl.out_shape, dtype=np.uint8)
+    rng = np.random.default_rng(82)
+    for z in planes:
+        mask[z] = rng.random(wl.out_shape[1:]) < 0.4
+    Htf = wl.Ht_field()
+    rho = wl.rho()
+    rho_t = torch.from_numpy(rho).to(DEV)
+    m.set_target(torch.from_numpy(mask).to(DEV), Ht=torch.from_numpy(Htf).to(DEV), w=w)
+    J1, G1 = m.evaluate(rho_t)
+    J2, G2 = m.objective_and_gradient(rho_t, torch.from_numpy(mask).to(DEV), Ht=torch.from_numpy(Htf).to(DEV), w=w)
+    op = oracle_op(wl)
+    Jr, Gr, _ = O.objective_and_gradient(op, rho, wl.M0_const(), wl.p, mask, Htf, w)
+    for J, G in ((J1, G1), (J2, G2)):
+        assert abs(J - Jr) <= 1e-5 * abs(Jr)
+        assert rel_l2(G.cpu().numpy(), Gr) <= 1e-4
+    H = m.stray_field(rho_t).cpu().numpy()
+    Hr = op.forward(O.magnetization(rho, wl.M0_const(), wl.p))
+    assert rel_l2(H, Hr) <= 1e-5
+
+
+@pytest.mark.parametrize("shape", [(140, 18, 12, 9), (150, 33, 10, 10)])
+def test_length_512_varying_magnetization(shape):
+    """A varying M0 on grids padded to 512 along x: three magnetization spectra in and out,
+    and the chain rule that sums the three components' inverse x transforms (the 32 x 16
+    form forms only the kept half of each row); prepared and one-shot calls and the
+    field against the oracle."""
+    nx, ny, nz, nzd = shape
+    wl = W.small((nx, ny, nz), nzd, seed=91, m0_kind="vmf", w=(1.0, 0.0, 2.0))
+    m = magnet(wl)
+    assert m.fft_lengths()[0] == 512
+    mask = wl.mask()
+    Htc = tuple(float(v) for v in wl.Ht_const_vec())
+    tmask = torch.from_numpy(mask).to(DEV)
+    m.set_target(tmask, Ht_const=Htc, w=wl.w)
+    rho = wl.rho()
+    rho_t = torch.from_numpy(rho).to(DEV)
+    out = [m.evaluate(rho_t), m.objective_and_gradient(rho_t, tmask, Ht_const=Htc, w=wl.w)]
+    op = oracle_op(wl)
+    Jr, Gr, _ = O.objective_and_gradient(op, rho, wl.M0_field(), wl.p, mask, wl.Ht_const_vec(), wl.w)
+    for J, G in out:
+        assert abs(J - Jr) <= 1e-5 * abs(Jr)
+        assert rel_l2(G.cpu().numpy(), Gr) <= 1e-4
+    H = m.stray_field(rho_t).cpu().numpy()
+    Hr = op.forward(O.magnetization(rho, wl.M0_field(), wl.p))
+    assert rel_l2(H, Hr) <= 1e-5
