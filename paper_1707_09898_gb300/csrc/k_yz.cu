@@ -510,6 +510,35 @@ __global__ void __launch_bounds__(kNT, 2) k_z3(ZArgs a) {
   __syncthreads();
   if (din) {
     direct_in<L>(tile, tw, in, a.zstride, ilo, ihi, small);
+  } else if constexpr (zmulti_plan<L>()) {  // n_in <= L/2: the half-zero radix-32 stage, then radix 16
+    constexpr int R0 = StageShape<L, 0>::R, M0 = StageShape<L, 0>::M, R1 = StageShape<L, 1>::R;
+    const int line = threadIdx.x % TB, j = threadIdx.x / TB;
+    {
+      cx<float> v[R0];
+#pragma unroll
+      for (int q = 0; q < R0 / 2; q++) {
+        const int z = j + q * M0;
+        v[q] = (z >= ilo && z < ihi) ? in[z * a.zstride + line] : zero<float>();
+      }
+      dft32_half_input<false>(v);
+      if (j != 0) {
+#pragma unroll
+        for (int q = 1; q < R0; q++) v[q] = cmul(v[q], tw[j * q]);
+      }
+#pragma unroll
+      for (int q = 0; q < R0; q++) tile[(j + q * M0) * TB + line] = v[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < 2; it++) {
+      const int g = it * (R0 / 2) + j;
+      cx<float> v[R1];
+#pragma unroll
+      for (int q = 0; q < R1; q++) v[q] = tile[(g * R1 + q) * TB + line];
+      DftF<R1, false>::run(v);
+#pragma unroll
+      for (int q = 0; q < R1; q++) tile[(g * R1 + q) * TB + line] = v[q];
+    }
   } else {
     dif_stage0_load<float, L, kNT>(tile, tw, [&](int pos, int line) {
       return (pos >= ilo && pos < ihi) ? in[pos * a.zstride + line] : zero<float>();
@@ -530,7 +559,7 @@ __global__ void __launch_bounds__(kNT, 2) k_z3(ZArgs a) {
 #pragma unroll
     for (int i = 0; i < 3; i++) {
       src[i] = i < a.nin ? cluster.map_shared_rank(tile, i) : tile;
-      tc[i] = make_tcol(a, r, i < a.nin ? i : 0, kyf, sy, chunk * TB);
+      if constexpr (!zmulti_plan<L>()) tc[i] = make_tcol(a, r, i < a.nin ? i : 0, kyf, sy, chunk * TB);
     }
 #pragma unroll
     for (int it = 0; it < ITER; it++) {
@@ -538,22 +567,43 @@ __global__ void __launch_bounds__(kNT, 2) k_z3(ZArgs a) {
       if (SS::NU % kNT == 0 || u < SS::NU) {
         const int line = u % TB, g = u / TB;
         const int kb = k_of_group<L>(g);
+        if constexpr (zmulti_plan<L>()) {
+          // the factors of one input at a time, all loads in flight (two folded-row bases)
 #pragma unroll
-        for (int q = 0; q < R; q++) {
-          const int pos = (g * R + q) * TB + line;
-          const int kz = kb + q * (L / R);
-          cx<float> acc = zero<float>();
+          for (int q = 0; q < R; q++) res[it][q] = zero<float>();
 #pragma unroll
           for (int i = 0; i < 3; i++) {
             if (i < a.nin) {
-              TensorCol tl = tc[i];
-              tl.T += line;
-              acc = acc + scale(src[i][pos], tl.at(kz, L));
+              const TensorCol tl = make_tcol(a, r, i, kyf, sy, chunk * TB + line);  // made here: fewer live registers
+              float f[R];
+              z_factors<L>(tl, kb, f);
+#pragma unroll
+              for (int q = 0; q < R; q++) res[it][q] = res[it][q] + scale(src[i][(g * R + q) * TB + line], f[q]);
             }
           }
-          res[it][q] = acc;
+          if (!dout) DftF<R, true>::run(res[it]);
+          if (it == 0) {  // the first unit waits in shared memory (its registers go to the second)
+#pragma unroll
+            for (int q = 0; q < R; q++) tile[L * TB + q * kNT + threadIdx.x] = res[0][q];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < R; q++) {
+            const int pos = (g * R + q) * TB + line;
+            const int kz = kb + q * (L / R);
+            cx<float> acc = zero<float>();
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+              if (i < a.nin) {
+                TensorCol tl = tc[i];
+                tl.T += line;
+                acc = acc + scale(src[i][pos], tl.at(kz, L));
+              }
+            }
+            res[it][q] = acc;
+          }
+          if (!dout) Dft<float, R, true>::run(res[it]);
         }
-        if (!dout) Dft<float, R, true>::run(res[it]);
       }
     }
   }
@@ -565,7 +615,8 @@ __global__ void __launch_bounds__(kNT, 2) k_z3(ZArgs a) {
     if (SS::NU % kNT == 0 || u < SS::NU) {
       const int line = u % TB, g = u / TB;
 #pragma unroll
-      for (int q = 0; q < R; q++) tile[(g * R + q) * TB + line] = res[it][q];
+      for (int q = 0; q < R; q++)
+        tile[(g * R + q) * TB + line] = (zmulti_plan<L>() && it == 0) ? tile[L * TB + q * kNT + threadIdx.x] : res[it][q];
     }
   }
   __syncthreads();
@@ -573,10 +624,28 @@ __global__ void __launch_bounds__(kNT, 2) k_z3(ZArgs a) {
   if (dout) {
     direct_out<L>(tile, tw, out, a.zstride, olo, ohi, small);
   } else {
-    DitRange<float, L, kNT, 1, S - 1>::run(tile, tw);
-    dit_stage0_store<float, L, kNT>(tile, tw, [&](int pos, int line, cx<float> v) {
-      if (pos >= olo && pos < ohi) out[pos * a.zstride + line] = v;
-    });
+    if constexpr (zmulti_plan<L>()) {  // n_out <= L/2: only the rows z < L/2 are formed
+      constexpr int R0 = StageShape<L, 0>::R, M0 = StageShape<L, 0>::M;
+      const int line = threadIdx.x % TB, j = threadIdx.x / TB;
+      cx<float> v[R0];
+#pragma unroll
+      for (int q = 0; q < R0; q++) v[q] = tile[(j + q * M0) * TB + line];
+      if (j != 0) {
+#pragma unroll
+        for (int q = 1; q < R0; q++) v[q] = cmulc(v[q], tw[j * q]);
+      }
+      dft_low_half<R0, true>(v);
+#pragma unroll
+      for (int q = 0; q < R0 / 2; q++) {
+        const int z = j + q * M0;
+        if (z >= olo && z < ohi) out[z * a.zstride + line] = v[q];
+      }
+    } else {
+      DitRange<float, L, kNT, 1, S - 1>::run(tile, tw);
+      dit_stage0_store<float, L, kNT>(tile, tw, [&](int pos, int line, cx<float> v) {
+        if (pos >= olo && pos < ohi) out[pos * a.zstride + line] = v;
+      });
+    }
   }
 }
 
@@ -628,16 +697,18 @@ int run_z(const ZArgs& a, cudaStream_t s) {
     k_z1<L><<<grid, kNT, sm, s>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? 0 : -1;
   }
+  // the 32 x 16 plan keeps each thread's first output unit in shared memory beside the tile
+  const size_t sm3 = sm + (zmulti_plan<L>() ? (size_t)kNT * TB * sizeof(float2) : 0);
   static bool init3 = false;
   if (!init3) {
-    if (cudaFuncSetAttribute(k_z3<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_z3<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3) != cudaSuccess)
       return -1;
     init3 = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.nin * (a.P / TB), a.Ly, 1);
   cfg.blockDim = dim3(kNT, 1, 1);
-  cfg.dynamicSmemBytes = sm;
+  cfg.dynamicSmemBytes = sm3;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -390,16 +390,17 @@ def test_length_512_z_pass(planes, w):
     assert rel_l2(H, Hr) <= 1e-5
 
 
-@pytest.mark.parametrize("shape", [(140, 18, 12, 9), (150, 33, 10, 10)])
-def test_length_512_varying_magnetization(shape):
-    """A varying M0 on grids padded to 512 along x: three magnetization spectra in and out,
-    and the chain rule that sums the three components' inverse x transforms (the 32 x 16
-    form forms only the kept half of each row); prepared and one-shot calls and the
-    field against the oracle."""
+@pytest.mark.parametrize("shape,axis", [((140, 18, 12, 9), 0), ((150, 33, 10, 10), 0), ((20, 16, 140, 130), 2)])
+def test_length_512_varying_magnetization(shape, axis):
+    """A varying M0 on grids padded to 512 along x or z: three magnetization spectra in and
+    out; along x the chain rule that sums the three components' inverse x transforms (the
+    32 x 16 form forms only the kept half of each row), along z the cluster z pass of three
+    inputs (half-zero forward stage, kept-half inverse); prepared and one-shot calls and
+    the field against the oracle."""
     nx, ny, nz, nzd = shape
     wl = W.small((nx, ny, nz), nzd, seed=91, m0_kind="vmf", w=(1.0, 0.0, 2.0))
     m = magnet(wl)
-    assert m.fft_lengths()[0] == 512
+    assert m.fft_lengths()[axis] == 512
     mask = wl.mask()
     Htc = tuple(float(v) for v in wl.Ht_const_vec())
     tmask = torch.from_numpy(mask).to(DEV)
