@@ -83,6 +83,10 @@ int tm_set_grid(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[
  */
 int tm_set_grid_lengths(tm_ctx* ctx, const int n_out[3], int nzd, const double cellsize[3], const int L[3]);
 
+/* The padded length tm_set_grid picks for an axis of n cells (1 <= n <= 288), else 0.
+ * Needs no context and no GPU. */
+int tm_default_fft_length(int n);
+
 /* The padded FFT lengths (Lx, Ly, Lz) chosen by tm_set_grid. */
 int tm_get_fft_lengths(const tm_ctx* ctx, int L[3]);
 

@@ -32,6 +32,7 @@ _SIGS = {
     "tm_version": (ctypes.c_char_p, []),
     "tm_set_grid": (ctypes.c_int, [vp, c_int3, ctypes.c_int, c_double3]),
     "tm_set_grid_lengths": (ctypes.c_int, [vp, c_int3, ctypes.c_int, c_double3, c_int3]),
+    "tm_default_fft_length": (ctypes.c_int, [ctypes.c_int]),
     "tm_get_fft_lengths": (ctypes.c_int, [vp, c_int3]),
     "tm_set_penalty": (ctypes.c_int, [vp, ctypes.c_double]),
     "tm_set_M0": (ctypes.c_int, [vp, vp, c_double3, vp]),

@@ -829,6 +829,8 @@ int tm_set_grid_lengths(tm_ctx* ctx, const int n_out[3], int nzd, const double c
   return TM_OK;
 }
 
+int tm_default_fft_length(int n) { return n >= 1 && n <= kMaxL / 2 ? pick_length(n) : 0; }
+
 int tm_get_fft_lengths(const tm_ctx* ctx, int L[3]) {
   if (!ctx || !L) return TM_ERR_ARG;
   if (!ctx->have_grid) return TM_ERR_STATE;

@@ -64,3 +64,19 @@ def test_fault_injection_from_the_environment(lib):
                          timeout=120)
     assert out.returncode == 0, out.stderr
     assert out.stdout.strip() == "[-1, -1, -7]"
+
+
+def test_default_padding_without_a_gpu(lib):
+    """tm_set_grid's padded length per axis: the smallest supported even 2^a 3^b >= 2 n,
+    with 288 and 384 replaced by 512 (any L >= 2 n is the same linear convolution); the
+    cuFFT comparison pipeline keeps the smallest length itself."""
+    from paper_1707_09898_gb300.cufft_pipeline import plain_length
+
+    L = lib.lib()
+    want = {1: 8, 4: 8, 5: 12, 10: 24, 17: 36, 60: 128, 100: 256, 128: 256, 129: 512, 144: 512,
+            150: 512, 192: 512, 200: 512, 256: 512, 257: 576, 288: 576}
+    for n, Lx in want.items():
+        assert L.tm_default_fft_length(n) == Lx, n
+        assert Lx >= 2 * n
+    assert L.tm_default_fft_length(0) == 0 and L.tm_default_fft_length(289) == 0
+    assert [plain_length(n) for n in (5, 17, 129, 150, 192, 256)] == [12, 36, 288, 384, 384, 512]
